@@ -1,0 +1,468 @@
+#!/usr/bin/env python
+"""Benchmark of the Hermite block-timestep force path on GB300.
+
+Workload (the force sweep the headline metric is quoted on): Plummer model,
+N = 16384, seed 2, eps = 1/256, standard N-body units.  One bench step is one
+full block step of the Hermite scheme (select -> predict -> force -> correct,
+steps 1-8 of Sec. 2) for each active-block size n_act in {32, 256, 2048,
+16384}; before each block step the state is restored on the device so every
+step does identical work.  The active block of size n_act is the first n_act
+particles of a seeded permutation (their dt is 2^-10, everyone else's 2^-4).
+
+Three precision modes run the same timed step: MIXED (the paper's scheme on
+FP32 pipes), DS (double-single pair arithmetic) and FP64.  Each is checked on
+every particle against the FP64 GPU path (itself held within 1e-10 of the
+FP64 CPU oracle by the parity tests); the headline value is acc+jerk
+interactions per second (n_act * N per block step, self pair counted) of the
+fastest mode whose largest relative error in acc, jerk and pot is <= 1e-6.
+The force kernel's roofline, an end-to-end figure through host buffers and
+the CPU oracle baseline are reported on the same JSON line.
+
+Under torchrun (--gpus N > 1) every rank runs an independent replica of the
+workload on its own GPU (weak scaling); the timed region is bracketed by a
+barrier and the slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1104_2700_gb300 import ics  # noqa: E402
+
+METRIC = "acc+jerk interactions/s on 1 GB300, mixed vs FP64, at rel. force err ≤1e-6"
+UNIT = "interactions/s"
+FLOPS_PER_INTERACTION = 60  # the paper's convention (Sec. 5)
+NACTS = ics.FORCE_SWEEP_NACT
+WL = ics.FORCE_SWEEP_N16K
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+# --- distributed plumbing -------------------------------------------------------
+def dist_setup(backend):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend=backend)
+    return rank, local, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --- clocks ---------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows
+                                   if r[3].replace(".", "").isdigit()) if rows else None}
+
+
+# --- workload -------------------------------------------------------------------
+def block_states(base, perm):
+    """Per n_act: the state whose scheduler picks the first n_act of perm."""
+    n = len(base["m"])
+    out = []
+    for k in NACTS:
+        dt = np.full(n, 2.0 ** -4)
+        dt[perm[:k]] = 2.0 ** -10
+        st = dict(base)
+        st["t"] = np.zeros(n)
+        st["dt"] = dt
+        out.append(st)
+    return out
+
+
+def to_device(st, torch, dev):
+    return {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in st.items()}
+
+
+def to_pinned(st, torch):
+    return {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in st.items()}
+
+
+def run_ours(args):
+    import torch
+    from paper_1104_2700_gb300 import build as nb_build
+    from paper_1104_2700_gb300 import nbody
+
+    rank, local, world = dist_setup("nccl" if args.gpus > 1 else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    nb_build.build()
+    # One explicit stream carries the library's kernels, the L2 flush and the
+    # timing events (the legacy default stream has handle 0, which the
+    # library would replace by a private stream).
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+
+    n, eps, eta = WL.n, WL.eps, WL.eta
+    m, r, v = WL.particles()
+    perm = ics.permutation(n, WL.seed)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    inter_per_step = sum(k * n for k in NACTS)
+    all_idx = np.arange(n, dtype=np.int32)
+
+    def forces_at_t0(ctx):
+        ctx.set_state(m, r, v, np.zeros((n, 3)), np.zeros((n, 3)), np.zeros(n),
+                      np.full(n, 1.0 / 16), eps, eta)
+        ctx.predict(0.0)
+        return ctx.force(all_idx)
+
+    # Accuracy reference for every particle: the FP64 GPU path (which the
+    # parity tests hold within 1e-10 of the FP64 CPU oracle on this workload).
+    with nbody.Context("fp64", device=local, stream=stream) as ref_ctx:
+        a_ref, j_ref, p_ref = forces_at_t0(ref_ctx)
+
+    def accuracy(ctx):
+        a, j, p = forces_at_t0(ctx)
+        ea = np.linalg.norm(a - a_ref, axis=1) / np.linalg.norm(a_ref, axis=1)
+        ej = np.linalg.norm(j - j_ref, axis=1) / np.linalg.norm(j_ref, axis=1)
+        ep = np.abs(p - p_ref) / np.abs(p_ref)
+        return {"particles": n,
+                "acc_rel_max": float(ea.max()), "acc_rel_p50": float(np.median(ea)),
+                "acc_rel_p99": float(np.quantile(ea, 0.99)),
+                "jerk_rel_max": float(ej.max()), "jerk_rel_p50": float(np.median(ej)),
+                "jerk_rel_p99": float(np.quantile(ej, 0.99)),
+                "pot_rel_max": float(ep.max()),
+                "n_above_1e-6": int(np.sum((ea > 1e-6) | (ej > 1e-6) | (ep > 1e-6)))}
+
+    def measure(precision, steps, warmup):
+        ctx = nbody.Context(precision, device=local, stream=stream)
+        ctx.set_particles(m, r, v, eps, eta)
+        base = ctx.get_state()
+        base["m"] = m
+        states = block_states({k: base[k] for k in ("m", "r", "v", "a", "j")}, perm)
+        dstates = [to_device(s, torch, dev) for s in states]
+
+        def enqueue_step():
+            for s in dstates:
+                ctx.set_state(s["m"], s["r"], s["v"], s["a"], s["j"], s["t"], s["dt"], eps, eta)
+                ctx.block_step(1.0)
+
+        # Every call above is stream-ordered and device-resident, so the whole
+        # step is captured once as a CUDA graph and replayed (one launch per
+        # step instead of ~100 host calls).
+        enqueue_step()
+        ctx.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            enqueue_step()
+        torch.cuda.set_stream(stream)
+        for _ in range(warmup):
+            graph.replay()
+        ctx.synchronize()
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        times = []
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            graph.replay()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        ctx.synchronize()
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        total = reduce_max(sum(times), world, dev)
+        del graph
+        return ctx, states, dstates, total
+
+    def force_launch_time(ctx, dstate, reps=20):
+        """Average duration of one force launch with n_act = N (CUDA events)."""
+        s = dstate
+        ctx.set_state(s["m"], s["r"], s["v"], s["a"], s["j"], s["t"], s["dt"], eps, eta)
+        ctx.predict(0.0)
+        idx_all = torch.arange(n, dtype=torch.int32, device=dev)
+        for _ in range(3):
+            ctx.force(idx_all)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            ctx.force(idx_all)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps
+
+    modes = {}
+    contexts = {}
+    clocks = ClockSampler(local)
+    order = [("mixed", args.steps), ("ds", args.steps)]
+    if not args.no_fp64:
+        order.append(("fp64", max(2, args.steps // 10)))
+    clk = None
+    for prec, k in order:
+        sampler = ClockSampler(local)
+        sampler.start()
+        ctx, states, dstates, total = measure(prec, k, args.warmup)
+        c = sampler.stop()
+        t_force = force_launch_time(ctx, dstates[-1])
+        acc = accuracy(ctx)
+        modes[prec] = {"value": world * inter_per_step * k / total, "unit": UNIT, "steps": k,
+                       "ms_per_step": 1e3 * total / k,
+                       "force_launch_ms_nact_N": t_force * 1e3,
+                       "force_interactions_per_s": n * n / t_force,
+                       "accuracy_vs_fp64": acc, "clocks": c}
+        contexts[prec] = (ctx, states)
+    gate = {p: max(mo["accuracy_vs_fp64"][q] for q in ("acc_rel_max", "jerk_rel_max",
+                                                          "pot_rel_max")) <= 1e-6
+            for p, mo in modes.items()}
+    passing = [p for p in modes if gate[p]]
+    head = max(passing, key=lambda p: modes[p]["value"]) if passing else "fp64"
+    hm = modes[head]
+    for p in modes:
+        modes[p]["meets_1e-6_gate"] = gate[p]
+
+    props = torch.cuda.get_device_properties(dev)
+    clk = hm["clocks"]
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak32 = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+
+    def roofline_of(p, kernel):
+        ach = FLOPS_PER_INTERACTION * modes[p]["force_interactions_per_s"] / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": peak32, "unit": "TFLOP/s",
+                "frac": ach / peak32, "traffic": None, "kernel": kernel,
+                "launch_ms": modes[p]["force_launch_ms_nact_N"],
+                "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x "
+                              f"{sm_max:.0f} MHz max SM clock (derived, not measured); "
+                              f"60 flop per interaction (paper convention)"}
+
+    kname = {"mixed": "force_kernel<PolicyMixed<2>,2>", "ds": "force_kernel<PolicyDS<1>,1>",
+             "fp64": "force_kernel<PolicyFP64<1>,1>"}
+    roofline = roofline_of(head, kname[head])
+    roofline_mixed = roofline_of("mixed", kname["mixed"])
+
+    # End to end through the public API with host buffers: every step copies
+    # the state in from pinned host memory and the corrected state back out.
+    e2e = None
+    if not args.no_e2e:
+        ctx, states = contexts[head]
+        hst = [to_pinned(s, torch) for s in states]
+        outs = {k: torch.empty((n, 3), dtype=torch.float64).pin_memory() for k in ("r", "v", "a", "j")}
+        outs.update({k: torch.empty(n, dtype=torch.float64).pin_memory() for k in ("t", "dt")})
+        lib = nbody
+
+        def e2e_step():
+            for s in hst:
+                st = lib.nb_set_state(ctx.handle, n, *[ctypes_ptr(s[k]) for k in
+                                                       ("m", "r", "v", "a", "j", "t", "dt")],
+                                      eps, eta, 0)
+                assert st == 0, lib.nb_last_error(ctx.handle)
+                ctx.block_step(1.0)
+                st = lib.nb_get_state(ctx.handle, *[ctypes_ptr(outs[k]) for k in
+                                                    ("r", "v", "a", "j", "t", "dt")], 0)
+                assert st == 0, lib.nb_last_error(ctx.handle)
+
+        ke = max(2, min(args.steps, 200))
+        for _ in range(min(args.warmup, 3)):
+            e2e_step()
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        w0 = time.perf_counter()
+        for _ in range(ke):
+            e2e_step()
+        torch.cuda.synchronize(dev)
+        w = reduce_max(time.perf_counter() - w0, world, dev)
+        e2e = {"value": world * inter_per_step * ke / w, "unit": UNIT, "steps": ke,
+               "precision": head,
+               "h2d_bytes_per_step": len(NACTS) * n * 8 * (1 + 12 + 2),
+               "d2h_bytes_per_step": len(NACTS) * n * 8 * (12 + 2)}
+    for ctx, _ in contexts.values():
+        ctx.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(m, r, v, eps, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": hm["value"], "unit": UNIT, "n_gpus": world,
+            "steps": hm["steps"], "warmup": args.warmup, "ms_per_step": hm["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WL.name, "n": n, "n_act": list(NACTS), "eps": eps,
+                       "seed": WL.seed, "precision": head, "parallelism": f"replicas{world}",
+                       "step": "select+predict+force+correct per n_act, state restored on "
+                               "device, whole step replayed as one CUDA graph",
+                       "l2": "flushed (512 MiB write) between timed steps",
+                       "interactions_per_step": inter_per_step,
+                       "gflops_60flop": hm["value"] * FLOPS_PER_INTERACTION / 1e9,
+                       "gate": "max over all N particles of rel. err of acc, jerk, pot <= 1e-6"},
+            "roofline": roofline,
+            "roofline_mixed_kernel": roofline_mixed,
+            "modes": modes,
+            "fp64_speedup": (hm["value"] / modes["fp64"]["value"]) if "fp64" in modes else None,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "gpu_launches": 10 * len(NACTS) * hm["steps"],
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def ctypes_ptr(t):
+    import ctypes
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# --- CPU baseline: the oracle as it stands ------------------------------------------
+def cpu_baseline(m, r, v, eps, seconds):
+    from oracle import oracle
+    n = len(m)
+    cores = os.cpu_count() or 1
+    perm = ics.permutation(n, 5)
+    probe = perm[:max(cores, 32)]
+    t0 = time.perf_counter()
+    oracle.force(m, r, v, eps, idx=probe, nthreads=cores)
+    dt = time.perf_counter() - t0
+    k = int(min(n, max(len(probe), seconds / max(dt, 1e-9) * len(probe))))
+    sample = perm[:k]
+    reps = 0
+    t0 = time.perf_counter()
+    while True:  # the whole sample, repeated until the time budget is used
+        oracle.force(m, r, v, eps, idx=sample, nthreads=cores)
+        reps += 1
+        dt = time.perf_counter() - t0
+        if dt >= 0.5 * seconds:
+            break
+    inter = reps * k * n
+    return {"value": inter / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle force (Eqs. acc, jrk, pot) on {k} of the {n} particles "
+                      f"against all {n} j, x{reps}, OpenMP over i, {dt:.1f} s",
+            "gflops_60flop": inter / dt * FLOPS_PER_INTERACTION / 1e9}
+
+
+def run_reference(args):
+    """The FP64 oracle timed on the host cores on a bounded sample of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle
+    oracle.build()
+    n, eps = WL.n, WL.eps
+    m, r, v = WL.particles()
+    perm = ics.permutation(n, WL.seed)
+    cores = os.cpu_count() or 1
+    # each step: the force sweep with every block capped at 64 i particles
+    blocks = [perm[:min(k, 64)] for k in NACTS]
+    inter = sum(len(b) * n for b in blocks)
+
+    def step():
+        for b in blocks:
+            oracle.force(m, r, v, eps, idx=b, nthreads=cores)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = inter * args.steps / dt
+    sample = (f"force sweep N={n} with each active block capped at 64 i "
+              f"({inter} interactions per step), FP64 oracle, OpenMP over i")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WL.name, "n": n, "n_act": list(NACTS), "eps": eps,
+                   "seed": WL.seed, "precision": "fp64-oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,171 @@
+/*
+ * nbody.h - C ABI of libnbody, a GB300 (sm_103a) implementation of the
+ * fourth-order Hermite scheme with hierarchical (block) individual
+ * timesteps of Tanikawa, Yoshikawa, Okamoto & Nitadori (arXiv:1104.2700),
+ * Sec. 2, whose O(n_act * N) force evaluation (Sec. 3, Eqs. acc, jrk, pot)
+ * runs in hand-written CUDA kernels.
+ *
+ * Conventions for every call
+ *   - Every call returns an nb_status; nothing throws across the ABI.  After
+ *     a failure nb_last_error() describes it.  A failure is sticky: every
+ *     later call on the context returns the same status until
+ *     nb_set_particles() or nb_set_state() reloads the system.
+ *   - Host arrays are read or written during the call and never kept.
+ *     Device arrays (on_device = 1) must be device memory of the context's
+ *     device; the call is then stream-ordered on the context stream and may
+ *     return before the GPU finishes (nb_synchronize() waits).
+ *   - Vectors are n x 3 row-major doubles: component c of particle i is
+ *     element 3*i + c.  Particle indices are int32 in [0, n).
+ *   - A context is not thread-safe; different contexts are independent.
+ *   - Units are whatever the caller uses; G is part of the configuration.
+ */
+#ifndef NBODY_H
+#define NBODY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nb_ctx nb_ctx; /* opaque; owns all device memory it allocates */
+
+typedef enum nb_status {
+    NB_OK = 0,
+    NB_EINVAL = 1,     /* bad argument (size, pointer, value out of range)   */
+    NB_ECUDA = 2,      /* a CUDA runtime call failed                          */
+    NB_ENOMEM = 3,     /* device or pinned host allocation failed             */
+    NB_ENONFINITE = 4, /* a force, jerk or timestep came out NaN or infinite  */
+    NB_EDTMIN = 5,     /* a timestep fell below dt_min                        */
+    NB_ETIMEOUT = 6,   /* a bounded device-side wait gave up                  */
+    NB_ESTATE = 7      /* call out of order (no particles, mismatched block)  */
+} nb_status;
+
+/* Precision of the force evaluation (Sec. 3.2 "Arithmetic precision").
+ *   NB_FP64  every operation in double precision (the baseline path).
+ *   NB_MIXED the paper's mixed scheme on FP32 pipes: r_ij from double-single
+ *            positions, the pair arithmetic in FP32 with a hardware rsqrt,
+ *            FP32 partial sums per j tile folded into compensated
+ *            (double-single) accumulators.  Fastest; per-particle relative
+ *            errors follow the FP32 rounding of each pair.
+ *   NB_DS    the same pair formulas in double-single (float-float)
+ *            arithmetic built from error-free FP32 transforms. */
+typedef enum nb_precision { NB_FP64 = 0, NB_MIXED = 1, NB_DS = 2 } nb_precision;
+
+typedef struct nb_config {
+    int32_t precision;    /* nb_precision                                       */
+    int32_t device;       /* CUDA device ordinal                                */
+    double G;             /* gravitational constant (Eq. eom)                   */
+    double eta_start;     /* first step: dt = eta_start |a|/|j|                 */
+    double dt_max;        /* largest timestep; must be a power of two           */
+    double dt_min;        /* smallest timestep allowed (NB_EDTMIN below it)     */
+    void* stream;         /* cudaStream_t to run on; NULL = a private stream    */
+    int32_t i_per_thread; /* force kernel register blocking; 0 = default        */
+    int32_t ctas_per_sm;  /* persistent force CTAs per SM; 0 = from occupancy   */
+} nb_config;
+
+/* Fill *cfg with the defaults: NB_MIXED, device 0, G = 1, eta_start = 0.01,
+ * dt_max = 1/16, dt_min = 2^-40, private stream, automatic launch shape. */
+void nb_config_init(nb_config* cfg);
+
+/* Create a context on cfg->device.  *out receives the handle.
+ * Errors: NB_EINVAL (NULL pointer, dt_max not a power of two, unknown
+ * precision), NB_ECUDA (no such device). */
+nb_status nb_create(const nb_config* cfg, nb_ctx** out);
+
+/* Release every resource of the context (NULL is accepted). */
+nb_status nb_destroy(nb_ctx* ctx);
+
+/* Load a system (Sec. 2 set-up): masses m[n], positions r[n][3] and
+ * velocities v[n][3] (host arrays, copied), softening eps (Eq. eom) and the
+ * Aarseth accuracy parameter eta (Eq. timestep).  Sets t_i = 0, evaluates
+ * a, j on every particle (Eqs. acc, jrk) and the first timesteps
+ * dt_i = pow2_floor(min(eta_start |a_i|/|j_i|, dt_max)).  Blocks until done.
+ * Errors: NB_EINVAL (n < 1, n > 2^31 - 1, eps < 0, eta <= 0, NULL array),
+ * NB_ENOMEM, NB_ENONFINITE (e.g. eps = 0 with two particles at one point). */
+nb_status nb_set_particles(nb_ctx* ctx, int64_t n, const double* m, const double* r,
+                           const double* v, double eps, double eta);
+
+/* Load a full Hermite state: m[n], r, v, a, j [n][3], t[n], dt[n] (the
+ * checkpoint/resume entry point).  Arrays are host memory, or device memory
+ * when on_device = 1.  Every dt_i must be a power of two <= dt_max and t_i a
+ * multiple of dt_i; this is the caller's responsibility.
+ * Errors: NB_EINVAL, NB_ENOMEM. */
+nb_status nb_set_state(nb_ctx* ctx, int64_t n, const double* m, const double* r,
+                       const double* v, const double* a, const double* j,
+                       const double* t, const double* dt, double eps, double eta,
+                       int32_t on_device);
+
+/* Copy the state out (any pointer may be NULL to skip that array).  Host
+ * arrays block until written; device arrays are stream-ordered. */
+nb_status nb_get_state(nb_ctx* ctx, double* r, double* v, double* a, double* j,
+                       double* t, double* dt, int32_t on_device);
+
+/* Steps 2-3 (Eqs. xpred, vpred): predict every particle to time t into the
+ * layout the force kernel streams.  Asynchronous. */
+nb_status nb_predict(nb_ctx* ctx, double t);
+
+/* Step 1: t_next = min_i (t_i + dt_i) and the active block, every i with
+ * t_i + dt_i == t_next, in ascending index order.  If t_next > t_end the
+ * block is empty.  *t_next and *n_act are written (host); idx (host, may be
+ * NULL, capacity n) receives the block.  Blocks until done. */
+nb_status nb_select(nb_ctx* ctx, double t_end, double* t_next, int32_t* n_act,
+                    int32_t* idx);
+
+/* Step 4 (Eqs. acc, jrk, pot): acceleration acc[n_act][3], jerk
+ * jerk[n_act][3] and potential pot[n_act] of the particles idx[0..n_act)
+ * from every particle j != i at the last predicted time (nb_predict).  Any
+ * output pointer may be NULL.  With on_device = 0, idx and the outputs are
+ * host arrays and the call blocks; with on_device = 1 they are device arrays
+ * and the call is stream-ordered.  The results are also kept for
+ * nb_correct.  Errors: NB_EINVAL (n_act < 0 or > n, bad index), NB_ESTATE
+ * (no particles loaded). */
+nb_status nb_force(nb_ctx* ctx, int32_t n_act, const int32_t* idx, double* acc,
+                   double* jerk, double* pot, int32_t on_device);
+
+/* Steps 5-8 for the block idx[0..n_act) whose particles are all due at time
+ * t (t_i + dt_i == t): Hermite interpolation (snap, crackle), corrector,
+ * a0 <- a1, j0 <- j1, t_i <- t, new power-of-two timestep from Eq. timestep.
+ * acc/jerk are the new a1, j1 ([n_act][3], host or device per on_device);
+ * NULL for both uses the last nb_force results (same n_act required).
+ * Blocks when on_device = 0.  Errors: NB_EINVAL, NB_ESTATE, NB_ENONFINITE,
+ * NB_EDTMIN (reported after the work completes). */
+nb_status nb_correct(nb_ctx* ctx, double t, int32_t n_act, const int32_t* idx,
+                     const double* acc, const double* jerk, int32_t on_device);
+
+/* One block step (steps 1-8) entirely on the device, no host round trip:
+ * select, predict, force, correct.  Does nothing once t_next > t_end.
+ * Asynchronous; device errors surface at the next blocking call. */
+nb_status nb_block_step(nb_ctx* ctx, double t_end);
+
+/* Integrate (steps 1-9 of Sec. 2) until every particle reaches t_end; with
+ * t_end a multiple of dt_max all particles end synchronised at t_end.
+ * *n_steps / *n_interactions (may be NULL) receive the block steps and the
+ * interactions (n_act * n per block, self pair counted) of this call.
+ * Blocks.  Errors: NB_ENONFINITE, NB_EDTMIN, NB_ETIMEOUT. */
+nb_status nb_step_until(nb_ctx* ctx, double t_end, uint64_t* n_steps,
+                        uint64_t* n_interactions);
+
+/* Energy diagnostic at a synchronised time: kinetic sum 1/2 m v^2 and
+ * potential 1/2 sum m_i phi_i (Eq. pot).  With fp64_potential = 1 the
+ * potential is summed in FP64 whatever the context precision.  Blocks. */
+nb_status nb_energy(nb_ctx* ctx, int32_t fp64_potential, double* kin, double* pot);
+
+/* Wait for all work queued on the context stream and report device errors. */
+nb_status nb_synchronize(nb_ctx* ctx);
+
+/* Number of particles loaded (0 before nb_set_particles). */
+int64_t nb_num_particles(const nb_ctx* ctx);
+
+/* Description of the last failure on ctx ("" if none); valid until the
+ * next call on ctx. */
+const char* nb_last_error(const nb_ctx* ctx);
+
+/* Static name of a status code. */
+const char* nb_status_string(nb_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NBODY_H */

@@ -1,0 +1,689 @@
+// C ABI of libnbody (declared in include/nbody.h): context lifetime, device
+// buffers and the host-side sequencing of the Hermite block-timestep steps
+// of Sec. 2.  All arithmetic of the method runs in the kernels of force.cu
+// and hermite.cu; this file only moves data and launches them.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "nb_device.cuh"
+#include "nb_launch.h"
+#include "nbody.h"
+
+using nb::Prec;
+
+struct nb_ctx {
+    nb_config cfg{};
+    Prec prec = Prec::MIXED;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 0;
+    int it = 1;          // i particles per thread in the context precision
+    int grid = 0;        // persistent force CTAs, context precision
+    int grid64 = 0;      // the same for the FP64 energy pass
+    int64_t n = 0, n_pad = 0, cap = 0;
+    double eps = 0.0, eta = 0.02;
+    nb::StateDev st;
+    nb::JLayout jl;      // context precision
+    nb::JLayout jl64;    // FP64 layout for the FP64 potential (non-FP64 contexts)
+    nb::SchedDev sd;
+    int32_t* idx_user = nullptr;
+    int32_t* n_act_user = nullptr;
+    double* acc1 = nullptr;
+    double* jerk1 = nullptr;
+    double* pot1 = nullptr;
+    double* scratch = nullptr;
+    uint32_t* counters = nullptr;
+    int64_t counter_stride = 0;
+    int64_t counter_words = 0;
+    uint32_t* status_dev = nullptr;
+    unsigned long long* ctr64 = nullptr;  // [0] block steps, [1] interactions
+    double* energy_partials = nullptr;
+    double* energy_out = nullptr;
+    uint32_t* energy_ticket = nullptr;
+    double* staging = nullptr;  // 3n doubles
+    unsigned char* pinned = nullptr;
+    int energy_blocks = 0;
+    int32_t last_force_n_act = -1;
+    bool loaded = false;
+    nb_status sticky = NB_OK;
+    std::string err;
+    // CUDA graph of GRAPH_STEPS device-resident block steps for one t_end.
+    cudaGraphExec_t step_graph = nullptr;
+    double graph_t_end = 0.0;
+};
+
+namespace {
+
+constexpr size_t PINNED_BYTES = 256;
+constexpr int GRAPH_STEPS = 16;  // block steps per replay of the step graph
+
+void drop_graph(nb_ctx* c)
+{
+    if (c->step_graph) cudaGraphExecDestroy(c->step_graph);
+    c->step_graph = nullptr;
+}
+
+nb_status fail(nb_ctx* c, nb_status s, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
+nb_status fail(nb_ctx* c, nb_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) {
+        c->err = buf;
+        if (s != NB_EINVAL) c->sticky = s;
+    }
+    return s;
+}
+
+#define NB_CK(ctx, call)                                                                 \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail((ctx), e_ == cudaErrorMemoryAllocation ? NB_ENOMEM : NB_ECUDA,   \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                        __LINE__);                                                       \
+    } while (0)
+
+bool is_pow2(double x)
+{
+    if (!(x > 0.0) || !std::isfinite(x)) return false;
+    int e;
+    return std::frexp(x, &e) == 0.5;
+}
+
+template <class T>
+void dfree(T*& p)
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+void free_buffers(nb_ctx* c)
+{
+    dfree(c->st.m), dfree(c->st.x), dfree(c->st.v), dfree(c->st.a), dfree(c->st.j);
+    dfree(c->st.t), dfree(c->st.dt);
+    for (int k = 0; k < 4; ++k) {
+        if (c->jl.arr[k]) cudaFree(c->jl.arr[k]);
+        if (c->jl64.arr[k]) cudaFree(c->jl64.arr[k]);
+        c->jl.arr[k] = c->jl64.arr[k] = nullptr;
+    }
+    dfree(c->sd.tmin_bits), dfree(c->sd.idx), dfree(c->sd.n_act);
+    dfree(c->sd.block_counts), dfree(c->sd.block_offsets), dfree(c->sd.ticket);
+    dfree(c->idx_user), dfree(c->n_act_user), dfree(c->acc1), dfree(c->jerk1), dfree(c->pot1);
+    dfree(c->scratch), dfree(c->counters), dfree(c->staging);
+    dfree(c->energy_partials), dfree(c->energy_out), dfree(c->energy_ticket);
+    c->cap = 0;
+}
+
+nb_status alloc_layout(nb_ctx* c, Prec p, nb::JLayout& jl, int64_t n_pad)
+{
+    for (int k = 0; k < nb::jlayout_narr(p); ++k)
+        NB_CK(c, cudaMalloc(&jl.arr[k], (size_t)n_pad * nb::jlayout_elem_bytes(p, k)));
+    return NB_OK;
+}
+
+// Size every n-dependent buffer for n particles.
+nb_status ensure_capacity(nb_ctx* c, int64_t n)
+{
+    const int64_t n_pad = (n + nb::TJ - 1) / nb::TJ * nb::TJ;
+    if (n <= c->cap) {
+        c->n = n;
+        c->n_pad = n_pad;
+        c->st.n = n;
+        c->st.n_pad = n_pad;
+        return NB_OK;
+    }
+    free_buffers(c);
+    const size_t d = sizeof(double);
+    NB_CK(c, cudaMalloc(&c->st.m, n * d));
+    NB_CK(c, cudaMalloc(&c->st.x, 3 * n * d));
+    NB_CK(c, cudaMalloc(&c->st.v, 3 * n * d));
+    NB_CK(c, cudaMalloc(&c->st.a, 3 * n * d));
+    NB_CK(c, cudaMalloc(&c->st.j, 3 * n * d));
+    NB_CK(c, cudaMalloc(&c->st.t, n * d));
+    NB_CK(c, cudaMalloc(&c->st.dt, n * d));
+    nb_status s = alloc_layout(c, c->prec, c->jl, n_pad);
+    if (s != NB_OK) return s;
+    if (c->prec != Prec::FP64) {
+        s = alloc_layout(c, Prec::FP64, c->jl64, n_pad);
+        if (s != NB_OK) return s;
+    }
+    c->sd.max_blocks = static_cast<int>((n + nb::SCHED_CHUNK - 1) / nb::SCHED_CHUNK);
+    NB_CK(c, cudaMalloc(&c->sd.tmin_bits, sizeof(unsigned long long)));
+    NB_CK(c, cudaMalloc(&c->sd.idx, n * sizeof(int32_t)));
+    NB_CK(c, cudaMalloc(&c->sd.n_act, sizeof(int32_t)));
+    NB_CK(c, cudaMalloc(&c->sd.block_counts, c->sd.max_blocks * sizeof(int32_t)));
+    NB_CK(c, cudaMalloc(&c->sd.block_offsets, c->sd.max_blocks * sizeof(int32_t)));
+    NB_CK(c, cudaMalloc(&c->sd.ticket, sizeof(uint32_t)));
+    NB_CK(c, cudaMemset(c->sd.ticket, 0, sizeof(uint32_t)));
+    NB_CK(c, cudaMemset(c->sd.n_act, 0, sizeof(int32_t)));
+    NB_CK(c, cudaMalloc(&c->idx_user, n * sizeof(int32_t)));
+    NB_CK(c, cudaMalloc(&c->n_act_user, sizeof(int32_t)));
+    NB_CK(c, cudaMalloc(&c->acc1, 3 * n * d));
+    NB_CK(c, cudaMalloc(&c->jerk1, 3 * n * d));
+    NB_CK(c, cudaMalloc(&c->pot1, n * d));
+    NB_CK(c, cudaMalloc(&c->staging, 3 * n * d));
+    // Scratch for the split-group partials of both force precisions.
+    const size_t s1 = nb::force_scratch_doubles(c->it, n, c->grid * nb::FORCE_WARPS);
+    const size_t s2 = nb::force_scratch_doubles(1, n, c->grid64 * nb::FORCE_WARPS);
+    NB_CK(c, cudaMalloc(&c->scratch, (s1 > s2 ? s1 : s2) * d));
+    const int max_warps = nb::FORCE_WARPS * std::max(c->grid, c->grid64);
+    c->counter_stride = nb::force_counter_stride(n, max_warps);
+    c->counter_words = nb::force_counter_entries(n, max_warps);
+    NB_CK(c, cudaMalloc(&c->counters, c->counter_words * sizeof(uint32_t)));
+    NB_CK(c, cudaMemset(c->counters, 0, c->counter_words * sizeof(uint32_t)));
+    c->energy_blocks = static_cast<int>(std::min<int64_t>((n + 255) / 256, 1024));
+    NB_CK(c, cudaMalloc(&c->energy_partials, 2 * c->energy_blocks * d));
+    NB_CK(c, cudaMalloc(&c->energy_out, 2 * d));
+    NB_CK(c, cudaMalloc(&c->energy_ticket, sizeof(uint32_t)));
+    NB_CK(c, cudaMemset(c->energy_ticket, 0, sizeof(uint32_t)));
+    c->cap = n;
+    c->n = n;
+    c->n_pad = n_pad;
+    c->st.n = n;
+    c->st.n_pad = n_pad;
+    return NB_OK;
+}
+
+nb_status enter(nb_ctx* c, bool need_particles)
+{
+    if (!c) return NB_EINVAL;
+    c->err.clear();
+    if (c->sticky != NB_OK) return fail(c, c->sticky, "context is in error state %d", c->sticky);
+    if (need_particles && !c->loaded) return fail(c, NB_ESTATE, "no particles loaded");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return fail(c, NB_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    return NB_OK;
+}
+
+// Read the device status word (blocking) and turn it into an nb_status.
+nb_status check_status(nb_ctx* c)
+{
+    uint32_t* h = reinterpret_cast<uint32_t*>(c->pinned);
+    NB_CK(c, cudaMemcpyAsync(h, c->status_dev, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                             c->stream));
+    NB_CK(c, cudaStreamSynchronize(c->stream));
+    const uint32_t st = *h;
+    if (st == 0) return NB_OK;
+    // Leave the split-group counters clean for the next launch.
+    cudaMemsetAsync(c->counters, 0, c->counter_words * sizeof(uint32_t), c->stream);
+    cudaMemsetAsync(c->status_dev, 0, sizeof(uint32_t), c->stream);
+    cudaStreamSynchronize(c->stream);
+    if (st & nb::ST_TIMEOUT) return fail(c, NB_ETIMEOUT, "device wait timed out");
+    if (st & nb::ST_NONFINITE) return fail(c, NB_ENONFINITE, "non-finite force, jerk or timestep");
+    if (st & nb::ST_DTMIN) return fail(c, NB_EDTMIN, "timestep below dt_min");
+    if (st & nb::ST_BADINDEX) return fail(c, NB_EINVAL, "particle index out of range");
+    if (st & nb::ST_NOTDUE) return fail(c, NB_ESTATE, "particle not due at the block time");
+    return fail(c, NB_ECUDA, "unknown device status 0x%x", st);
+}
+
+nb_status run_force(nb_ctx* c, Prec p, const nb::JLayout& jl, const int32_t* idx,
+                    const int32_t* n_act_dev)
+{
+    nb::ForceArgs f;
+    f.prec = p;
+    f.it = p == c->prec ? c->it : 1;
+    f.jl = jl;
+    f.n = c->n;
+    f.n_pad = c->n_pad;
+    f.idx = idx;
+    f.n_act_dev = n_act_dev;
+    f.acc = c->acc1;
+    f.jerk = c->jerk1;
+    f.pot = c->pot1;
+    f.scratch = c->scratch;
+    f.counters = c->counters;
+    f.counter_stride = c->counter_stride;
+    f.status = c->status_dev;
+    f.eps2 = c->eps * c->eps;
+    f.grid = p == c->prec ? c->grid : c->grid64;
+    NB_CK(c, nb::force_launch(f, c->stream));
+    return NB_OK;
+}
+
+nb_status upload_vec3(nb_ctx* c, const double* src, double* dst_soa, int on_device)
+{
+    NB_CK(c, cudaMemcpyAsync(c->staging, src, 3 * c->n * sizeof(double),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                             c->stream));
+    NB_CK(c, nb::aos_to_soa_launch(c->staging, dst_soa, c->n, c->stream));
+    return NB_OK;
+}
+
+nb_status download_vec3(nb_ctx* c, const double* src_soa, double* dst, int on_device)
+{
+    NB_CK(c, nb::soa_to_aos_launch(src_soa, c->staging, c->n, c->stream));
+    NB_CK(c, cudaMemcpyAsync(dst, c->staging, 3 * c->n * sizeof(double),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                             c->stream));
+    return NB_OK;
+}
+
+nb_status validate_idx(nb_ctx* c, int32_t n_act, const int32_t* idx)
+{
+    for (int32_t k = 0; k < n_act; ++k)
+        if (idx[k] < 0 || idx[k] >= c->n)
+            return fail(c, NB_EINVAL, "idx[%d] = %d outside [0, %lld)", k, idx[k],
+                        static_cast<long long>(c->n));
+    return NB_OK;
+}
+
+nb_status block_step(nb_ctx* c, double t_end)
+{
+    NB_CK(c, nb::select_launch(c->st, c->sd, t_end, c->stream));
+    NB_CK(c, nb::predict_launch(c->st, c->prec, c->jl, c->cfg.G, c->sd.tmin_bits, 0.0,
+                                c->sd.n_act, c->stream));
+    nb_status s = run_force(c, c->prec, c->jl, c->sd.idx, c->sd.n_act);
+    if (s != NB_OK) return s;
+    nb::CorrectArgs ca;
+    ca.idx = c->sd.idx;
+    ca.n_act_dev = c->sd.n_act;
+    ca.t_bits = c->sd.tmin_bits;
+    ca.acc1 = c->acc1;
+    ca.jerk1 = c->jerk1;
+    ca.eta = c->eta;
+    ca.dt_max = c->cfg.dt_max;
+    ca.dt_min = c->cfg.dt_min;
+    ca.status = c->status_dev;
+    ca.step_counter = c->ctr64;
+    ca.inter_counter = c->ctr64 + 1;
+    NB_CK(c, nb::correct_launch(c->st, ca, c->stream));
+    c->last_force_n_act = -1;
+    return NB_OK;
+}
+
+// Capture GRAPH_STEPS block steps for t_end into c->step_graph.  Every node
+// reads its block (t_next, n_act, idx) from device memory, so one graph
+// serves every replay until t_end changes or the buffers are reallocated.
+nb_status build_step_graph(nb_ctx* c, double t_end)
+{
+    drop_graph(c);
+    NB_CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    nb_status s = NB_OK;
+    for (int k = 0; k < GRAPH_STEPS && s == NB_OK; ++k) s = block_step(c, t_end);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (s != NB_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    if (e != cudaSuccess) return fail(c, NB_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    const cudaError_t ei = cudaGraphInstantiate(&c->step_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+        c->step_graph = nullptr;
+        return fail(c, NB_ECUDA, "graph instantiate: %s", cudaGetErrorString(ei));
+    }
+    c->graph_t_end = t_end;
+    return NB_OK;
+}
+
+// Set-up shared by nb_set_particles / nb_set_state.
+nb_status begin_load(nb_ctx* c, int64_t n, double eps, double eta)
+{
+    if (n < 1 || n > 0x7fffffffLL) return fail(c, NB_EINVAL, "n = %lld out of range", (long long)n);
+    if (!(eps >= 0.0) || !std::isfinite(eps)) return fail(c, NB_EINVAL, "eps must be >= 0");
+    if (!(eta > 0.0) || !std::isfinite(eta)) return fail(c, NB_EINVAL, "eta must be > 0");
+    c->sticky = NB_OK;
+    c->loaded = false;
+    c->err.clear();
+    drop_graph(c);
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return fail(c, NB_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    nb_status s = ensure_capacity(c, n);
+    if (s != NB_OK) return s;
+    c->eps = eps;
+    c->eta = eta;
+    NB_CK(c, cudaMemsetAsync(c->status_dev, 0, sizeof(uint32_t), c->stream));
+    NB_CK(c, cudaMemsetAsync(c->counters, 0, c->counter_words * sizeof(uint32_t), c->stream));
+    c->last_force_n_act = -1;
+    return NB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void nb_config_init(nb_config* cfg)
+{
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->precision = NB_MIXED;
+    cfg->device = 0;
+    cfg->G = 1.0;
+    cfg->eta_start = 0.01;
+    cfg->dt_max = 1.0 / 16.0;
+    cfg->dt_min = std::ldexp(1.0, -40);
+    cfg->stream = nullptr;
+    cfg->i_per_thread = 0;
+    cfg->ctas_per_sm = 0;
+}
+
+nb_status nb_create(const nb_config* cfg, nb_ctx** out)
+{
+    if (!cfg || !out) return NB_EINVAL;
+    *out = nullptr;
+    if (cfg->precision < NB_FP64 || cfg->precision > NB_DS) return NB_EINVAL;
+    if (!is_pow2(cfg->dt_max) || !(cfg->dt_min > 0.0) || cfg->dt_min > cfg->dt_max) return NB_EINVAL;
+    if (!(cfg->eta_start > 0.0) || !std::isfinite(cfg->G)) return NB_EINVAL;
+    nb_ctx* c = new (std::nothrow) nb_ctx;
+    if (!c) return NB_ENOMEM;
+    c->cfg = *cfg;
+    c->prec = static_cast<Prec>(cfg->precision);
+    c->device = cfg->device;
+    auto bail = [&](nb_status s) {
+        nb_destroy(c);
+        return s;
+    };
+    if (cudaSetDevice(c->device) != cudaSuccess) return bail(NB_ECUDA);
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
+        return bail(NB_ECUDA);
+    if (cfg->stream) {
+        c->stream = static_cast<cudaStream_t>(cfg->stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(NB_ECUDA);
+        c->own_stream = true;
+    }
+    int it = cfg->i_per_thread;
+    if (it == 0) it = c->prec == Prec::MIXED ? 2 : 1;
+    if (!nb::force_variant_exists(c->prec, it)) return bail(NB_EINVAL);
+    c->it = it;
+    if (nb::force_setup(c->prec, it) != cudaSuccess) return bail(NB_ECUDA);
+    if (nb::force_setup(Prec::FP64, 1) != cudaSuccess) return bail(NB_ECUDA);
+    int per_sm = cfg->ctas_per_sm > 0 ? cfg->ctas_per_sm : nb::force_ctas_per_sm(c->prec, it);
+    if (per_sm < 1) return bail(NB_ECUDA);
+    c->grid = per_sm * c->num_sms;
+    const int per_sm64 = nb::force_ctas_per_sm(Prec::FP64, 1);
+    if (per_sm64 < 1) return bail(NB_ECUDA);
+    c->grid64 = per_sm64 * c->num_sms;
+    if (cudaMalloc(&c->status_dev, sizeof(uint32_t)) != cudaSuccess) return bail(NB_ENOMEM);
+    if (cudaMemset(c->status_dev, 0, sizeof(uint32_t)) != cudaSuccess) return bail(NB_ECUDA);
+    if (cudaMalloc(&c->ctr64, 2 * sizeof(unsigned long long)) != cudaSuccess) return bail(NB_ENOMEM);
+    if (cudaMemset(c->ctr64, 0, 2 * sizeof(unsigned long long)) != cudaSuccess) return bail(NB_ECUDA);
+    if (cudaMallocHost(&c->pinned, PINNED_BYTES) != cudaSuccess) return bail(NB_ENOMEM);
+    *out = c;
+    return NB_OK;
+}
+
+nb_status nb_destroy(nb_ctx* c)
+{
+    if (!c) return NB_OK;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    drop_graph(c);
+    free_buffers(c);
+    if (c->status_dev) cudaFree(c->status_dev);
+    if (c->ctr64) cudaFree(c->ctr64);
+    if (c->pinned) cudaFreeHost(c->pinned);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return NB_OK;
+}
+
+nb_status nb_set_particles(nb_ctx* c, int64_t n, const double* m, const double* r,
+                           const double* v, double eps, double eta)
+{
+    if (!c) return NB_EINVAL;
+    if (!m || !r || !v) return fail(c, NB_EINVAL, "NULL array");
+    nb_status s = begin_load(c, n, eps, eta);
+    if (s != NB_OK) return s;
+    NB_CK(c, cudaMemcpyAsync(c->st.m, m, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if ((s = upload_vec3(c, r, c->st.x, 0)) != NB_OK) return s;
+    if ((s = upload_vec3(c, v, c->st.v, 0)) != NB_OK) return s;
+    NB_CK(c, cudaMemsetAsync(c->st.a, 0, 3 * n * sizeof(double), c->stream));
+    NB_CK(c, cudaMemsetAsync(c->st.j, 0, 3 * n * sizeof(double), c->stream));
+    NB_CK(c, cudaMemsetAsync(c->st.t, 0, n * sizeof(double), c->stream));
+    // Forces on every particle at t = 0, then the first timesteps.
+    NB_CK(c, nb::predict_launch(c->st, c->prec, c->jl, c->cfg.G, nullptr, 0.0, nullptr, c->stream));
+    NB_CK(c, nb::iota_launch(c->idx_user, n, c->n_act_user, c->stream));
+    if ((s = run_force(c, c->prec, c->jl, c->idx_user, c->n_act_user)) != NB_OK) return s;
+    NB_CK(c, nb::init_dt_launch(c->st, c->acc1, c->jerk1, c->cfg.eta_start, c->cfg.dt_max,
+                                c->cfg.dt_min, 0.0, c->status_dev, c->stream));
+    if ((s = check_status(c)) != NB_OK) return s;
+    c->loaded = true;
+    return NB_OK;
+}
+
+nb_status nb_set_state(nb_ctx* c, int64_t n, const double* m, const double* r, const double* v,
+                       const double* a, const double* j, const double* t, const double* dt,
+                       double eps, double eta, int32_t on_device)
+{
+    if (!c) return NB_EINVAL;
+    if (!m || !r || !v || !a || !j || !t || !dt) return fail(c, NB_EINVAL, "NULL array");
+    nb_status s = begin_load(c, n, eps, eta);
+    if (s != NB_OK) return s;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    NB_CK(c, cudaMemcpyAsync(c->st.m, m, n * sizeof(double), k, c->stream));
+    if ((s = upload_vec3(c, r, c->st.x, on_device)) != NB_OK) return s;
+    if ((s = upload_vec3(c, v, c->st.v, on_device)) != NB_OK) return s;
+    if ((s = upload_vec3(c, a, c->st.a, on_device)) != NB_OK) return s;
+    if ((s = upload_vec3(c, j, c->st.j, on_device)) != NB_OK) return s;
+    NB_CK(c, cudaMemcpyAsync(c->st.t, t, n * sizeof(double), k, c->stream));
+    NB_CK(c, cudaMemcpyAsync(c->st.dt, dt, n * sizeof(double), k, c->stream));
+    if (!on_device) NB_CK(c, cudaStreamSynchronize(c->stream));
+    c->loaded = true;
+    return NB_OK;
+}
+
+nb_status nb_get_state(nb_ctx* c, double* r, double* v, double* a, double* j, double* t,
+                       double* dt, int32_t on_device)
+{
+    nb_status s = enter(c, true);
+    if (s != NB_OK) return s;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    double* src[4] = {c->st.x, c->st.v, c->st.a, c->st.j};
+    double* dst[4] = {r, v, a, j};
+    for (int q = 0; q < 4; ++q) {
+        if (!dst[q]) continue;
+        if ((s = download_vec3(c, src[q], dst[q], on_device)) != NB_OK) return s;
+        if (!on_device) NB_CK(c, cudaStreamSynchronize(c->stream));
+    }
+    if (t) NB_CK(c, cudaMemcpyAsync(t, c->st.t, c->n * sizeof(double), k, c->stream));
+    if (dt) NB_CK(c, cudaMemcpyAsync(dt, c->st.dt, c->n * sizeof(double), k, c->stream));
+    if (!on_device) NB_CK(c, cudaStreamSynchronize(c->stream));
+    return NB_OK;
+}
+
+nb_status nb_predict(nb_ctx* c, double t)
+{
+    nb_status s = enter(c, true);
+    if (s != NB_OK) return s;
+    if (!std::isfinite(t)) return fail(c, NB_EINVAL, "t not finite");
+    NB_CK(c, nb::predict_launch(c->st, c->prec, c->jl, c->cfg.G, nullptr, t, nullptr, c->stream));
+    return NB_OK;
+}
+
+nb_status nb_select(nb_ctx* c, double t_end, double* t_next, int32_t* n_act, int32_t* idx)
+{
+    nb_status s = enter(c, true);
+    if (s != NB_OK) return s;
+    NB_CK(c, nb::select_launch(c->st, c->sd, t_end, c->stream));
+    unsigned long long* hk = reinterpret_cast<unsigned long long*>(c->pinned + 16);
+    int32_t* hn = reinterpret_cast<int32_t*>(c->pinned + 24);
+    NB_CK(c, cudaMemcpyAsync(hk, c->sd.tmin_bits, sizeof(*hk), cudaMemcpyDeviceToHost, c->stream));
+    NB_CK(c, cudaMemcpyAsync(hn, c->sd.n_act, sizeof(*hn), cudaMemcpyDeviceToHost, c->stream));
+    NB_CK(c, cudaStreamSynchronize(c->stream));
+    if (t_next) *t_next = nb::time_from_key(*hk);
+    if (n_act) *n_act = *hn;
+    if (idx && *hn > 0) {
+        NB_CK(c, cudaMemcpyAsync(idx, c->sd.idx, (size_t)*hn * sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, c->stream));
+        NB_CK(c, cudaStreamSynchronize(c->stream));
+    }
+    return NB_OK;
+}
+
+nb_status nb_force(nb_ctx* c, int32_t n_act, const int32_t* idx, double* acc, double* jerk,
+                   double* pot, int32_t on_device)
+{
+    nb_status s = enter(c, true);
+    if (s != NB_OK) return s;
+    if (n_act < 0 || n_act > c->n) return fail(c, NB_EINVAL, "n_act = %d out of range", n_act);
+    if (n_act > 0 && !idx) return fail(c, NB_EINVAL, "NULL idx");
+    if (!on_device && n_act > 0 && (s = validate_idx(c, n_act, idx)) != NB_OK) return s;
+    const int32_t* idx_dev = idx;
+    if (n_act > 0 && !on_device) {
+        NB_CK(c, cudaMemcpyAsync(c->idx_user, idx, (size_t)n_act * sizeof(int32_t),
+                                 cudaMemcpyHostToDevice, c->stream));
+        idx_dev = c->idx_user;
+    }
+    NB_CK(c, nb::set_scalars_launch(c->n_act_user, n_act, nullptr, 0.0, c->stream));
+    if (n_act > 0 && (s = run_force(c, c->prec, c->jl, idx_dev, c->n_act_user)) != NB_OK) return s;
+    c->last_force_n_act = n_act;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (n_act > 0) {
+        if (acc) NB_CK(c, cudaMemcpyAsync(acc, c->acc1, 3 * (size_t)n_act * sizeof(double), k, c->stream));
+        if (jerk) NB_CK(c, cudaMemcpyAsync(jerk, c->jerk1, 3 * (size_t)n_act * sizeof(double), k, c->stream));
+        if (pot) NB_CK(c, cudaMemcpyAsync(pot, c->pot1, (size_t)n_act * sizeof(double), k, c->stream));
+    }
+    if (!on_device) return check_status(c);
+    return NB_OK;
+}
+
+nb_status nb_correct(nb_ctx* c, double t, int32_t n_act, const int32_t* idx, const double* acc,
+                     const double* jerk, int32_t on_device)
+{
+    nb_status s = enter(c, true);
+    if (s != NB_OK) return s;
+    if (n_act < 0 || n_act > c->n) return fail(c, NB_EINVAL, "n_act = %d out of range", n_act);
+    if (!std::isfinite(t)) return fail(c, NB_EINVAL, "t not finite");
+    if (n_act > 0 && !idx) return fail(c, NB_EINVAL, "NULL idx");
+    if ((acc == nullptr) != (jerk == nullptr)) return fail(c, NB_EINVAL, "give both acc and jerk or neither");
+    if (!acc && n_act != c->last_force_n_act)
+        return fail(c, NB_ESTATE, "no nb_force result for a block of %d particles", n_act);
+    if (n_act == 0) return NB_OK;
+    if (!on_device && (s = validate_idx(c, n_act, idx)) != NB_OK) return s;
+    const int32_t* idx_dev = idx;
+    const double* a1 = acc ? acc : c->acc1;
+    const double* j1 = jerk ? jerk : c->jerk1;
+    if (!on_device) {
+        NB_CK(c, cudaMemcpyAsync(c->idx_user, idx, (size_t)n_act * sizeof(int32_t),
+                                 cudaMemcpyHostToDevice, c->stream));
+        idx_dev = c->idx_user;
+        if (acc) {
+            NB_CK(c, cudaMemcpyAsync(c->acc1, acc, 3 * (size_t)n_act * sizeof(double),
+                                     cudaMemcpyHostToDevice, c->stream));
+            NB_CK(c, cudaMemcpyAsync(c->jerk1, jerk, 3 * (size_t)n_act * sizeof(double),
+                                     cudaMemcpyHostToDevice, c->stream));
+            a1 = c->acc1;
+            j1 = c->jerk1;
+        }
+    }
+    NB_CK(c, nb::set_scalars_launch(c->n_act_user, n_act, c->sd.tmin_bits, t, c->stream));
+    nb::CorrectArgs ca;
+    ca.idx = idx_dev;
+    ca.n_act_dev = c->n_act_user;
+    ca.t_bits = c->sd.tmin_bits;
+    ca.acc1 = a1;
+    ca.jerk1 = j1;
+    ca.eta = c->eta;
+    ca.dt_max = c->cfg.dt_max;
+    ca.dt_min = c->cfg.dt_min;
+    ca.status = c->status_dev;
+    NB_CK(c, nb::correct_launch(c->st, ca, c->stream));
+    c->last_force_n_act = -1;
+    if (!on_device) return check_status(c);
+    return NB_OK;
+}
+
+nb_status nb_block_step(nb_ctx* c, double t_end)
+{
+    nb_status s = enter(c, true);
+    if (s != NB_OK) return s;
+    return block_step(c, t_end);
+}
+
+nb_status nb_step_until(nb_ctx* c, double t_end, uint64_t* n_steps, uint64_t* n_interactions)
+{
+    nb_status s = enter(c, true);
+    if (s != NB_OK) return s;
+    if (!std::isfinite(t_end)) return fail(c, NB_EINVAL, "t_end not finite");
+    NB_CK(c, cudaMemsetAsync(c->ctr64, 0, 2 * sizeof(unsigned long long), c->stream));
+    if (!c->step_graph || c->graph_t_end != t_end) {
+        if ((s = build_step_graph(c, t_end)) != NB_OK) return s;
+    }
+    int32_t* hn = reinterpret_cast<int32_t*>(c->pinned + 24);
+    uint32_t* hs = reinterpret_cast<uint32_t*>(c->pinned + 28);
+    // Replay GRAPH_STEPS block steps at a time; once t_next passes t_end the
+    // remaining steps of a replay are empty.  One host round trip per replay.
+    for (;;) {
+        NB_CK(c, cudaGraphLaunch(c->step_graph, c->stream));
+        NB_CK(c, cudaMemcpyAsync(hn, c->sd.n_act, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+        NB_CK(c, cudaMemcpyAsync(hs, c->status_dev, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+        NB_CK(c, cudaStreamSynchronize(c->stream));
+        if (*hs != 0) return check_status(c);
+        if (*hn == 0) break;
+    }
+    unsigned long long* hc = reinterpret_cast<unsigned long long*>(c->pinned + 32);
+    NB_CK(c, cudaMemcpyAsync(hc, c->ctr64, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+    NB_CK(c, cudaStreamSynchronize(c->stream));
+    if (n_steps) *n_steps = hc[0];
+    if (n_interactions) *n_interactions = hc[1];
+    return NB_OK;
+}
+
+nb_status nb_energy(nb_ctx* c, int32_t fp64_potential, double* kin, double* pot)
+{
+    nb_status s = enter(c, true);
+    if (s != NB_OK) return s;
+    const bool use64 = fp64_potential || c->prec == Prec::FP64;
+    const Prec p = use64 ? Prec::FP64 : c->prec;
+    nb::JLayout& jl = (p == c->prec) ? c->jl : c->jl64;
+    // Predict every particle to its own time (all t_i are equal at a
+    // synchronised time, so this is the identity there).
+    double* ht = reinterpret_cast<double*>(c->pinned + 48);
+    NB_CK(c, cudaMemcpyAsync(ht, c->st.t, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    NB_CK(c, cudaStreamSynchronize(c->stream));
+    NB_CK(c, nb::predict_launch(c->st, p, jl, c->cfg.G, nullptr, *ht, nullptr, c->stream));
+    NB_CK(c, nb::iota_launch(c->idx_user, c->n, c->n_act_user, c->stream));
+    if ((s = run_force(c, p, jl, c->idx_user, c->n_act_user)) != NB_OK) return s;
+    NB_CK(c, nb::energy_launch(c->st, c->pot1, c->energy_partials, c->energy_blocks,
+                               c->energy_out, c->energy_ticket, c->stream));
+    double* he = reinterpret_cast<double*>(c->pinned + 64);
+    NB_CK(c, cudaMemcpyAsync(he, c->energy_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if ((s = check_status(c)) != NB_OK) return s;
+    if (kin) *kin = he[0];
+    if (pot) *pot = he[1];
+    c->last_force_n_act = -1;
+    return NB_OK;
+}
+
+nb_status nb_synchronize(nb_ctx* c)
+{
+    nb_status s = enter(c, false);
+    if (s != NB_OK) return s;
+    NB_CK(c, cudaStreamSynchronize(c->stream));
+    if (c->loaded) return check_status(c);
+    return NB_OK;
+}
+
+int64_t nb_num_particles(const nb_ctx* c) { return c && c->loaded ? c->n : 0; }
+
+const char* nb_last_error(const nb_ctx* c) { return c ? c->err.c_str() : "NULL context"; }
+
+const char* nb_status_string(nb_status s)
+{
+    switch (s) {
+    case NB_OK: return "NB_OK";
+    case NB_EINVAL: return "NB_EINVAL";
+    case NB_ECUDA: return "NB_ECUDA";
+    case NB_ENOMEM: return "NB_ENOMEM";
+    case NB_ENONFINITE: return "NB_ENONFINITE";
+    case NB_EDTMIN: return "NB_EDTMIN";
+    case NB_ETIMEOUT: return "NB_ETIMEOUT";
+    case NB_ESTATE: return "NB_ESTATE";
+    }
+    return "unknown";
+}
+
+}  // extern "C"

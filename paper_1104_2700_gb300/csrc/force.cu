@@ -1,0 +1,705 @@
+// Step 4 of the Hermite integration procedure (Sec. 2): acceleration, jerk
+// and potential of the active i particles from every predicted j particle,
+// Eqs. acc, jrk and pot, with the self pair excluded by index (Sec. 3.3,
+// force-loop step 3).
+//
+// Work decomposition (GB300-first, not the paper's 2 i x 4 j AVX pairing):
+//   * an i-group is 32*IT consecutive entries of the active list; each lane
+//     of a warp holds IT i particles in registers;
+//   * the j particles stream through shared memory in tiles of TJ, staged by
+//     1-D bulk copies (cp.async.bulk) into a STAGES-deep ring owned by the
+//     warp and completed on mbarriers; every lane reads the same j (a
+//     shared-memory broadcast);
+//   * the flattened (i-group, j-tile) space is cut into equal contiguous
+//     ranges, one per persistent warp ("stream-K"), so every warp does the
+//     same number of tiles whatever n_act is.  A group split across several
+//     warps is summed by the last warp to finish, in warp order, from
+//     partials in global scratch: deterministic, and no warp ever waits on
+//     another.
+#include "nb_device.cuh"
+#include "nb_launch.h"
+
+namespace nb {
+
+struct ForceParams {
+    const void* jl0;
+    const void* jl1;
+    const void* jl2;
+    const void* jl3;
+    int64_t n;
+    int64_t n_pad;
+    const int32_t* idx;
+    const int32_t* n_act_dev;
+    double* acc;
+    double* jerk;
+    double* pot;
+    double* scratch;
+    uint32_t* counters;      // RLEVELS arrays of counter_stride entries
+    int64_t counter_stride;  // >= warps + groups
+    uint32_t* status;
+    double eps2;
+};
+
+// ---------------------------------------------------------------------------
+// Precision policies.  Each provides: the j-layout arrays it stages, the
+// i state it keeps in registers, the per-tile pair loop and the final values.
+// ---------------------------------------------------------------------------
+
+// Plain FP64: the baseline path.
+template <int IT>
+struct PolicyFP64 {
+    static constexpr int NARR = 2;
+    __host__ __device__ static constexpr int elem(int a) { return a < 2 ? 32 : 0; }
+    static constexpr int TILE_BYTES = TJ * 64;
+    static constexpr int STAGES = 3;
+
+    struct I {
+        double x, y, z, vx, vy, vz;
+        int p;
+    };
+    struct Acc {
+        double ax, ay, az, jx, jy, jz, ph;
+        __device__ void zero() { ax = ay = az = jx = jy = jz = ph = 0.0; }
+    };
+
+    __device__ static void load_i(const ForceParams& f, int p, I& s)
+    {
+        s.p = p;
+        if (p < 0) {
+            s.x = s.y = s.z = s.vx = s.vy = s.vz = 0.0;
+            return;
+        }
+        const double2* P = static_cast<const double2*>(f.jl0) + 2 * (int64_t)p;
+        const double2* V = static_cast<const double2*>(f.jl1) + 2 * (int64_t)p;
+        const double2 p0 = __ldg(P), p1 = __ldg(P + 1);
+        const double2 v0 = __ldg(V), v1 = __ldg(V + 1);
+        s.x = p0.x, s.y = p0.y, s.z = p1.x;
+        s.vx = v0.x, s.vy = v0.y, s.vz = v1.x;
+    }
+
+    template <bool MASK>
+    __device__ static void tile(const unsigned char* buf, int64_t j0, const ForceParams& f,
+                                I (&is)[IT], Acc (&ac)[IT])
+    {
+        const double2* sP = reinterpret_cast<const double2*>(buf);
+        const double2* sV = reinterpret_cast<const double2*>(buf + TJ * 32);
+        const double eps2 = f.eps2;
+#pragma unroll 2
+        for (int k = 0; k < TJ; ++k) {
+            const double2 p0 = sP[2 * k], p1 = sP[2 * k + 1];
+            const double2 v0 = sV[2 * k], v1 = sV[2 * k + 1];
+#pragma unroll
+            for (int q = 0; q < IT; ++q) {
+                const double dx = p0.x - is[q].x, dy = p0.y - is[q].y, dz = p1.x - is[q].z;
+                const double dvx = v0.x - is[q].vx, dvy = v0.y - is[q].vy,
+                             dvz = v1.x - is[q].vz;
+                const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
+                double ri = rsqrt(r2);
+                if (MASK) ri = (j0 + k == is[q].p) ? 0.0 : ri;
+                const double mr = p1.y * ri;
+                const double ri2 = ri * ri;
+                const double g = mr * ri2;
+                const double rv = fma(dx, dvx, fma(dy, dvy, dz * dvz));
+                const double t = -3.0 * rv * ri2;
+                ac[q].ax = fma(g, dx, ac[q].ax);
+                ac[q].ay = fma(g, dy, ac[q].ay);
+                ac[q].az = fma(g, dz, ac[q].az);
+                ac[q].jx = fma(g, fma(t, dx, dvx), ac[q].jx);
+                ac[q].jy = fma(g, fma(t, dy, dvy), ac[q].jy);
+                ac[q].jz = fma(g, fma(t, dz, dvz), ac[q].jz);
+                ac[q].ph += mr;
+            }
+        }
+    }
+
+    __device__ static void values(const Acc& a, double (&v)[7])
+    {
+        v[0] = a.ax, v[1] = a.ay, v[2] = a.az;
+        v[3] = a.jx, v[4] = a.jy, v[5] = a.jz;
+        v[6] = -a.ph;
+    }
+};
+
+// Mixed precision (Sec. 3.2): r_ij from double-single positions (the
+// double-single difference stands in for the paper's DP subtraction), the
+// remaining pair arithmetic in FP32 with a hardware rsqrt, FP32 partial
+// sums over each tile folded into double-single accumulators.
+template <int IT>
+struct PolicyMixed {
+    static constexpr int NARR = 3;
+    __host__ __device__ static constexpr int elem(int a) { return a < 2 ? 16 : (a == 2 ? 8 : 0); }
+    static constexpr int TILE_BYTES = TJ * 40;
+    static constexpr int STAGES = 4;
+
+    struct I {
+        float xh, yh, zh, xl, yl, zl, vx, vy, vz;
+        int p;
+    };
+    struct Acc {
+        DSAcc ax, ay, az, jx, jy, jz, ph;
+        __device__ void zero()
+        {
+            ax.zero(), ay.zero(), az.zero(), jx.zero(), jy.zero(), jz.zero(), ph.zero();
+        }
+    };
+
+    __device__ static void load_i(const ForceParams& f, int p, I& s)
+    {
+        s.p = p;
+        if (p < 0) {
+            s.xh = s.yh = s.zh = s.xl = s.yl = s.zl = s.vx = s.vy = s.vz = 0.f;
+            return;
+        }
+        const float4 A = __ldg(static_cast<const float4*>(f.jl0) + p);
+        const float4 B = __ldg(static_cast<const float4*>(f.jl1) + p);
+        const float2 C = __ldg(static_cast<const float2*>(f.jl2) + p);
+        s.xh = A.x, s.yh = A.y, s.zh = A.z;
+        s.xl = B.x, s.yl = B.y, s.zl = B.z;
+        s.vx = B.w, s.vy = C.x, s.vz = C.y;
+    }
+
+    template <bool MASK>
+    __device__ static void tile(const unsigned char* buf, int64_t j0, const ForceParams& f,
+                                I (&is)[IT], Acc (&ac)[IT])
+    {
+        const float4* sA = reinterpret_cast<const float4*>(buf);
+        const float4* sB = reinterpret_cast<const float4*>(buf + TJ * 16);
+        const float2* sC = reinterpret_cast<const float2*>(buf + TJ * 32);
+        const float eps2 = static_cast<float>(f.eps2);
+        float ax[IT], ay[IT], az[IT], jx[IT], jy[IT], jz[IT], ph[IT];
+#pragma unroll
+        for (int q = 0; q < IT; ++q)
+            ax[q] = ay[q] = az[q] = jx[q] = jy[q] = jz[q] = ph[q] = 0.f;
+#pragma unroll 4
+        for (int k = 0; k < TJ; ++k) {
+            const float4 A = sA[k];
+            const float4 B = sB[k];
+            const float2 C = sC[k];
+#pragma unroll
+            for (int q = 0; q < IT; ++q) {
+                const float dx = (A.x - is[q].xh) + (B.x - is[q].xl);
+                const float dy = (A.y - is[q].yh) + (B.y - is[q].yl);
+                const float dz = (A.z - is[q].zh) + (B.z - is[q].zl);
+                const float dvx = B.w - is[q].vx;
+                const float dvy = C.x - is[q].vy;
+                const float dvz = C.y - is[q].vz;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+                float ri = rsqrtf(r2);
+                if (MASK) ri = (j0 + k == is[q].p) ? 0.f : ri;
+                const float mr = A.w * ri;
+                const float ri2 = ri * ri;
+                const float g = mr * ri2;
+                const float rv = fmaf(dx, dvx, fmaf(dy, dvy, dz * dvz));
+                const float t = rv * (-3.f * ri2);
+                ax[q] = fmaf(g, dx, ax[q]);
+                ay[q] = fmaf(g, dy, ay[q]);
+                az[q] = fmaf(g, dz, az[q]);
+                jx[q] = fmaf(g, fmaf(t, dx, dvx), jx[q]);
+                jy[q] = fmaf(g, fmaf(t, dy, dvy), jy[q]);
+                jz[q] = fmaf(g, fmaf(t, dz, dvz), jz[q]);
+                ph[q] += mr;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < IT; ++q) {
+            ac[q].ax.fold(ax[q]), ac[q].ay.fold(ay[q]), ac[q].az.fold(az[q]);
+            ac[q].jx.fold(jx[q]), ac[q].jy.fold(jy[q]), ac[q].jz.fold(jz[q]);
+            ac[q].ph.fold(ph[q]);
+        }
+    }
+
+    __device__ static void values(const Acc& a, double (&v)[7])
+    {
+        v[0] = a.ax.value(), v[1] = a.ay.value(), v[2] = a.az.value();
+        v[3] = a.jx.value(), v[4] = a.jy.value(), v[5] = a.jz.value();
+        v[6] = -a.ph.value();
+    }
+};
+
+// Double-single ("float-float") precision: the pair formulas of Eqs. acc,
+// jrk and pot carried as unevaluated sums hi + lo of two FP32 numbers.  Each
+// product is formed exactly with an FMA (TwoProd) and each sum with TwoSum;
+// the rsqrt estimate is refined through its exact residual 1 - r^2 y^2, and
+// only second-order terms (lo * lo) are dropped.  The result carries about
+// 44 bits, so cancellation among pair terms (near neighbours around a
+// particle with a small net acceleration or jerk) costs no accuracy at the
+// 1e-6 level.
+__device__ __forceinline__ void ds_diff(float jh, float jl, float ih, float il, float& dh,
+                                        float& dl)
+{
+    float s, e;
+    two_sum(jh, -ih, s, e);
+    const float t = __fadd_rn(__fsub_rn(jl, il), e);
+    two_sum(s, t, dh, dl);
+}
+
+// (ah + al) * (bh + bl) to first order: (p, e) with p = fl(ah * bh).
+__device__ __forceinline__ void ds_mul(float ah, float al, float bh, float bl, float& p,
+                                       float& e)
+{
+    two_prod(ah, bh, p, e);
+    e = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, e));
+}
+
+template <int IT>
+struct PolicyDS {
+    static constexpr int NARR = 4;
+    __host__ __device__ static constexpr int elem(int a) { return a < 4 ? 16 : 0; }
+    static constexpr int TILE_BYTES = TJ * 64;
+    static constexpr int STAGES = 2;
+
+    struct I {
+        float xh, yh, zh, xl, yl, zl;
+        float vxh, vyh, vzh, vxl, vyl, vzl;
+        int p;
+    };
+    struct Acc {
+        DSAcc ax, ay, az, jx, jy, jz, ph;
+        __device__ void zero()
+        {
+            ax.zero(), ay.zero(), az.zero(), jx.zero(), jy.zero(), jz.zero(), ph.zero();
+        }
+    };
+
+    __device__ static void load_i(const ForceParams& f, int p, I& s)
+    {
+        s.p = p;
+        if (p < 0) {
+            s.xh = s.yh = s.zh = s.xl = s.yl = s.zl = 0.f;
+            s.vxh = s.vyh = s.vzh = s.vxl = s.vyl = s.vzl = 0.f;
+            return;
+        }
+        const float4 A = __ldg(static_cast<const float4*>(f.jl0) + p);
+        const float4 B = __ldg(static_cast<const float4*>(f.jl1) + p);
+        const float4 C = __ldg(static_cast<const float4*>(f.jl2) + p);
+        const float4 D = __ldg(static_cast<const float4*>(f.jl3) + p);
+        s.xh = A.x, s.yh = A.y, s.zh = A.z;
+        s.xl = B.x, s.yl = B.y, s.zl = B.z;
+        s.vxh = C.x, s.vyh = C.y, s.vzh = C.z;
+        s.vxl = D.x, s.vyl = D.y, s.vzl = D.z;
+    }
+
+    template <bool MASK>
+    __device__ static void tile(const unsigned char* buf, int64_t j0, const ForceParams& f,
+                                I (&is)[IT], Acc (&ac)[IT])
+    {
+        const float4* sA = reinterpret_cast<const float4*>(buf);
+        const float4* sB = reinterpret_cast<const float4*>(buf + TJ * 16);
+        const float4* sC = reinterpret_cast<const float4*>(buf + TJ * 32);
+        const float4* sD = reinterpret_cast<const float4*>(buf + TJ * 48);
+        const float e2h = static_cast<float>(f.eps2);
+        const float e2l = static_cast<float>(f.eps2 - static_cast<double>(e2h));
+#pragma unroll 1
+        for (int k = 0; k < TJ; ++k) {
+            const float4 A = sA[k];
+            const float4 B = sB[k];
+            const float4 C = sC[k];
+            const float4 D = sD[k];
+#pragma unroll
+            for (int q = 0; q < IT; ++q) {
+                const I& s = is[q];
+                float dxh, dxl, dyh, dyl, dzh, dzl;
+                ds_diff(A.x, B.x, s.xh, s.xl, dxh, dxl);
+                ds_diff(A.y, B.y, s.yh, s.yl, dyh, dyl);
+                ds_diff(A.z, B.z, s.zh, s.zl, dzh, dzl);
+                float vxh, vxl, vyh, vyl, vzh, vzl;
+                ds_diff(C.x, D.x, s.vxh, s.vxl, vxh, vxl);
+                ds_diff(C.y, D.y, s.vyh, s.vyl, vyh, vyl);
+                ds_diff(C.z, D.z, s.vzh, s.vzl, vzh, vzl);
+                // r^2 = dx^2 + dy^2 + dz^2 + eps^2 (all terms >= 0)
+                float px, pxe, py, pye, pz, pze;
+                ds_mul(dxh, dxl, dxh, dxl, px, pxe);
+                ds_mul(dyh, dyl, dyh, dyl, py, pye);
+                ds_mul(dzh, dzl, dzh, dzl, pz, pze);
+                float s1, e1, s2, e2, r2h, e3;
+                two_sum(px, py, s1, e1);
+                two_sum(s1, pz, s2, e2);
+                two_sum(s2, e2h, r2h, e3);
+                const float r2l = __fadd_rn(__fadd_rn(__fadd_rn(pxe, pye), __fadd_rn(pze, e1)),
+                                            __fadd_rn(__fadd_rn(e2, e3), e2l));
+                // 1/r: hardware estimate y, refined by the exact residual
+                // h = 1 - r^2 y^2, 1/r = y (1 + h/2 + O(h^2)).
+                float y = rsqrtf(r2h);
+                if (MASK) y = (j0 + k == s.p) ? 0.f : y;
+                float y2, ey2;
+                two_prod(y, y, y2, ey2);
+                float h = __fmaf_rn(-r2h, y2, 1.f);
+                h = __fmaf_rn(-r2h, ey2, h);
+                h = __fmaf_rn(-r2l, y2, h);
+                if (MASK) h = (j0 + k == s.p) ? 0.f : h;
+                const float ril = __fmul_rn(0.5f, __fmul_rn(y, h));
+                // m / r and 1 / r^2, then g = m / r^3
+                float mrh, mrl;
+                ds_mul(A.w, B.w, y, ril, mrh, mrl);
+                const float ri2h = y2;
+                const float ri2l = __fmaf_rn(__fadd_rn(y, y), ril, ey2);
+                float gh, gl;
+                ds_mul(mrh, mrl, ri2h, ri2l, gh, gl);
+                // acceleration terms g * dr
+                float t0, t1;
+                ds_mul(gh, gl, dxh, dxl, t0, t1);
+                ac[q].ax.add(t0, t1);
+                ds_mul(gh, gl, dyh, dyl, t0, t1);
+                ac[q].ay.add(t0, t1);
+                ds_mul(gh, gl, dzh, dzl, t0, t1);
+                ac[q].az.add(t0, t1);
+                ac[q].ph.add(mrh, mrl);
+                // r.v, then tau = -3 (r.v) / r^2
+                float qx, qxe, qy, qye, qz, qze;
+                ds_mul(dxh, dxl, vxh, vxl, qx, qxe);
+                ds_mul(dyh, dyl, vyh, vyl, qy, qye);
+                ds_mul(dzh, dzl, vzh, vzl, qz, qze);
+                float u1, f1, rvh, f2;
+                two_sum(qx, qy, u1, f1);
+                two_sum(u1, qz, rvh, f2);
+                const float rvl = __fadd_rn(__fadd_rn(qxe, qye), __fadd_rn(__fadd_rn(qze, f1), f2));
+                float ch, cl;
+                two_prod(-3.f, ri2h, ch, cl);
+                cl = __fmaf_rn(-3.f, ri2l, cl);
+                float tauh, taul;
+                ds_mul(rvh, rvl, ch, cl, tauh, taul);
+                // jerk terms g * (dv + tau dr)
+                float wh, wl, th_, tl_, we;
+                ds_mul(tauh, taul, dxh, dxl, th_, tl_);
+                two_sum(vxh, th_, wh, we);
+                wl = __fadd_rn(we, __fadd_rn(vxl, tl_));
+                ds_mul(gh, gl, wh, wl, t0, t1);
+                ac[q].jx.add(t0, t1);
+                ds_mul(tauh, taul, dyh, dyl, th_, tl_);
+                two_sum(vyh, th_, wh, we);
+                wl = __fadd_rn(we, __fadd_rn(vyl, tl_));
+                ds_mul(gh, gl, wh, wl, t0, t1);
+                ac[q].jy.add(t0, t1);
+                ds_mul(tauh, taul, dzh, dzl, th_, tl_);
+                two_sum(vzh, th_, wh, we);
+                wl = __fadd_rn(we, __fadd_rn(vzl, tl_));
+                ds_mul(gh, gl, wh, wl, t0, t1);
+                ac[q].jz.add(t0, t1);
+            }
+        }
+    }
+
+    __device__ static void values(const Acc& a, double (&v)[7])
+    {
+        v[0] = a.ax.value(), v[1] = a.ay.value(), v[2] = a.az.value();
+        v[3] = a.jx.value(), v[4] = a.jy.value(), v[5] = a.jz.value();
+        v[6] = -a.ph.value();
+    }
+};
+
+template <class K>
+struct WarpSmem {
+    static constexpr int BAR_BYTES = 128;  // STAGES mbarriers, padded
+    static constexpr int BYTES = BAR_BYTES + K::STAGES * K::TILE_BYTES;
+};
+
+template <class K>
+__device__ __forceinline__ void issue_tile(const ForceParams& f, unsigned char* stage,
+                                           uint64_t* bar, int64_t jtile)
+{
+    mbar_arrive_expect_tx(bar, K::TILE_BYTES);
+    const void* src[4] = {f.jl0, f.jl1, f.jl2, f.jl3};
+    unsigned char* dst = stage;
+#pragma unroll
+    for (int a = 0; a < K::NARR; ++a) {
+        const uint32_t bytes = TJ * K::elem(a);
+        bulk_g2s(dst, static_cast<const unsigned char*>(src[a]) + jtile * (int64_t)bytes,
+                 bytes, bar);
+        dst += bytes;
+    }
+}
+
+// Radix of the deterministic reduction tree over the warps sharing a group.
+constexpr int RB = 16;
+constexpr int RLEVELS = 4;  // RB^RLEVELS >= any warp count
+
+// Warp that owns flattened tile x when T tiles are cut into Pu ranges.
+__device__ __forceinline__ int64_t owner_warp(int64_t x, int64_t T, int64_t Pu)
+{
+    return ((x + 1) * Pu - 1) / T;
+}
+
+template <class K, int IT>
+__global__ void __launch_bounds__(FORCE_WARPS * 32)
+    force_kernel(const ForceParams f)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int64_t w = (int64_t)blockIdx.x * FORCE_WARPS + wib;
+    const int64_t P = (int64_t)gridDim.x * FORCE_WARPS;
+
+    const int n_act = *f.n_act_dev;
+    constexpr int GI = 32 * IT;
+    const int64_t G = (n_act + GI - 1) / GI;
+    const int64_t NT = f.n_pad / TJ;
+    const int64_t T = G * NT;
+    if (T <= 0) return;
+    const int64_t Pu = P < T ? P : T;
+    if (w >= Pu) return;
+    const int64_t t0 = T * w / Pu;
+    const int64_t t1 = T * (w + 1) / Pu;
+
+    unsigned char* wsm = smem + (size_t)wib * WarpSmem<K>::BYTES;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(wsm);
+    unsigned char* ring = wsm + WarpSmem<K>::BAR_BYTES;
+
+    if (lane == 0) {
+#pragma unroll
+        for (int s = 0; s < K::STAGES; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    if (lane == 0) {
+        for (int s = 0; s < K::STAGES && t0 + s < t1; ++s)
+            issue_tile<K>(f, ring + s * K::TILE_BYTES, &bars[s], (t0 + s) % NT);
+    }
+
+    typename K::I is[IT];
+    typename K::Acc ac[IT];
+    int64_t g_cur = -1;
+
+    for (int64_t t = t0; t < t1; ++t) {
+        const int64_t k = t - t0;
+        const int s = static_cast<int>(k % K::STAGES);
+        const uint32_t parity = static_cast<uint32_t>((k / K::STAGES) & 1);
+        const int64_t g = t / NT;
+        const int64_t jt = t - g * NT;
+        if (g != g_cur) {
+            g_cur = g;
+#pragma unroll
+            for (int q = 0; q < IT; ++q) {
+                const int64_t a = g * GI + q * 32 + lane;
+                int p = -1;
+                if (a < n_act) {
+                    p = f.idx[a];
+                    if (p < 0 || p >= f.n) {
+                        atomicOr(f.status, ST_BADINDEX);
+                        p = -1;
+                    }
+                }
+                K::load_i(f, p, is[q]);
+                ac[q].zero();
+            }
+        }
+        const bool ok = mbar_wait_bounded(&bars[s], parity);
+        if (!__all_sync(0xffffffffu, ok)) {
+            if (lane == 0) atomicOr(f.status, ST_TIMEOUT);
+            return;
+        }
+        const int64_t j0 = jt * TJ;
+        bool self_here = false;
+#pragma unroll
+        for (int q = 0; q < IT; ++q)
+            self_here |= (is[q].p >= j0 && is[q].p < j0 + TJ);
+        const unsigned char* buf = ring + s * K::TILE_BYTES;
+        if (__any_sync(0xffffffffu, self_here))
+            K::template tile<true>(buf, j0, f, is, ac);
+        else
+            K::template tile<false>(buf, j0, f, is, ac);
+        __syncwarp();
+        if (lane == 0 && t + K::STAGES < t1) {
+            fence_proxy_async_smem();
+            issue_tile<K>(f, ring + s * K::TILE_BYTES, &bars[s], (t + K::STAGES) % NT);
+        }
+
+        if (jt == NT - 1 || t == t1 - 1) {
+            // This warp's share of group g is complete.  The K warps that
+            // share the group are summed by a radix-RB tree: within each
+            // chunk of RB consecutive contributors the last to arrive adds
+            // the chunk in order and carries the sum one level up.  Level-L
+            // entry r lives in scratch slot key + r * RB^L (the first slot of
+            // the chunk it replaces); each level has its own counters.
+            const int64_t wf = owner_warp(g * NT, T, Pu);
+            const int64_t wl = owner_warp((g + 1) * NT - 1, T, Pu);
+            double v[IT][7];
+#pragma unroll
+            for (int q = 0; q < IT; ++q) K::values(ac[q], v[q]);
+            const int64_t key = wf + g;
+            int64_t kk = wl - wf + 1;  // entries at this level
+            int64_t r = w - wf;        // my entry at this level
+            int64_t stride = 1;
+            bool final_here = true;
+            for (int level = 0; kk > 1; ++level) {
+                double* mine = f.scratch + (size_t)(key + r * stride) * 7 * GI;
+#pragma unroll
+                for (int q = 0; q < IT; ++q)
+#pragma unroll
+                    for (int c = 0; c < 7; ++c) mine[c * GI + q * 32 + lane] = v[q][c];
+                __threadfence();
+                __syncwarp();
+                const int64_t chunk = r / RB;
+                const int64_t first = chunk * RB;
+                const int64_t cs = kk - first < RB ? kk - first : RB;
+                uint32_t* cnt = f.counters + (size_t)level * f.counter_stride + key + chunk;
+                uint32_t prev = 0;
+                if (lane == 0) prev = atomicAdd(cnt, 1u);
+                prev = __shfl_sync(0xffffffffu, prev, 0);
+                if (prev != static_cast<uint32_t>(cs - 1)) {
+                    final_here = false;
+                    break;
+                }
+                __threadfence();
+                if (lane == 0) *cnt = 0u;
+#pragma unroll
+                for (int q = 0; q < IT; ++q)
+#pragma unroll
+                    for (int c = 0; c < 7; ++c) {
+                        double sum = 0.0;
+#pragma unroll 4
+                        for (int64_t u = 0; u < cs; ++u)
+                            sum += __ldcg(f.scratch + (size_t)(key + (first + u) * stride) * 7 * GI +
+                                          c * GI + q * 32 + lane);
+                        v[q][c] = sum;
+                    }
+                r = chunk;
+                kk = (kk + RB - 1) / RB;
+                stride *= RB;
+            }
+            if (final_here) {
+#pragma unroll
+                for (int q = 0; q < IT; ++q) {
+                    const int64_t a = g * GI + q * 32 + lane;
+                    if (a < n_act) {
+                        f.acc[3 * a + 0] = v[q][0];
+                        f.acc[3 * a + 1] = v[q][1];
+                        f.acc[3 * a + 2] = v[q][2];
+                        f.jerk[3 * a + 0] = v[q][3];
+                        f.jerk[3 * a + 1] = v[q][4];
+                        f.jerk[3 * a + 2] = v[q][5];
+                        f.pot[a] = v[q][6];
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+namespace {
+
+template <class K, int IT>
+const void* kfn()
+{
+    return reinterpret_cast<const void*>(&force_kernel<K, IT>);
+}
+
+const void* kernel_ptr(Prec p, int it)
+{
+    switch (p) {
+    case Prec::FP64:
+        if (it == 1) return kfn<PolicyFP64<1>, 1>();
+        if (it == 2) return kfn<PolicyFP64<2>, 2>();
+        return nullptr;
+    case Prec::MIXED:
+        if (it == 1) return kfn<PolicyMixed<1>, 1>();
+        if (it == 2) return kfn<PolicyMixed<2>, 2>();
+        if (it == 4) return kfn<PolicyMixed<4>, 4>();
+        return nullptr;
+    case Prec::DS:
+        if (it == 1) return kfn<PolicyDS<1>, 1>();
+        if (it == 2) return kfn<PolicyDS<2>, 2>();
+        return nullptr;
+    }
+    return nullptr;
+}
+
+}  // namespace
+
+int jlayout_narr(Prec p)
+{
+    switch (p) {
+    case Prec::FP64: return 2;
+    case Prec::MIXED: return 3;
+    case Prec::DS: return 4;
+    }
+    return 0;
+}
+
+int jlayout_elem_bytes(Prec p, int k)
+{
+    switch (p) {
+    case Prec::FP64: return k < 2 ? 32 : 0;
+    case Prec::MIXED: return k < 2 ? 16 : (k == 2 ? 8 : 0);
+    case Prec::DS: return k < 4 ? 16 : 0;
+    }
+    return 0;
+}
+
+size_t force_smem_bytes(Prec p)
+{
+    switch (p) {
+    case Prec::FP64: return (size_t)FORCE_WARPS * WarpSmem<PolicyFP64<1>>::BYTES;
+    case Prec::MIXED: return (size_t)FORCE_WARPS * WarpSmem<PolicyMixed<1>>::BYTES;
+    case Prec::DS: return (size_t)FORCE_WARPS * WarpSmem<PolicyDS<1>>::BYTES;
+    }
+    return 0;
+}
+
+bool force_variant_exists(Prec p, int it) { return kernel_ptr(p, it) != nullptr; }
+
+cudaError_t force_setup(Prec p, int it)
+{
+    const void* fn = kernel_ptr(p, it);
+    if (!fn) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(force_smem_bytes(p)));
+}
+
+int force_ctas_per_sm(Prec p, int it)
+{
+    const void* fn = kernel_ptr(p, it);
+    if (!fn) return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, FORCE_WARPS * 32,
+                                                      force_smem_bytes(p)) != cudaSuccess)
+        return 0;
+    return nb;
+}
+
+size_t force_scratch_doubles(int it, int64_t n_act_max, int warps)
+{
+    const int64_t GI = 32 * it;
+    const int64_t G = (n_act_max + GI - 1) / GI;
+    return (size_t)(warps + G) * 7 * GI;
+}
+
+int64_t force_counter_stride(int64_t n_act_max, int warps)
+{
+    return warps + (n_act_max + 31) / 32;  // groups are at least 32 wide
+}
+
+int64_t force_counter_entries(int64_t n_act_max, int warps)
+{
+    return RLEVELS * force_counter_stride(n_act_max, warps);
+}
+
+cudaError_t force_launch(const ForceArgs& a, cudaStream_t s)
+{
+    const void* fn = kernel_ptr(a.prec, a.it);
+    if (!fn || a.grid <= 0) return cudaErrorInvalidValue;
+    ForceParams f;
+    f.jl0 = a.jl.arr[0];
+    f.jl1 = a.jl.arr[1];
+    f.jl2 = a.jl.arr[2];
+    f.jl3 = a.jl.arr[3];
+    f.n = a.n;
+    f.n_pad = a.n_pad;
+    f.idx = a.idx;
+    f.n_act_dev = a.n_act_dev;
+    f.acc = a.acc;
+    f.jerk = a.jerk;
+    f.pot = a.pot;
+    f.scratch = a.scratch;
+    f.counters = a.counters;
+    f.counter_stride = a.counter_stride;
+    f.status = a.status;
+    f.eps2 = a.eps2;
+    void* args[] = {&f};
+    return cudaLaunchKernel(fn, dim3(a.grid), dim3(FORCE_WARPS * 32), args,
+                            force_smem_bytes(a.prec), s);
+}
+
+}  // namespace nb

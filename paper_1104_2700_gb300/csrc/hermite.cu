@@ -1,0 +1,558 @@
+// O(N) and O(n_act) kernels of the Hermite block-timestep scheme (Sec. 2):
+// step 1 (next block time and the active list), steps 2-3 (predictor, which
+// also writes the j layout the force kernels stream), steps 5-8 (Hermite
+// interpolation, corrector, a0 <- a1, Aarseth timestep in powers of two),
+// the first timesteps and the energy diagnostic.
+#include <cfloat>
+#include <cstring>
+
+#include "nb_device.cuh"
+#include "nb_launch.h"
+
+namespace nb {
+
+// Order-preserving map of doubles to unsigned 64-bit keys (for atomicMin).
+__device__ __forceinline__ unsigned long long dkey(double x)
+{
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double dkey_decode(unsigned long long k)
+{
+    const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+    return __longlong_as_double(static_cast<long long>(b));
+}
+
+// ---------------------------------------------------------------------------
+// Steps 2-3: Taylor predictor (Eqs. xpred, vpred) for every j particle, in
+// Horner form with FMA, written straight into the force kernel's j layout.
+// ---------------------------------------------------------------------------
+template <int PREC>
+__global__ void predict_kernel(const StateDev st, const JLayout jl, const double G,
+                               const unsigned long long* t_bits, const double t_host,
+                               const int32_t* n_act_dev)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= st.n_pad) return;
+    if (n_act_dev && *n_act_dev == 0) return;
+    const int64_t n = st.n;
+    double xp[3], vp[3], gm;
+    if (i < n) {
+        const double t = t_bits ? dkey_decode(*t_bits) : t_host;
+        const double h = t - st.t[i];
+        gm = G * st.m[i];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double x = st.x[c * n + i], v = st.v[c * n + i];
+            const double a = st.a[c * n + i], j = st.j[c * n + i];
+            xp[c] = fma(h, fma(h, fma(h, j * (1.0 / 6.0), a * 0.5), v), x);
+            vp[c] = fma(h, fma(h, j * 0.5, a), v);
+        }
+    } else {
+        xp[0] = xp[1] = xp[2] = GHOST_POS;
+        vp[0] = vp[1] = vp[2] = 0.0;
+        gm = 0.0;
+    }
+    if (PREC == static_cast<int>(Prec::FP64)) {
+        double2* P = static_cast<double2*>(jl.arr[0]) + 2 * i;
+        double2* V = static_cast<double2*>(jl.arr[1]) + 2 * i;
+        P[0] = make_double2(xp[0], xp[1]);
+        P[1] = make_double2(xp[2], gm);
+        V[0] = make_double2(vp[0], vp[1]);
+        V[1] = make_double2(vp[2], 0.0);
+    } else {
+        float hi[3], lo[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            hi[c] = __double2float_rn(xp[c]);
+            lo[c] = __double2float_rn(xp[c] - static_cast<double>(hi[c]));
+        }
+        if (PREC == static_cast<int>(Prec::MIXED)) {
+            static_cast<float4*>(jl.arr[0])[i] =
+                make_float4(hi[0], hi[1], hi[2], __double2float_rn(gm));
+            static_cast<float4*>(jl.arr[1])[i] =
+                make_float4(lo[0], lo[1], lo[2], __double2float_rn(vp[0]));
+            static_cast<float2*>(jl.arr[2])[i] =
+                make_float2(__double2float_rn(vp[1]), __double2float_rn(vp[2]));
+        } else {
+            const float gh = __double2float_rn(gm);
+            const float gl = __double2float_rn(gm - static_cast<double>(gh));
+            float vh[3], vl[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                vh[c] = __double2float_rn(vp[c]);
+                vl[c] = __double2float_rn(vp[c] - static_cast<double>(vh[c]));
+            }
+            static_cast<float4*>(jl.arr[0])[i] = make_float4(hi[0], hi[1], hi[2], gh);
+            static_cast<float4*>(jl.arr[1])[i] = make_float4(lo[0], lo[1], lo[2], gl);
+            static_cast<float4*>(jl.arr[2])[i] = make_float4(vh[0], vh[1], vh[2], 0.f);
+            static_cast<float4*>(jl.arr[3])[i] = make_float4(vl[0], vl[1], vl[2], 0.f);
+        }
+    }
+}
+
+cudaError_t predict_launch(const StateDev& st, Prec p, const JLayout& jl, double G,
+                           const unsigned long long* t_bits, double t_host,
+                           const int32_t* n_act_dev, cudaStream_t s)
+{
+    if (st.n_pad <= 0) return cudaSuccess;
+    const int threads = 256;
+    const unsigned blocks = static_cast<unsigned>((st.n_pad + threads - 1) / threads);
+    switch (p) {
+    case Prec::FP64:
+        predict_kernel<0><<<blocks, threads, 0, s>>>(st, jl, G, t_bits, t_host, n_act_dev);
+        break;
+    case Prec::MIXED:
+        predict_kernel<1><<<blocks, threads, 0, s>>>(st, jl, G, t_bits, t_host, n_act_dev);
+        break;
+    case Prec::DS:
+        predict_kernel<2><<<blocks, threads, 0, s>>>(st, jl, G, t_bits, t_host, n_act_dev);
+        break;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Step 1: next block time t_next = min_i (t_i + dt_i) and the stable
+// (ascending-index) compaction of the block {i : t_i + dt_i == t_next}.
+// Times are dyadic rationals, so the equality test is exact.
+// ---------------------------------------------------------------------------
+__global__ void tmin_kernel(const double* __restrict__ t, const double* __restrict__ dt,
+                            int64_t n, unsigned long long* tmin_bits)
+{
+    unsigned long long best = ~0ull;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long k = dkey(t[i] + dt[i]);
+        best = k < best ? k : best;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+        best = other < best ? other : best;
+    }
+    __shared__ unsigned long long wbest[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) wbest[wid] = best;
+    __syncthreads();
+    if (wid == 0) {
+        best = lane < (int)(blockDim.x >> 5) ? wbest[lane] : ~0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+            best = other < best ? other : best;
+        }
+        if (lane == 0 && best != ~0ull) atomicMin(tmin_bits, best);
+    }
+}
+
+__device__ __forceinline__ bool is_active(const double* t, const double* dt, int64_t i,
+                                          double tn)
+{
+    return t[i] + dt[i] == tn;
+}
+
+// Block-wide exclusive scan of one int per thread (SCHED_THREADS threads).
+__device__ int block_exclusive_scan(int v, int* total)
+{
+    __shared__ int wsum[SCHED_THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int s = lane < SCHED_THREADS / 32 ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < SCHED_THREADS / 32) wsum[lane] = s;
+    }
+    __syncthreads();
+    const int before = wid > 0 ? wsum[wid - 1] : 0;
+    *total = wsum[SCHED_THREADS / 32 - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(SCHED_THREADS)
+    count_kernel(const double* __restrict__ t, const double* __restrict__ dt, int64_t n,
+                 const unsigned long long* tmin_bits, double t_end, SchedDev sd)
+{
+    const double tn = dkey_decode(*tmin_bits);
+    const bool live = tn <= t_end;
+    int c = 0;
+    const int64_t base = (int64_t)blockIdx.x * SCHED_CHUNK + (int64_t)threadIdx.x * SCHED_PER_THREAD;
+    if (live) {
+#pragma unroll
+        for (int e = 0; e < SCHED_PER_THREAD; ++e) {
+            const int64_t i = base + e;
+            if (i < n && is_active(t, dt, i, tn)) ++c;
+        }
+    }
+    int total;
+    block_exclusive_scan(c, &total);
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        sd.block_counts[blockIdx.x] = total;
+        __threadfence();
+        last = atomicAdd(sd.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // The last block scans the per-block counts in block order.
+    const int nb = gridDim.x;
+    int running = 0;
+    for (int b0 = 0; b0 < nb; b0 += SCHED_THREADS) {
+        const int b = b0 + threadIdx.x;
+        const int v = b < nb ? __ldcg(sd.block_counts + b) : 0;
+        int tot;
+        const int ex = block_exclusive_scan(v, &tot);
+        if (b < nb) sd.block_offsets[b] = running + ex;
+        running += tot;
+    }
+    if (threadIdx.x == 0) {
+        *sd.n_act = running;
+        *sd.ticket = 0u;
+    }
+}
+
+__global__ void __launch_bounds__(SCHED_THREADS)
+    scatter_kernel(const double* __restrict__ t, const double* __restrict__ dt, int64_t n,
+                   const unsigned long long* tmin_bits, double t_end, SchedDev sd)
+{
+    const double tn = dkey_decode(*tmin_bits);
+    if (!(tn <= t_end)) return;
+    const int64_t base = (int64_t)blockIdx.x * SCHED_CHUNK + (int64_t)threadIdx.x * SCHED_PER_THREAD;
+    unsigned flags = 0;
+    int c = 0;
+#pragma unroll
+    for (int e = 0; e < SCHED_PER_THREAD; ++e) {
+        const int64_t i = base + e;
+        if (i < n && is_active(t, dt, i, tn)) {
+            flags |= 1u << e;
+            ++c;
+        }
+    }
+    int total;
+    int pos = block_exclusive_scan(c, &total) + sd.block_offsets[blockIdx.x];
+#pragma unroll
+    for (int e = 0; e < SCHED_PER_THREAD; ++e)
+        if (flags & (1u << e)) sd.idx[pos++] = static_cast<int32_t>(base + e);
+}
+
+cudaError_t select_launch(const StateDev& st, const SchedDev& sd, double t_end, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(sd.tmin_bits, 0xff, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    if (st.n <= 0) return cudaMemsetAsync(sd.n_act, 0, sizeof(int32_t), s);
+    const int64_t nb64 = (st.n + SCHED_CHUNK - 1) / SCHED_CHUNK;
+    if (nb64 > sd.max_blocks) return cudaErrorInvalidValue;
+    const int nb = static_cast<int>(nb64);
+    int tb = nb < 1024 ? nb : 1024;
+    tmin_kernel<<<tb, 256, 0, s>>>(st.t, st.dt, st.n, sd.tmin_bits);
+    count_kernel<<<nb, SCHED_THREADS, 0, s>>>(st.t, st.dt, st.n, sd.tmin_bits, t_end, sd);
+    scatter_kernel<<<nb, SCHED_THREADS, 0, s>>>(st.t, st.dt, st.n, sd.tmin_bits, t_end, sd);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Steps 5-8 for each active particle.  The arithmetic is written operation
+// by operation with non-contracted intrinsics in the order of the
+// equations, so that identical inputs give the oracle's bits.
+// ---------------------------------------------------------------------------
+#define DADD __dadd_rn
+#define DSUB __dsub_rn
+#define DMUL __dmul_rn
+#define DDIV __ddiv_rn
+
+__device__ __forceinline__ double norm3_rn(double x, double y, double z)
+{
+    return __dsqrt_rn(DADD(DADD(DMUL(x, x), DMUL(y, y)), DMUL(z, z)));
+}
+
+__device__ __forceinline__ double pow2_floor(double x)
+{
+    int e;
+    frexp(x, &e);
+    return ldexp(1.0, e - 1);
+}
+
+__global__ void correct_kernel(const StateDev st, const CorrectArgs c)
+{
+    const int n_act = *c.n_act_dev;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0 && n_act > 0) {
+        if (c.step_counter) atomicAdd(c.step_counter, 1ull);
+        if (c.inter_counter)
+            atomicAdd(c.inter_counter,
+                      static_cast<unsigned long long>(n_act) * static_cast<unsigned long long>(st.n));
+    }
+    if (k >= n_act) return;
+    const int64_t n = st.n;
+    const int64_t i = c.idx[k];
+    if (i < 0 || i >= n) {
+        atomicOr(c.status, ST_BADINDEX);
+        return;
+    }
+    const double tn = dkey_decode(*c.t_bits);
+    const double h = st.dt[i];
+    if (DADD(st.t[i], h) != tn) {
+        atomicOr(c.status, ST_NOTDUE);
+        return;
+    }
+    const double dtp = DSUB(tn, st.t[i]);
+    const double p2 = DMUL(dtp, dtp), p3 = DMUL(p2, dtp);
+    const double h2 = DMUL(h, h), h3 = DMUL(h2, h), h4 = DMUL(h3, h), h5 = DMUL(h4, h);
+    // h is a power of two, so dividing by h^2 or h^3 (and by 2) is an exact
+    // scaling: multiplying by the exact reciprocal gives the quotient's bits.
+    const double ih2 = DDIV(1.0, h2), ih3 = DDIV(1.0, h3);
+    double a1[3], j1[3], s0[3], c0[3];
+    bool finite = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        a1[d] = c.acc1[3 * k + d];
+        j1[d] = c.jerk1[3 * k + d];
+        finite = finite && isfinite(a1[d]) && isfinite(j1[d]);
+    }
+    if (!finite) {
+        atomicOr(c.status, ST_NONFINITE);
+        return;
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int64_t q = d * n + i;
+        const double x0 = st.x[q], v0 = st.v[q], a0 = st.a[q], j0 = st.j[q];
+        // Eqs. xpred, vpred for the i particle (step 2).
+        const double rp = DADD(DADD(DADD(x0, DMUL(v0, dtp)), DMUL(DMUL(a0, 0.5), p2)),
+                               DMUL(DDIV(j0, 6.0), p3));
+        const double vp = DADD(DADD(v0, DMUL(a0, dtp)), DMUL(DMUL(j0, 0.5), p2));
+        // Step 5: snap and crackle from the Hermite interpolation.
+        const double da = DSUB(a0, a1[d]);
+        s0[d] = DMUL(DMUL(2.0, DSUB(DMUL(-3.0, da), DMUL(DADD(DMUL(2.0, j0), j1[d]), h))), ih2);
+        c0[d] = DMUL(DMUL(6.0, DADD(DMUL(2.0, da), DMUL(DADD(j0, j1[d]), h))), ih3);
+        // Step 6: corrector.
+        const double r1 = DADD(DADD(rp, DDIV(DMUL(s0[d], h4), 24.0)), DDIV(DMUL(c0[d], h5), 120.0));
+        const double v1 = DADD(DADD(vp, DDIV(DMUL(s0[d], h3), 6.0)), DDIV(DMUL(c0[d], h4), 24.0));
+        // Step 7: a0 <- a1, j0 <- j1.
+        st.x[q] = r1;
+        st.v[q] = v1;
+        st.a[q] = a1[d];
+        st.j[q] = j1[d];
+    }
+    st.t[i] = tn;
+    // Step 8: Eq. timestep at the new time (a1, j1, snap carried to t_next,
+    // crackle), then the power-of-two rule of the hierarchical scheme.
+    double sn[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) sn[d] = DADD(s0[d], DMUL(c0[d], h));
+    const double A = norm3_rn(a1[0], a1[1], a1[2]);
+    const double J = norm3_rn(j1[0], j1[1], j1[2]);
+    const double S = norm3_rn(sn[0], sn[1], sn[2]);
+    const double C = norm3_rn(c0[0], c0[1], c0[2]);
+    const double dta = DMUL(c.eta, __dsqrt_rn(DDIV(DADD(DMUL(A, S), DMUL(J, J)),
+                                                   DADD(DMUL(J, C), DMUL(S, S)))));
+    if (isnan(dta)) {
+        atomicOr(c.status, ST_NONFINITE);
+        return;
+    }
+    const double cand = dta < c.dt_max ? dta : c.dt_max;
+    double dt_new = h;
+    if (cand >= DMUL(2.0, h) && fmod(tn, DMUL(2.0, h)) == 0.0) {
+        dt_new = DMUL(2.0, h);
+    } else if (cand >= h) {
+        dt_new = h;
+    } else {
+        while (dt_new > cand && dt_new >= c.dt_min) dt_new = DMUL(dt_new, 0.5);
+    }
+    st.dt[i] = dt_new;
+    if (dt_new < c.dt_min) atomicOr(c.status, ST_DTMIN);
+}
+
+cudaError_t correct_launch(const StateDev& st, const CorrectArgs& c, cudaStream_t s)
+{
+    if (st.n <= 0) return cudaSuccess;
+    const int threads = 128;
+    const unsigned blocks = static_cast<unsigned>((st.n + threads - 1) / threads);
+    correct_kernel<<<blocks, threads, 0, s>>>(st, c);
+    return cudaGetLastError();
+}
+
+// Reading R3 of the oracle: dt = pow2_floor(min(eta_start |a| / |j|, dt_max)).
+__global__ void init_dt_kernel(const StateDev st, const double* acc, const double* jerk,
+                               double eta_start, double dt_max, double dt_min, double t0,
+                               uint32_t* status)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= st.n) return;
+    const double A = norm3_rn(acc[3 * i], acc[3 * i + 1], acc[3 * i + 2]);
+    const double J = norm3_rn(jerk[3 * i], jerk[3 * i + 1], jerk[3 * i + 2]);
+    double raw = DDIV(DMUL(eta_start, A), J);
+    st.t[i] = t0;
+    if (isnan(raw)) {
+        atomicOr(status, ST_NONFINITE);
+        st.dt[i] = dt_max;
+        return;
+    }
+    if (raw > dt_max) raw = dt_max;
+    if (raw <= 0.0) {
+        atomicOr(status, ST_DTMIN);
+        st.dt[i] = dt_max;
+        return;
+    }
+    const double dt = pow2_floor(raw);
+    st.dt[i] = dt;
+    if (dt < dt_min) atomicOr(status, ST_DTMIN);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        st.a[d * st.n + i] = acc[3 * i + d];
+        st.j[d * st.n + i] = jerk[3 * i + d];
+    }
+}
+
+cudaError_t init_dt_launch(const StateDev& st, const double* acc, const double* jerk,
+                           double eta_start, double dt_max, double dt_min, double t0,
+                           uint32_t* status, cudaStream_t s)
+{
+    if (st.n <= 0) return cudaSuccess;
+    const int threads = 256;
+    const unsigned blocks = static_cast<unsigned>((st.n + threads - 1) / threads);
+    init_dt_kernel<<<blocks, threads, 0, s>>>(st, acc, jerk, eta_start, dt_max, dt_min, t0, status);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Energy diagnostic: per-block partial sums, then the last block adds the
+// partials in block order (deterministic).
+// ---------------------------------------------------------------------------
+__global__ void energy_kernel(const StateDev st, const double* pot_all, double* partials,
+                              double* out, uint32_t* ticket)
+{
+    __shared__ double sk[256], sw[256];
+    double k = 0.0, w = 0.0;
+    const int64_t n = st.n;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double vx = st.v[i], vy = st.v[n + i], vz = st.v[2 * n + i];
+        k += 0.5 * st.m[i] * (vx * vx + vy * vy + vz * vz);
+        w += 0.5 * st.m[i] * pot_all[i];
+    }
+    sk[threadIdx.x] = k;
+    sw[threadIdx.x] = w;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            sk[threadIdx.x] += sk[threadIdx.x + o];
+            sw[threadIdx.x] += sw[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = sk[0];
+        partials[2 * blockIdx.x + 1] = sw[0];
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double K = 0.0, W = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) {
+            K += __ldcg(partials + 2 * b);
+            W += __ldcg(partials + 2 * b + 1);
+        }
+        out[0] = K;
+        out[1] = W;
+        *ticket = 0u;
+    }
+}
+
+cudaError_t energy_launch(const StateDev& st, const double* pot_all, double* partials,
+                          int max_blocks, double* out, uint32_t* ticket, cudaStream_t s)
+{
+    int blocks = static_cast<int>((st.n + 255) / 256);
+    if (blocks > max_blocks) blocks = max_blocks;
+    if (blocks < 1) blocks = 1;
+    energy_kernel<<<blocks, 256, 0, s>>>(st, pot_all, partials, out, ticket);
+    return cudaGetLastError();
+}
+
+__global__ void set_scalars_kernel(int32_t* i32, int32_t v, unsigned long long* t_bits,
+                                   double t)
+{
+    if (i32) *i32 = v;
+    if (t_bits) *t_bits = dkey(t);
+}
+
+cudaError_t set_scalars_launch(int32_t* i32, int32_t v, unsigned long long* t_bits, double t,
+                               cudaStream_t s)
+{
+    set_scalars_kernel<<<1, 1, 0, s>>>(i32, v, t_bits, t);
+    return cudaGetLastError();
+}
+
+double time_from_key(unsigned long long k)
+{
+    const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+    double x;
+    static_assert(sizeof(x) == sizeof(b), "double is 64-bit");
+    memcpy(&x, &b, sizeof(x));
+    return x;
+}
+
+// ---------------------------------------------------------------------------
+// Layout helpers.
+// ---------------------------------------------------------------------------
+__global__ void aos_to_soa_kernel(const double* aos, double* soa, int64_t n)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= 3 * n) return;
+    const int64_t i = q / 3, c = q - 3 * i;
+    soa[c * n + i] = aos[q];
+}
+
+__global__ void soa_to_aos_kernel(const double* soa, double* aos, int64_t n)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= 3 * n) return;
+    const int64_t i = q / 3, c = q - 3 * i;
+    aos[q] = soa[c * n + i];
+}
+
+__global__ void iota_kernel(int32_t* idx, int64_t n, int32_t* n_act_dev)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) idx[i] = static_cast<int32_t>(i);
+    if (i == 0 && n_act_dev) *n_act_dev = static_cast<int32_t>(n);
+}
+
+cudaError_t aos_to_soa_launch(const double* aos, double* soa, int64_t n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    aos_to_soa_kernel<<<static_cast<unsigned>((3 * n + 255) / 256), 256, 0, s>>>(aos, soa, n);
+    return cudaGetLastError();
+}
+
+cudaError_t soa_to_aos_launch(const double* soa, double* aos, int64_t n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    soa_to_aos_kernel<<<static_cast<unsigned>((3 * n + 255) / 256), 256, 0, s>>>(soa, aos, n);
+    return cudaGetLastError();
+}
+
+cudaError_t iota_launch(int32_t* idx, int64_t n, int32_t* n_act_dev, cudaStream_t s)
+{
+    const int64_t m = n > 0 ? n : 1;
+    iota_kernel<<<static_cast<unsigned>((m + 255) / 256), 256, 0, s>>>(idx, n, n_act_dev);
+    return cudaGetLastError();
+}
+
+}  // namespace nb

@@ -1,0 +1,144 @@
+// Device-side building blocks shared by the kernels of libnbody: status bits,
+// mbarrier / bulk-copy wrappers (inline PTX, sm_100+), error-free FP32
+// transforms and the per-context launch arguments.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace nb {
+
+// ---------------------------------------------------------------------------
+// Device status word (OR-ed by kernels, read back by the host).
+// ---------------------------------------------------------------------------
+enum : uint32_t {
+    ST_TIMEOUT = 1u,    // a bounded wait on an mbarrier gave up
+    ST_NONFINITE = 2u,  // a force/jerk value or a timestep was not finite
+    ST_DTMIN = 4u,      // a timestep fell below dt_min
+    ST_BADINDEX = 8u,   // an active index was outside [0, n)
+    ST_NOTDUE = 16u,    // a corrected particle was not due at the block time
+};
+
+// j particles per staged tile (the depth of each warp's tile ring is a
+// property of each precision policy).
+constexpr int TJ = 64;
+constexpr int FORCE_WARPS = 4;  // warps per CTA of the force kernels
+
+// About one second at the GB300 SM clock: the bound on any spin wait.
+constexpr long long WAIT_LIMIT_CYCLES = 2000000000LL;
+
+// Ghost j particles pad every system to a multiple of TJ; they carry zero
+// mass and sit this far away, so each of their terms is an exact zero.
+constexpr double GHOST_POS = 1.0e10;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                     smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// One-dimensional bulk copy global -> shared, completing on `bar`.
+// Both addresses must be 16-byte aligned and `bytes` a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for phase `parity` of `bar`; false after WAIT_LIMIT_CYCLES.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > WAIT_LIMIT_CYCLES) return false;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Error-free FP32 transforms (Knuth TwoSum; FMA-based TwoProd).  The _rn
+// intrinsics keep the compiler from contracting or reordering them.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// p + e == a * b exactly (FMA-based TwoProd).
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e)
+{
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+// Running double-single accumulator: hi carries the sum, lo the collected
+// rounding errors of every fold.
+struct DSAcc {
+    float hi, lo;
+    __device__ __forceinline__ void zero() { hi = 0.f, lo = 0.f; }
+    __device__ __forceinline__ void fold(float x)
+    {
+        float s, e;
+        two_sum(hi, x, s, e);
+        hi = s;
+        lo = __fadd_rn(lo, e);
+    }
+    // Add a double-single term (th + tl).
+    __device__ __forceinline__ void add(float th, float tl)
+    {
+        float s, e;
+        two_sum(hi, th, s, e);
+        hi = s;
+        lo = __fadd_rn(lo, __fadd_rn(e, tl));
+    }
+    __device__ __forceinline__ double value() const
+    {
+        return static_cast<double>(hi) + static_cast<double>(lo);
+    }
+};
+
+}  // namespace nb

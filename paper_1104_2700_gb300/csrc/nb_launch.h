@@ -1,0 +1,139 @@
+// Host-side interface between the C ABI (capi.cu) and the kernel translation
+// units (force.cu, hermite.cu).  Internal to libnbody; not installed.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace nb {
+
+// Precision of the force path.
+//   FP64  - every operation in double (the plain baseline).
+//   MIXED - Sec. 3.2 "mixed" precision: r_ij from double-single positions,
+//           the pair arithmetic in FP32, per-tile FP32 partial sums folded
+//           into compensated (double-single) accumulators.
+//   DS    - the same pair formulas evaluated in double-single ("float-float")
+//           arithmetic on the FP32 pipes with error-free transforms.
+enum class Prec : int { FP64 = 0, MIXED = 1, DS = 2 };
+
+// Device Hermite state of one context, structure of arrays.  x, v, a, j
+// hold 3*n doubles: component c of particle i at [c*n + i].
+struct StateDev {
+    int64_t n = 0;      // real particles
+    int64_t n_pad = 0;  // j-layout length (multiple of the tile size)
+    double* m = nullptr;
+    double* x = nullptr;
+    double* v = nullptr;
+    double* a = nullptr;
+    double* j = nullptr;
+    double* t = nullptr;
+    double* dt = nullptr;
+};
+
+// Predicted j particles in the layout a force kernel streams.
+//   FP64 : arr[0] = double4 (x, y, z, G m), arr[1] = double4 (vx, vy, vz, 0)
+//   MIXED: arr[0] = float4 (x_hi, y_hi, z_hi, G m), arr[1] = float4 (x_lo,
+//          y_lo, z_lo, vx), arr[2] = float2 (vy, vz)
+//   DS   : arr[0] = float4 (x_hi, y_hi, z_hi, Gm_hi), arr[1] = float4 (x_lo,
+//          y_lo, z_lo, Gm_lo), arr[2] = float4 (vx_hi, vy_hi, vz_hi, 0),
+//          arr[3] = float4 (vx_lo, vy_lo, vz_lo, 0)
+struct JLayout {
+    void* arr[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+int jlayout_narr(Prec p);
+int jlayout_elem_bytes(Prec p, int k);
+
+// Scheduler buffers (step 1 of the integration procedure).
+struct SchedDev {
+    unsigned long long* tmin_bits = nullptr;  // next block time, as bits
+    int32_t* idx = nullptr;                   // active list, capacity n
+    int32_t* n_act = nullptr;                 // device scalar
+    int32_t* block_counts = nullptr;
+    int32_t* block_offsets = nullptr;
+    uint32_t* ticket = nullptr;
+    int max_blocks = 0;
+};
+constexpr int SCHED_THREADS = 256;
+constexpr int SCHED_PER_THREAD = 8;
+constexpr int SCHED_CHUNK = SCHED_THREADS * SCHED_PER_THREAD;
+
+// Force launch (step 4): active list -> acc, jerk, pot.
+struct ForceArgs {
+    Prec prec = Prec::MIXED;
+    int it = 1;          // i particles per thread (register blocking)
+    JLayout jl;
+    int64_t n = 0;       // real particles (index validation)
+    int64_t n_pad = 0;   // j count incl. ghosts, multiple of TJ
+    const int32_t* idx = nullptr;
+    const int32_t* n_act_dev = nullptr;
+    double* acc = nullptr;   // [n_act][3]
+    double* jerk = nullptr;  // [n_act][3]
+    double* pot = nullptr;   // [n_act]
+    double* scratch = nullptr;
+    uint32_t* counters = nullptr;   // force_counter_entries() zeroed words
+    int64_t counter_stride = 0;     // entries per reduction level
+    uint32_t* status = nullptr;
+    double eps2 = 0.0;
+    int grid = 0;        // CTAs (persistent)
+};
+
+cudaError_t force_setup(Prec p, int it);  // one-time attribute setup
+int force_ctas_per_sm(Prec p, int it);
+size_t force_smem_bytes(Prec p);
+bool force_variant_exists(Prec p, int it);
+// Scratch needed for n_act_max active particles with `warps` persistent warps.
+size_t force_scratch_doubles(int it, int64_t n_act_max, int warps);
+// Arrival counters of the split-group reduction tree: stride per level and
+// the total number of 32-bit words (all must start at zero; the kernel
+// leaves them at zero).
+int64_t force_counter_stride(int64_t n_act_max, int warps);
+int64_t force_counter_entries(int64_t n_act_max, int warps);
+cudaError_t force_launch(const ForceArgs& f, cudaStream_t s);
+
+// Predictor (steps 2-3) to the time in *t_bits (if non-null) else t_host.
+// With n_act_dev non-null nothing is done when *n_act_dev == 0.
+cudaError_t predict_launch(const StateDev& st, Prec p, const JLayout& jl, double G,
+                           const unsigned long long* t_bits, double t_host,
+                           const int32_t* n_act_dev, cudaStream_t s);
+
+// Stream-ordered scalar stores: *i32 = v (if i32), *t_bits = key(t) (if t_bits).
+cudaError_t set_scalars_launch(int32_t* i32, int32_t v, unsigned long long* t_bits,
+                               double t, cudaStream_t s);
+// Host mirror of the device time key.
+double time_from_key(unsigned long long k);
+
+// Step 1: t_next = min(t + dt), stable compaction of the active block.
+// When t_next > t_end the block is empty (n_act = 0).
+cudaError_t select_launch(const StateDev& st, const SchedDev& sd, double t_end,
+                          cudaStream_t s);
+
+// Steps 5-8 on the active list at the time in *t_bits.
+struct CorrectArgs {
+    const int32_t* idx = nullptr;
+    const int32_t* n_act_dev = nullptr;
+    const unsigned long long* t_bits = nullptr;
+    const double* acc1 = nullptr;   // [n_act][3]
+    const double* jerk1 = nullptr;  // [n_act][3]
+    double eta = 0.02, dt_max = 1.0 / 16, dt_min = 0x1p-40;
+    uint32_t* status = nullptr;
+    unsigned long long* step_counter = nullptr;   // +1 per non-empty block
+    unsigned long long* inter_counter = nullptr;  // += n_act * n
+};
+cudaError_t correct_launch(const StateDev& st, const CorrectArgs& c, cudaStream_t s);
+
+// Initial timesteps from a, j (reading R3), t = t0.
+cudaError_t init_dt_launch(const StateDev& st, const double* acc, const double* jerk,
+                           double eta_start, double dt_max, double dt_min, double t0,
+                           uint32_t* status, cudaStream_t s);
+
+// Deterministic sums: out[0] = sum 1/2 m v^2, out[1] = sum 1/2 m phi.
+cudaError_t energy_launch(const StateDev& st, const double* pot_all, double* partials,
+                          int max_blocks, double* out, uint32_t* ticket,
+                          cudaStream_t s);
+
+// Layout conversions between host AoS [n][3] and device SoA.
+cudaError_t aos_to_soa_launch(const double* aos, double* soa, int64_t n, cudaStream_t s);
+cudaError_t soa_to_aos_launch(const double* soa, double* aos, int64_t n, cudaStream_t s);
+cudaError_t iota_launch(int32_t* idx, int64_t n, int32_t* n_act_dev, cudaStream_t s);
+
+}  // namespace nb
