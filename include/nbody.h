@@ -164,6 +164,38 @@ const char* nb_last_error(const nb_ctx* ctx);
 /* Static name of a status code. */
 const char* nb_status_string(nb_status s);
 
+/* Force evaluation that allocates no memory.  The paper has no counterpart:
+ * this is a service for callers that cannot allocate device memory, for
+ * example a host framework that owns every device allocation and forbids
+ * others, or a process whose GPU memory is already fully reserved.
+ * The calls above keep their buffers in a context that nb_set_particles
+ * sizes with cudaMalloc; this one keeps nothing between calls and never
+ * calls cudaMalloc, cudaFree or an allocating library routine.
+ *
+ * It computes what nb_force computes in NB_DS precision (Eqs. acc, jrk,
+ * pot): acc[n_act][3], jerk[n_act][3] and pot[n_act] of the particles
+ * idx[0..n_act) from every particle j != i, given masses m[n], positions
+ * r[n][3] and velocities v[n][3] (already at the wanted time), softening
+ * eps and constant G.  All pointers are device memory of the current
+ * device; the work runs on `stream` (a cudaStream_t, NULL = legacy default)
+ * and the call returns after it has finished.
+ *
+ * Its only working memory is one fixed device array of
+ * NB_STATIC_SCRATCH_BYTES inside the library, present on every GPU that
+ * loads the library until the process exits.  Limit: n <= NB_STATIC_MAX_N
+ * (larger n returns NB_EINVAL with a message on stderr).  The first call on
+ * a device performs a one-time set-up (the array's device address, kernel
+ * attributes); make that first call before any stream capture.  Every call
+ * shares the array: calls that overlap on the GPU (other threads, other
+ * streams) race and must be serialised by the caller.
+ * Errors: NB_EINVAL (sizes, NULL pointers, an index outside [0, n)),
+ * NB_ECUDA, NB_ETIMEOUT. */
+#define NB_STATIC_MAX_N 131072
+#define NB_STATIC_SCRATCH_BYTES (32 * 1024 * 1024)
+nb_status nb_force_static(int64_t n, const double* m, const double* r, const double* v,
+                          double eps, double G, int32_t n_act, const int32_t* idx,
+                          double* acc, double* jerk, double* pot, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -74,6 +74,8 @@ def load(path: str = LIB_PATH):
         "nb_num_particles": (c_int64, [P]),
         "nb_last_error": (c_char_p, [P]),
         "nb_status_string": (c_char_p, [c_int32]),
+        "nb_force_static": (c_int32, [c_int64, P, P, P, c_double, c_double, c_int32, P, P, P,
+                                      P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -168,6 +170,11 @@ def nb_num_particles(ctx) -> int:
 
 def nb_status_string(st: int) -> str:
     return load().nb_status_string(st).decode()
+
+
+def nb_force_static(n, m, r, v, eps, G, n_act, idx, acc, jerk, pot, stream):
+    """Allocation-free force evaluation on device pointers (see nbody.h)."""
+    return load().nb_force_static(n, m, r, v, eps, G, n_act, idx, acc, jerk, pot, stream)
 
 
 # --- marshalling helpers ------------------------------------------------------
