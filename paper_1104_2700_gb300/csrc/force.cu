@@ -224,13 +224,19 @@ struct PolicyMixed {
 // 44 bits, so cancellation among pair terms (near neighbours around a
 // particle with a small net acceleration or jerk) costs no accuracy at the
 // 1e-6 level.
+// (jh + jl) - (ih + il) as a normalised double-single pair.  s = fl(jh - ih)
+// and its error e are exact (TwoSum); the correction t = (jl - il) + e is no
+// larger in exponent than s whenever s != 0 (the lo parts are at most half
+// an ulp of their hi parts), and with s == 0 the sum is t itself, so the
+// final renormalisation can be Fast2Sum.
 __device__ __forceinline__ void ds_diff(float jh, float jl, float ih, float il, float& dh,
                                         float& dl)
 {
     float s, e;
     two_sum(jh, -ih, s, e);
     const float t = __fadd_rn(__fsub_rn(jl, il), e);
-    two_sum(s, t, dh, dl);
+    dh = __fadd_rn(s, t);
+    dl = __fsub_rn(t, __fsub_rn(dh, s));
 }
 
 // (ah + al) * (bh + bl) to first order: (p, e) with p = fl(ah * bh).
