@@ -154,6 +154,29 @@ nb_status nb_energy(nb_ctx* ctx, int32_t fp64_potential, double* kin, double* po
 /* Wait for all work queued on the context stream and report device errors. */
 nb_status nb_synchronize(nb_ctx* ctx);
 
+/* Load an ensemble of k independent systems (Sec. 2 set-up, applied to each
+ * system on its own).  System q owns particles [offsets[q], offsets[q+1])
+ * of the concatenated host arrays m[n], r[n][3], v[n][3] (n = offsets[k],
+ * offsets[0] = 0, every system non-empty) and has softening eps[q]; all
+ * share G (configuration) and eta.  Particles of different systems never
+ * interact.  Each system keeps its own block schedule: one block step
+ * (nb_block_step, nb_step_until) advances every system whose next block time
+ * is within t_end by one block, all of them in the same kernel launches.
+ * nb_force then needs idx strictly ascending; nb_correct is not available.
+ * Errors: NB_EINVAL (k < 1, empty system, eps < 0, eta <= 0), NB_ENOMEM,
+ * NB_ENONFINITE. */
+nb_status nb_set_ensemble(nb_ctx* ctx, int32_t k, const int64_t* offsets, const double* m,
+                          const double* r, const double* v, const double* eps, double eta);
+
+/* Energy of each system at a synchronised time: kin[q] = sum 1/2 m v^2 and
+ * pot[q] = 1/2 sum m phi over system q (Eq. pot), k entries each (one for a
+ * single system).  fp64_potential as in nb_energy.  Blocks. */
+nb_status nb_energy_systems(nb_ctx* ctx, int32_t fp64_potential, double* kin, double* pot);
+
+/* Number of systems loaded (1 after nb_set_particles, k after
+ * nb_set_ensemble, 0 before either). */
+int32_t nb_num_systems(const nb_ctx* ctx);
+
 /* Number of particles loaded (0 before nb_set_particles). */
 int64_t nb_num_particles(const nb_ctx* ctx);
 

@@ -33,6 +33,9 @@
  *      two no larger than dt_max.
  *   R4 The active block is every i with t_i + dt_i == t_next exactly (times
  *      are dyadic, so the comparison is exact), listed by ascending index.
+ *   R5 A particle that feels nothing (a system of one particle) has
+ *      a = j = s = c = 0, where Eq. timestep and the start rule read 0/0: a
+ *      zero denominator means no constraint, so the step is dt_max.
  */
 #include <math.h>
 #include <stddef.h>
@@ -152,7 +155,9 @@ double orc_aarseth_dt(double eta, const double *a, const double *j,
                       const double *s, const double *c)
 {
     const double A = norm3(a), J = norm3(j), S = norm3(s), C = norm3(c);
-    return eta * sqrt((A * S + J * J) / (J * C + S * S));
+    const double den = J * C + S * S;
+    if (den == 0.0) return INFINITY; /* reading R5: no constraint */
+    return eta * sqrt((A * S + J * J) / den);
 }
 
 /* Largest power of two (2^k, k integer) that is <= x, for x > 0 finite. */
@@ -187,7 +192,7 @@ int orc_initial_dt(double eta_start, const double *a, const double *j,
                    double dt_max, double dt_min, double *dt_out)
 {
     const double A = norm3(a), J = norm3(j);
-    double raw = eta_start * A / J; /* J == 0 gives +inf */
+    double raw = J == 0.0 ? INFINITY : eta_start * A / J; /* reading R5 */
     if (!(raw == raw)) return ORC_ENONFINITE;
     if (raw > dt_max) raw = dt_max;
     if (raw <= 0.0) return ORC_EDTMIN;

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "nb_device.cuh"
 #include "nb_launch.h"
@@ -47,6 +48,12 @@ struct nb_ctx {
     double* energy_out = nullptr;
     uint32_t* energy_ticket = nullptr;
     double* staging = nullptr;  // 3n doubles
+    // Ensemble mode (nb_set_ensemble): k independent systems in one context.
+    bool ens = false;
+    nb::ClusterDev cl;
+    std::vector<int64_t> h_off;  // host copy of the particle offsets
+    double* cl_energy = nullptr; // 2k
+    int64_t cap_pad = 0, cap_k = 0;
     unsigned char* pinned = nullptr;
     int energy_blocks = 0;
     int32_t last_force_n_act = -1;
@@ -121,7 +128,11 @@ void free_buffers(nb_ctx* c)
     dfree(c->idx_user), dfree(c->n_act_user), dfree(c->acc1), dfree(c->jerk1), dfree(c->pot1);
     dfree(c->scratch), dfree(c->counters), dfree(c->staging);
     dfree(c->energy_partials), dfree(c->energy_out), dfree(c->energy_ticket);
-    c->cap = 0;
+    dfree(c->cl.off), dfree(c->cl.joff), dfree(c->cl.eps2), dfree(c->cl.cluster_of);
+    dfree(c->cl.jsrc), dfree(c->cl.tkey), dfree(c->cl.grp_cluster), dfree(c->cl.grp_act_begin);
+    dfree(c->cl.grp_act_count), dfree(c->cl.grp_tile0), dfree(c->cl.plan_scalars);
+    dfree(c->cl_energy);
+    c->cap = c->cap_pad = c->cap_k = 0;
 }
 
 nb_status alloc_layout(nb_ctx* c, Prec p, nb::JLayout& jl, int64_t n_pad)
@@ -131,15 +142,16 @@ nb_status alloc_layout(nb_ctx* c, Prec p, nb::JLayout& jl, int64_t n_pad)
     return NB_OK;
 }
 
-// Size every n-dependent buffer for n particles.
-nb_status ensure_capacity(nb_ctx* c, int64_t n)
+// Size every n-dependent buffer for n particles in k systems (k = 0: one
+// system without cluster arrays) whose j layout has n_pad slots.
+nb_status ensure_capacity(nb_ctx* c, int64_t n, int64_t n_pad, int64_t k)
 {
-    const int64_t n_pad = (n + nb::TJ - 1) / nb::TJ * nb::TJ;
-    if (n <= c->cap) {
+    if (n <= c->cap && n_pad <= c->cap_pad && k <= c->cap_k) {
         c->n = n;
         c->n_pad = n_pad;
         c->st.n = n;
         c->st.n_pad = n_pad;
+        c->cl.k = static_cast<int>(k);
         return NB_OK;
     }
     free_buffers(c);
@@ -151,6 +163,8 @@ nb_status ensure_capacity(nb_ctx* c, int64_t n)
     NB_CK(c, cudaMalloc(&c->st.j, 3 * n * d));
     NB_CK(c, cudaMalloc(&c->st.t, n * d));
     NB_CK(c, cudaMalloc(&c->st.dt, n * d));
+    // i-groups never mix systems: at most n / 32 + k of them
+    const int64_t groups_bound = n + 32 * k;
     nb_status s = alloc_layout(c, c->prec, c->jl, n_pad);
     if (s != NB_OK) return s;
     if (c->prec != Prec::FP64) {
@@ -173,12 +187,13 @@ nb_status ensure_capacity(nb_ctx* c, int64_t n)
     NB_CK(c, cudaMalloc(&c->pot1, n * d));
     NB_CK(c, cudaMalloc(&c->staging, 3 * n * d));
     // Scratch for the split-group partials of both force precisions.
-    const size_t s1 = nb::force_scratch_doubles(c->it, n, c->grid * nb::FORCE_WARPS);
-    const size_t s2 = nb::force_scratch_doubles(1, n, c->grid64 * nb::FORCE_WARPS);
+    const size_t s1 = nb::force_scratch_doubles(c->it, groups_bound + 32 * c->it * k,
+                                                c->grid * nb::FORCE_WARPS);
+    const size_t s2 = nb::force_scratch_doubles(1, groups_bound, c->grid64 * nb::FORCE_WARPS);
     NB_CK(c, cudaMalloc(&c->scratch, (s1 > s2 ? s1 : s2) * d));
     const int max_warps = nb::FORCE_WARPS * std::max(c->grid, c->grid64);
-    c->counter_stride = nb::force_counter_stride(n, max_warps);
-    c->counter_words = nb::force_counter_entries(n, max_warps);
+    c->counter_stride = nb::force_counter_stride(groups_bound, max_warps);
+    c->counter_words = nb::force_counter_entries(groups_bound, max_warps);
     NB_CK(c, cudaMalloc(&c->counters, c->counter_words * sizeof(uint32_t)));
     NB_CK(c, cudaMemset(c->counters, 0, c->counter_words * sizeof(uint32_t)));
     c->energy_blocks = static_cast<int>(std::min<int64_t>((n + 255) / 256, 1024));
@@ -186,6 +201,25 @@ nb_status ensure_capacity(nb_ctx* c, int64_t n)
     NB_CK(c, cudaMalloc(&c->energy_out, 2 * d));
     NB_CK(c, cudaMalloc(&c->energy_ticket, sizeof(uint32_t)));
     NB_CK(c, cudaMemset(c->energy_ticket, 0, sizeof(uint32_t)));
+    if (k > 0) {
+        nb::ClusterDev& cl = c->cl;
+        cl.max_groups = n / 32 + k + 1;
+        NB_CK(c, cudaMalloc(&cl.off, (k + 1) * sizeof(int64_t)));
+        NB_CK(c, cudaMalloc(&cl.joff, (k + 1) * sizeof(int64_t)));
+        NB_CK(c, cudaMalloc(&cl.eps2, k * sizeof(double)));
+        NB_CK(c, cudaMalloc(&cl.cluster_of, n * sizeof(int32_t)));
+        NB_CK(c, cudaMalloc(&cl.jsrc, n_pad * sizeof(int32_t)));
+        NB_CK(c, cudaMalloc(&cl.tkey, k * sizeof(unsigned long long)));
+        NB_CK(c, cudaMalloc(&cl.grp_cluster, cl.max_groups * sizeof(int32_t)));
+        NB_CK(c, cudaMalloc(&cl.grp_act_begin, cl.max_groups * sizeof(int32_t)));
+        NB_CK(c, cudaMalloc(&cl.grp_act_count, cl.max_groups * sizeof(int32_t)));
+        NB_CK(c, cudaMalloc(&cl.grp_tile0, (cl.max_groups + 1) * sizeof(int64_t)));
+        NB_CK(c, cudaMalloc(&cl.plan_scalars, 2 * sizeof(int64_t)));
+        NB_CK(c, cudaMalloc(&c->cl_energy, 2 * k * sizeof(double)));
+    }
+    c->cl.k = static_cast<int>(k);
+    c->cap_pad = n_pad;
+    c->cap_k = k;
     c->cap = n;
     c->n = n;
     c->n_pad = n_pad;
@@ -246,8 +280,30 @@ nb_status run_force(nb_ctx* c, Prec p, const nb::JLayout& jl, const int32_t* idx
     f.status = c->status_dev;
     f.eps2 = c->eps * c->eps;
     f.grid = p == c->prec ? c->grid : c->grid64;
+    if (c->ens) {
+        // the plan for this active list must have been written by plan_launch
+        f.plan.grp_cluster = c->cl.grp_cluster;
+        f.plan.grp_act_begin = c->cl.grp_act_begin;
+        f.plan.grp_act_count = c->cl.grp_act_count;
+        f.plan.grp_tile0 = c->cl.grp_tile0;
+        f.plan.scalars = c->cl.plan_scalars;
+        f.plan.cl_off = c->cl.off;
+        f.plan.cl_joff = c->cl.joff;
+        f.plan.cl_eps2 = c->cl.eps2;
+    }
     NB_CK(c, nb::force_launch(f, c->stream));
     return NB_OK;
+}
+
+// Force on a sorted active list: in ensemble mode the plan comes first.
+nb_status run_force_list(nb_ctx* c, Prec p, const nb::JLayout& jl, const int32_t* idx,
+                         const int32_t* n_act_dev)
+{
+    if (c->ens) {
+        const int gi = 32 * (p == c->prec ? c->it : 1);
+        NB_CK(c, nb::plan_launch(c->cl, idx, n_act_dev, gi, c->stream));
+    }
+    return run_force(c, p, jl, idx, n_act_dev);
 }
 
 nb_status upload_vec3(nb_ctx* c, const double* src, double* dst_soa, int on_device)
@@ -279,15 +335,24 @@ nb_status validate_idx(nb_ctx* c, int32_t n_act, const int32_t* idx)
 
 nb_status block_step(nb_ctx* c, double t_end)
 {
-    NB_CK(c, nb::select_launch(c->st, c->sd, t_end, c->stream));
-    NB_CK(c, nb::predict_launch(c->st, c->prec, c->jl, c->cfg.G, c->sd.tmin_bits, 0.0,
-                                c->sd.n_act, c->stream));
-    nb_status s = run_force(c, c->prec, c->jl, c->sd.idx, c->sd.n_act);
+    const nb::ClusterDev* cl = c->ens ? &c->cl : nullptr;
+    const unsigned long long* tkeys = c->ens ? c->cl.tkey : c->sd.tmin_bits;
+    if (c->ens)
+        NB_CK(c, nb::cluster_select_launch(c->st, c->cl, c->sd, t_end, c->stream));
+    else
+        NB_CK(c, nb::select_launch(c->st, c->sd, t_end, c->stream));
+    NB_CK(c, nb::predict_launch(c->st, c->prec, c->jl, c->cfg.G, tkeys, 0.0, c->sd.n_act,
+                                c->stream, cl));
+    nb_status s = run_force_list(c, c->prec, c->jl, c->sd.idx, c->sd.n_act);
     if (s != NB_OK) return s;
     nb::CorrectArgs ca;
     ca.idx = c->sd.idx;
     ca.n_act_dev = c->sd.n_act;
-    ca.t_bits = c->sd.tmin_bits;
+    ca.t_bits = tkeys;
+    if (c->ens) {
+        ca.cluster_of = c->cl.cluster_of;
+        ca.cl_off = c->cl.off;
+    }
     ca.acc1 = c->acc1;
     ca.jerk1 = c->jerk1;
     ca.eta = c->eta;
@@ -339,7 +404,8 @@ nb_status begin_load(nb_ctx* c, int64_t n, double eps, double eta)
     drop_graph(c);
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) return fail(c, NB_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
-    nb_status s = ensure_capacity(c, n);
+    c->ens = false;
+    nb_status s = ensure_capacity(c, n, (n + nb::TJ - 1) / nb::TJ * nb::TJ, 0);
     if (s != NB_OK) return s;
     c->eps = eps;
     c->eta = eta;
@@ -499,7 +565,8 @@ nb_status nb_predict(nb_ctx* c, double t)
     nb_status s = enter(c, true);
     if (s != NB_OK) return s;
     if (!std::isfinite(t)) return fail(c, NB_EINVAL, "t not finite");
-    NB_CK(c, nb::predict_launch(c->st, c->prec, c->jl, c->cfg.G, nullptr, t, nullptr, c->stream));
+    NB_CK(c, nb::predict_launch(c->st, c->prec, c->jl, c->cfg.G, nullptr, t, nullptr, c->stream,
+                                c->ens ? &c->cl : nullptr));
     return NB_OK;
 }
 
@@ -507,12 +574,22 @@ nb_status nb_select(nb_ctx* c, double t_end, double* t_next, int32_t* n_act, int
 {
     nb_status s = enter(c, true);
     if (s != NB_OK) return s;
-    NB_CK(c, nb::select_launch(c->st, c->sd, t_end, c->stream));
     unsigned long long* hk = reinterpret_cast<unsigned long long*>(c->pinned + 16);
     int32_t* hn = reinterpret_cast<int32_t*>(c->pinned + 24);
-    NB_CK(c, cudaMemcpyAsync(hk, c->sd.tmin_bits, sizeof(*hk), cudaMemcpyDeviceToHost, c->stream));
-    NB_CK(c, cudaMemcpyAsync(hn, c->sd.n_act, sizeof(*hn), cudaMemcpyDeviceToHost, c->stream));
-    NB_CK(c, cudaStreamSynchronize(c->stream));
+    if (c->ens) {
+        NB_CK(c, nb::cluster_select_launch(c->st, c->cl, c->sd, t_end, c->stream));
+        std::vector<unsigned long long> keys(c->cl.k);
+        NB_CK(c, cudaMemcpyAsync(keys.data(), c->cl.tkey, keys.size() * sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, c->stream));
+        NB_CK(c, cudaMemcpyAsync(hn, c->sd.n_act, sizeof(*hn), cudaMemcpyDeviceToHost, c->stream));
+        NB_CK(c, cudaStreamSynchronize(c->stream));
+        *hk = *std::min_element(keys.begin(), keys.end());  // keys order like times
+    } else {
+        NB_CK(c, nb::select_launch(c->st, c->sd, t_end, c->stream));
+        NB_CK(c, cudaMemcpyAsync(hk, c->sd.tmin_bits, sizeof(*hk), cudaMemcpyDeviceToHost, c->stream));
+        NB_CK(c, cudaMemcpyAsync(hn, c->sd.n_act, sizeof(*hn), cudaMemcpyDeviceToHost, c->stream));
+        NB_CK(c, cudaStreamSynchronize(c->stream));
+    }
     if (t_next) *t_next = nb::time_from_key(*hk);
     if (n_act) *n_act = *hn;
     if (idx && *hn > 0) {
@@ -531,6 +608,10 @@ nb_status nb_force(nb_ctx* c, int32_t n_act, const int32_t* idx, double* acc, do
     if (n_act < 0 || n_act > c->n) return fail(c, NB_EINVAL, "n_act = %d out of range", n_act);
     if (n_act > 0 && !idx) return fail(c, NB_EINVAL, "NULL idx");
     if (!on_device && n_act > 0 && (s = validate_idx(c, n_act, idx)) != NB_OK) return s;
+    if (c->ens && !on_device)
+        for (int32_t k = 1; k < n_act; ++k)
+            if (idx[k] <= idx[k - 1])
+                return fail(c, NB_EINVAL, "ensemble force needs idx strictly ascending");
     const int32_t* idx_dev = idx;
     if (n_act > 0 && !on_device) {
         NB_CK(c, cudaMemcpyAsync(c->idx_user, idx, (size_t)n_act * sizeof(int32_t),
@@ -538,7 +619,8 @@ nb_status nb_force(nb_ctx* c, int32_t n_act, const int32_t* idx, double* acc, do
         idx_dev = c->idx_user;
     }
     NB_CK(c, nb::set_scalars_launch(c->n_act_user, n_act, nullptr, 0.0, c->stream));
-    if (n_act > 0 && (s = run_force(c, c->prec, c->jl, idx_dev, c->n_act_user)) != NB_OK) return s;
+    if (n_act > 0 && (s = run_force_list(c, c->prec, c->jl, idx_dev, c->n_act_user)) != NB_OK)
+        return s;
     c->last_force_n_act = n_act;
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (n_act > 0) {
@@ -555,6 +637,9 @@ nb_status nb_correct(nb_ctx* c, double t, int32_t n_act, const int32_t* idx, con
 {
     nb_status s = enter(c, true);
     if (s != NB_OK) return s;
+    if (c->ens)
+        return fail(c, NB_ESTATE, "nb_correct works on one system; an ensemble advances with "
+                                  "nb_block_step or nb_step_until");
     if (n_act < 0 || n_act > c->n) return fail(c, NB_EINVAL, "n_act = %d out of range", n_act);
     if (!std::isfinite(t)) return fail(c, NB_EINVAL, "t not finite");
     if (n_act > 0 && !idx) return fail(c, NB_EINVAL, "NULL idx");
@@ -644,11 +729,14 @@ nb_status nb_energy(nb_ctx* c, int32_t fp64_potential, double* kin, double* pot)
     double* ht = reinterpret_cast<double*>(c->pinned + 48);
     NB_CK(c, cudaMemcpyAsync(ht, c->st.t, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     NB_CK(c, cudaStreamSynchronize(c->stream));
-    NB_CK(c, nb::predict_launch(c->st, p, jl, c->cfg.G, nullptr, *ht, nullptr, c->stream));
+    NB_CK(c, nb::predict_launch(c->st, p, jl, c->cfg.G, nullptr, *ht, nullptr, c->stream,
+                                c->ens ? &c->cl : nullptr));
     NB_CK(c, nb::iota_launch(c->idx_user, c->n, c->n_act_user, c->stream));
-    if ((s = run_force(c, p, jl, c->idx_user, c->n_act_user)) != NB_OK) return s;
+    if ((s = run_force_list(c, p, jl, c->idx_user, c->n_act_user)) != NB_OK) return s;
     NB_CK(c, nb::energy_launch(c->st, c->pot1, c->energy_partials, c->energy_blocks,
                                c->energy_out, c->energy_ticket, c->stream));
+    if (c->ens)
+        NB_CK(c, nb::cluster_energy_launch(c->st, c->cl, c->pot1, c->cl_energy, c->stream));
     double* he = reinterpret_cast<double*>(c->pinned + 64);
     NB_CK(c, cudaMemcpyAsync(he, c->energy_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     if ((s = check_status(c)) != NB_OK) return s;
@@ -666,6 +754,99 @@ nb_status nb_synchronize(nb_ctx* c)
     if (c->loaded) return check_status(c);
     return NB_OK;
 }
+
+nb_status nb_set_ensemble(nb_ctx* c, int32_t k, const int64_t* offsets, const double* m,
+                          const double* r, const double* v, const double* eps, double eta)
+{
+    if (!c) return NB_EINVAL;
+    if (k < 1 || !offsets || !m || !r || !v || !eps)
+        return fail(c, NB_EINVAL, "need k >= 1 and non-NULL arrays");
+    if (offsets[0] != 0) return fail(c, NB_EINVAL, "offsets[0] must be 0");
+    for (int32_t q = 0; q < k; ++q) {
+        if (offsets[q + 1] <= offsets[q])
+            return fail(c, NB_EINVAL, "system %d is empty or offsets not increasing", q);
+        if (!(eps[q] >= 0.0) || !std::isfinite(eps[q]))
+            return fail(c, NB_EINVAL, "eps[%d] must be finite and >= 0", q);
+    }
+    const int64_t n = offsets[k];
+    if (n > 0x7fffffffLL) return fail(c, NB_EINVAL, "too many particles");
+    if (!(eta > 0.0) || !std::isfinite(eta)) return fail(c, NB_EINVAL, "eta must be > 0");
+    c->sticky = NB_OK;
+    c->loaded = false;
+    c->err.clear();
+    drop_graph(c);
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, NB_ECUDA, "cudaSetDevice");
+    // j layout: each system's particles, then ghosts up to a whole tile
+    std::vector<int64_t> joff(k + 1, 0);
+    for (int32_t q = 0; q < k; ++q)
+        joff[q + 1] = joff[q] + (offsets[q + 1] - offsets[q] + nb::TJ - 1) / nb::TJ * nb::TJ;
+    const int64_t n_pad = joff[k];
+    std::vector<int32_t> cluster_of(n), jsrc(n_pad, -1);
+    std::vector<double> eps2(k);
+    for (int32_t q = 0; q < k; ++q) {
+        eps2[q] = eps[q] * eps[q];
+        for (int64_t i = offsets[q]; i < offsets[q + 1]; ++i) {
+            cluster_of[i] = q;
+            jsrc[joff[q] + (i - offsets[q])] = static_cast<int32_t>(i);
+        }
+    }
+    c->ens = true;
+    nb_status s = ensure_capacity(c, n, n_pad, k);
+    if (s != NB_OK) return s;
+    c->eps = 0.0;  // per system: cl.eps2
+    c->eta = eta;
+    c->h_off.assign(offsets, offsets + k + 1);
+    const auto h2d = cudaMemcpyHostToDevice;
+    NB_CK(c, cudaMemcpyAsync(c->cl.off, offsets, (k + 1) * sizeof(int64_t), h2d, c->stream));
+    NB_CK(c, cudaMemcpyAsync(c->cl.joff, joff.data(), (k + 1) * sizeof(int64_t), h2d, c->stream));
+    NB_CK(c, cudaMemcpyAsync(c->cl.eps2, eps2.data(), k * sizeof(double), h2d, c->stream));
+    NB_CK(c, cudaMemcpyAsync(c->cl.cluster_of, cluster_of.data(), n * sizeof(int32_t), h2d, c->stream));
+    NB_CK(c, cudaMemcpyAsync(c->cl.jsrc, jsrc.data(), n_pad * sizeof(int32_t), h2d, c->stream));
+    NB_CK(c, cudaMemsetAsync(c->status_dev, 0, sizeof(uint32_t), c->stream));
+    NB_CK(c, cudaMemsetAsync(c->counters, 0, c->counter_words * sizeof(uint32_t), c->stream));
+    NB_CK(c, cudaMemcpyAsync(c->st.m, m, n * sizeof(double), h2d, c->stream));
+    if ((s = upload_vec3(c, r, c->st.x, 0)) != NB_OK) return s;
+    if ((s = upload_vec3(c, v, c->st.v, 0)) != NB_OK) return s;
+    NB_CK(c, cudaMemsetAsync(c->st.a, 0, 3 * n * sizeof(double), c->stream));
+    NB_CK(c, cudaMemsetAsync(c->st.j, 0, 3 * n * sizeof(double), c->stream));
+    NB_CK(c, cudaMemsetAsync(c->st.t, 0, n * sizeof(double), c->stream));
+    // forces on every particle of every system at t = 0, first timesteps
+    NB_CK(c, nb::predict_launch(c->st, c->prec, c->jl, c->cfg.G, nullptr, 0.0, nullptr, c->stream,
+                                &c->cl));
+    NB_CK(c, nb::iota_launch(c->idx_user, n, c->n_act_user, c->stream));
+    if ((s = run_force_list(c, c->prec, c->jl, c->idx_user, c->n_act_user)) != NB_OK) return s;
+    NB_CK(c, nb::init_dt_launch(c->st, c->acc1, c->jerk1, c->cfg.eta_start, c->cfg.dt_max,
+                                c->cfg.dt_min, 0.0, c->status_dev, c->stream));
+    if ((s = check_status(c)) != NB_OK) return s;
+    c->last_force_n_act = -1;
+    c->loaded = true;
+    return NB_OK;
+}
+
+nb_status nb_energy_systems(nb_ctx* c, int32_t fp64_potential, double* kin, double* pot)
+{
+    nb_status s = enter(c, true);
+    if (s != NB_OK) return s;
+    if (!c->ens) {
+        double K = 0.0, W = 0.0;
+        if ((s = nb_energy(c, fp64_potential, &K, &W)) != NB_OK) return s;
+        if (kin) kin[0] = K;
+        if (pot) pot[0] = W;
+        return NB_OK;
+    }
+    if ((s = nb_energy(c, fp64_potential, nullptr, nullptr)) != NB_OK) return s;
+    std::vector<double> h(2 * c->cl.k);
+    NB_CK(c, cudaMemcpyAsync(h.data(), c->cl_energy, h.size() * sizeof(double),
+                             cudaMemcpyDeviceToHost, c->stream));
+    NB_CK(c, cudaStreamSynchronize(c->stream));
+    for (int q = 0; q < c->cl.k; ++q) {
+        if (kin) kin[q] = h[2 * q];
+        if (pot) pot[q] = h[2 * q + 1];
+    }
+    return NB_OK;
+}
+
+int32_t nb_num_systems(const nb_ctx* c) { return c && c->loaded ? (c->ens ? c->cl.k : 1) : 0; }
 
 int64_t nb_num_particles(const nb_ctx* c) { return c && c->loaded ? c->n : 0; }
 

@@ -38,6 +38,16 @@ struct ForceParams {
     int64_t counter_stride;  // >= warps + groups
     uint32_t* status;
     double eps2;
+    // Ensemble plan (all null for one system): i-groups built by
+    // plan_launch, and per-cluster particle / j-layout offsets and eps^2.
+    const int32_t* grp_cluster;
+    const int32_t* grp_act_begin;
+    const int32_t* grp_act_count;
+    const int64_t* grp_tile0;     // n_groups + 1 entries
+    const int64_t* plan_scalars;  // [0] groups, [1] tiles
+    const int64_t* cl_off;
+    const int64_t* cl_joff;
+    const double* cl_eps2;
 };
 
 // ---------------------------------------------------------------------------
@@ -78,12 +88,11 @@ struct PolicyFP64 {
     }
 
     template <bool MASK>
-    __device__ static void tile(const unsigned char* buf, int64_t j0, const ForceParams& f,
+    __device__ static void tile(const unsigned char* buf, int64_t j0, const double eps2,
                                 I (&is)[IT], Acc (&ac)[IT])
     {
         const double2* sP = reinterpret_cast<const double2*>(buf);
         const double2* sV = reinterpret_cast<const double2*>(buf + TJ * 32);
-        const double eps2 = f.eps2;
 #pragma unroll 2
         for (int k = 0; k < TJ; ++k) {
             const double2 p0 = sP[2 * k], p1 = sP[2 * k + 1];
@@ -159,13 +168,13 @@ struct PolicyMixed {
     }
 
     template <bool MASK>
-    __device__ static void tile(const unsigned char* buf, int64_t j0, const ForceParams& f,
+    __device__ static void tile(const unsigned char* buf, int64_t j0, const double eps2d,
                                 I (&is)[IT], Acc (&ac)[IT])
     {
         const float4* sA = reinterpret_cast<const float4*>(buf);
         const float4* sB = reinterpret_cast<const float4*>(buf + TJ * 16);
         const float2* sC = reinterpret_cast<const float2*>(buf + TJ * 32);
-        const float eps2 = static_cast<float>(f.eps2);
+        const float eps2 = static_cast<float>(eps2d);
         float ax[IT], ay[IT], az[IT], jx[IT], jy[IT], jz[IT], ph[IT];
 #pragma unroll
         for (int q = 0; q < IT; ++q)
@@ -286,15 +295,15 @@ struct PolicyDS {
     }
 
     template <bool MASK>
-    __device__ static void tile(const unsigned char* buf, int64_t j0, const ForceParams& f,
+    __device__ static void tile(const unsigned char* buf, int64_t j0, const double eps2d,
                                 I (&is)[IT], Acc (&ac)[IT])
     {
         const float4* sA = reinterpret_cast<const float4*>(buf);
         const float4* sB = reinterpret_cast<const float4*>(buf + TJ * 16);
         const float4* sC = reinterpret_cast<const float4*>(buf + TJ * 32);
         const float4* sD = reinterpret_cast<const float4*>(buf + TJ * 48);
-        const float e2h = static_cast<float>(f.eps2);
-        const float e2l = static_cast<float>(f.eps2 - static_cast<double>(e2h));
+        const float e2h = static_cast<float>(eps2d);
+        const float e2l = static_cast<float>(eps2d - static_cast<double>(e2h));
 #pragma unroll 1
         for (int k = 0; k < TJ; ++k) {
             const float4 A = sA[k];
@@ -425,7 +434,80 @@ __device__ __forceinline__ int64_t owner_warp(int64_t x, int64_t T, int64_t Pu)
     return ((x + 1) * Pu - 1) / T;
 }
 
-template <class K, int IT>
+// One i-group of a launch: up to 32*IT consecutive active-list entries of
+// one system and the j tiles of that system, placed at flattened tile0.
+struct GroupInfo {
+    int64_t act_begin, act_count;  // active-list entries
+    int64_t tile0, ntiles;         // flattened tiles of the group
+    int64_t jtile0;                // first j tile of its system in the j layout
+    int64_t pj_shift;              // j-layout slot of particle p = p + pj_shift
+    double eps2;
+};
+
+// One system over the whole j layout: groups of GI consecutive entries.
+struct UniformPlan {
+    int64_t n_act, G, NT, T;
+    double eps2;
+    int GI;
+    __device__ void init(const ForceParams& f, int gi)
+    {
+        GI = gi;
+        n_act = *f.n_act_dev;
+        G = (n_act + GI - 1) / GI;
+        NT = f.n_pad / TJ;
+        T = G * NT;
+        eps2 = f.eps2;
+    }
+    __device__ int64_t find(int64_t t) const { return t / NT; }
+    __device__ GroupInfo group(int64_t g) const
+    {
+        GroupInfo gi;
+        gi.act_begin = g * GI;
+        gi.act_count = n_act - gi.act_begin < GI ? n_act - gi.act_begin : GI;
+        gi.tile0 = g * NT;
+        gi.ntiles = NT;
+        gi.jtile0 = 0;
+        gi.pj_shift = 0;
+        gi.eps2 = eps2;
+        return gi;
+    }
+};
+
+// Independent systems (ensemble): group descriptors from plan_launch.
+struct ClusterPlan {
+    const ForceParams* f;
+    int64_t G, T;
+    __device__ void init(const ForceParams& fp, int)
+    {
+        f = &fp;
+        G = fp.plan_scalars[0];
+        T = fp.plan_scalars[1];
+    }
+    __device__ int64_t find(int64_t t) const
+    {
+        int64_t lo = 0, hi = G;  // last g with tile0[g] <= t
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (f->grp_tile0[mid] <= t) lo = mid; else hi = mid;
+        }
+        return lo;
+    }
+    __device__ GroupInfo group(int64_t g) const
+    {
+        GroupInfo gi;
+        const int c = f->grp_cluster[g];
+        gi.act_begin = f->grp_act_begin[g];
+        gi.act_count = f->grp_act_count[g];
+        gi.tile0 = f->grp_tile0[g];
+        gi.ntiles = f->grp_tile0[g + 1] - gi.tile0;
+        gi.jtile0 = f->cl_joff[c] / TJ;
+        gi.pj_shift = f->cl_joff[c] - f->cl_off[c];
+        gi.eps2 = f->cl_eps2[c];
+        return gi;
+    }
+};
+
+template <class K, int IT, class Plan>
 __global__ void __launch_bounds__(FORCE_WARPS * 32)
     force_kernel(const ForceParams f)
 {
@@ -435,11 +517,10 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
     const int64_t w = (int64_t)blockIdx.x * FORCE_WARPS + wib;
     const int64_t P = (int64_t)gridDim.x * FORCE_WARPS;
 
-    const int n_act = *f.n_act_dev;
     constexpr int GI = 32 * IT;
-    const int64_t G = (n_act + GI - 1) / GI;
-    const int64_t NT = f.n_pad / TJ;
-    const int64_t T = G * NT;
+    Plan plan;
+    plan.init(f, GI);
+    const int64_t T = plan.T;
     if (T <= 0) return;
     const int64_t Pu = P < T ? P : T;
     if (w >= Pu) return;
@@ -456,32 +537,46 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
         fence_mbar_init();
     }
     __syncwarp();
-    if (lane == 0) {
-        for (int s = 0; s < K::STAGES && t0 + s < t1; ++s)
-            issue_tile<K>(f, ring + s * K::TILE_BYTES, &bars[s], (t0 + s) % NT);
-    }
+    // Compute cursor (g, gi) and load cursor (lg, lgi): both start at the
+    // group of tile t0; the load cursor runs STAGES tiles ahead.
+    int64_t g = plan.find(t0);
+    GroupInfo gi = plan.group(g);
+    int64_t lg = g;
+    GroupInfo lgi = gi;
+    int64_t tl = t0;
+    auto issue_next = [&](int s) {
+        while (tl >= lgi.tile0 + lgi.ntiles) lgi = plan.group(++lg);
+        if (lane == 0)
+            issue_tile<K>(f, ring + s * K::TILE_BYTES, &bars[s], lgi.jtile0 + (tl - lgi.tile0));
+        ++tl;
+    };
+    for (int s = 0; s < K::STAGES && t0 + s < t1; ++s) issue_next(s);
 
     typename K::I is[IT];
     typename K::Acc ac[IT];
-    int64_t g_cur = -1;
+    bool fresh = true;
 
     for (int64_t t = t0; t < t1; ++t) {
         const int64_t k = t - t0;
         const int s = static_cast<int>(k % K::STAGES);
         const uint32_t parity = static_cast<uint32_t>((k / K::STAGES) & 1);
-        const int64_t g = t / NT;
-        const int64_t jt = t - g * NT;
-        if (g != g_cur) {
-            g_cur = g;
+        while (t >= gi.tile0 + gi.ntiles) {
+            gi = plan.group(++g);
+            fresh = true;
+        }
+        if (fresh) {
+            fresh = false;
 #pragma unroll
             for (int q = 0; q < IT; ++q) {
-                const int64_t a = g * GI + q * 32 + lane;
+                const int64_t a = gi.act_begin + q * 32 + lane;
                 int p = -1;
-                if (a < n_act) {
+                if (a < gi.act_begin + gi.act_count) {
                     p = f.idx[a];
                     if (p < 0 || p >= f.n) {
                         atomicOr(f.status, ST_BADINDEX);
                         p = -1;
+                    } else {
+                        p = static_cast<int>(p + gi.pj_shift);
                     }
                 }
                 K::load_i(f, p, is[q]);
@@ -493,31 +588,32 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
             if (lane == 0) atomicOr(f.status, ST_TIMEOUT);
             return;
         }
-        const int64_t j0 = jt * TJ;
+        const int64_t jt = t - gi.tile0;
+        const int64_t j0 = (gi.jtile0 + jt) * TJ;
         bool self_here = false;
 #pragma unroll
         for (int q = 0; q < IT; ++q)
             self_here |= (is[q].p >= j0 && is[q].p < j0 + TJ);
         const unsigned char* buf = ring + s * K::TILE_BYTES;
         if (__any_sync(0xffffffffu, self_here))
-            K::template tile<true>(buf, j0, f, is, ac);
+            K::template tile<true>(buf, j0, gi.eps2, is, ac);
         else
-            K::template tile<false>(buf, j0, f, is, ac);
+            K::template tile<false>(buf, j0, gi.eps2, is, ac);
         __syncwarp();
-        if (lane == 0 && t + K::STAGES < t1) {
-            fence_proxy_async_smem();
-            issue_tile<K>(f, ring + s * K::TILE_BYTES, &bars[s], (t + K::STAGES) % NT);
+        if (t + K::STAGES < t1) {
+            if (lane == 0) fence_proxy_async_smem();
+            issue_next(s);
         }
 
-        if (jt == NT - 1 || t == t1 - 1) {
-            // This warp's share of group g is complete.  The K warps that
+        if (jt == gi.ntiles - 1 || t == t1 - 1) {
+            // This warp's share of group g is complete.  The warps that
             // share the group are summed by a radix-RB tree: within each
             // chunk of RB consecutive contributors the last to arrive adds
             // the chunk in order and carries the sum one level up.  Level-L
             // entry r lives in scratch slot key + r * RB^L (the first slot of
             // the chunk it replaces); each level has its own counters.
-            const int64_t wf = owner_warp(g * NT, T, Pu);
-            const int64_t wl = owner_warp((g + 1) * NT - 1, T, Pu);
+            const int64_t wf = owner_warp(gi.tile0, T, Pu);
+            const int64_t wl = owner_warp(gi.tile0 + gi.ntiles - 1, T, Pu);
             double v[IT][7];
 #pragma unroll
             for (int q = 0; q < IT; ++q) K::values(ac[q], v[q]);
@@ -565,8 +661,8 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
             if (final_here) {
 #pragma unroll
                 for (int q = 0; q < IT; ++q) {
-                    const int64_t a = g * GI + q * 32 + lane;
-                    if (a < n_act) {
+                    const int64_t a = gi.act_begin + q * 32 + lane;
+                    if (a < gi.act_begin + gi.act_count) {
                         f.acc[3 * a + 0] = v[q][0];
                         f.acc[3 * a + 1] = v[q][1];
                         f.acc[3 * a + 2] = v[q][2];
@@ -587,26 +683,24 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
 namespace {
 
 template <class K, int IT>
-const void* kfn()
+const void* kfn(bool ens)
 {
-    return reinterpret_cast<const void*>(&force_kernel<K, IT>);
+    return ens ? reinterpret_cast<const void*>(&force_kernel<K, IT, ClusterPlan>)
+               : reinterpret_cast<const void*>(&force_kernel<K, IT, UniformPlan>);
 }
 
-const void* kernel_ptr(Prec p, int it)
+const void* kernel_ptr(Prec p, int it, bool ens = false)
 {
     switch (p) {
     case Prec::FP64:
-        if (it == 1) return kfn<PolicyFP64<1>, 1>();
-        if (it == 2) return kfn<PolicyFP64<2>, 2>();
+        if (it == 1) return kfn<PolicyFP64<1>, 1>(ens);
         return nullptr;
     case Prec::MIXED:
-        if (it == 1) return kfn<PolicyMixed<1>, 1>();
-        if (it == 2) return kfn<PolicyMixed<2>, 2>();
-        if (it == 4) return kfn<PolicyMixed<4>, 4>();
+        if (it == 1) return kfn<PolicyMixed<1>, 1>(ens);
+        if (it == 2) return kfn<PolicyMixed<2>, 2>(ens);
         return nullptr;
     case Prec::DS:
-        if (it == 1) return kfn<PolicyDS<1>, 1>();
-        if (it == 2) return kfn<PolicyDS<2>, 2>();
+        if (it == 1) return kfn<PolicyDS<1>, 1>(ens);
         return nullptr;
     }
     return nullptr;
@@ -648,10 +742,14 @@ bool force_variant_exists(Prec p, int it) { return kernel_ptr(p, it) != nullptr;
 
 cudaError_t force_setup(Prec p, int it)
 {
-    const void* fn = kernel_ptr(p, it);
-    if (!fn) return cudaErrorInvalidValue;
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(force_smem_bytes(p)));
+    for (int e = 0; e < 2; ++e) {
+        const void* fn = kernel_ptr(p, it, e == 1);
+        if (!fn) return cudaErrorInvalidValue;
+        const cudaError_t r = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   static_cast<int>(force_smem_bytes(p)));
+        if (r != cudaSuccess) return r;
+    }
+    return cudaSuccess;
 }
 
 int force_ctas_per_sm(Prec p, int it)
@@ -684,7 +782,7 @@ int64_t force_counter_entries(int64_t n_act_max, int warps)
 
 cudaError_t force_launch(const ForceArgs& a, cudaStream_t s)
 {
-    const void* fn = kernel_ptr(a.prec, a.it);
+    const void* fn = kernel_ptr(a.prec, a.it, a.plan.grp_tile0 != nullptr);
     if (!fn || a.grid <= 0) return cudaErrorInvalidValue;
     ForceParams f;
     f.jl0 = a.jl.arr[0];
@@ -703,6 +801,14 @@ cudaError_t force_launch(const ForceArgs& a, cudaStream_t s)
     f.counter_stride = a.counter_stride;
     f.status = a.status;
     f.eps2 = a.eps2;
+    f.grp_cluster = a.plan.grp_cluster;
+    f.grp_act_begin = a.plan.grp_act_begin;
+    f.grp_act_count = a.plan.grp_act_count;
+    f.grp_tile0 = a.plan.grp_tile0;
+    f.plan_scalars = a.plan.scalars;
+    f.cl_off = a.plan.cl_off;
+    f.cl_joff = a.plan.cl_joff;
+    f.cl_eps2 = a.plan.cl_eps2;
     void* args[] = {&f};
     return cudaLaunchKernel(fn, dim3(a.grid), dim3(FORCE_WARPS * 32), args,
                             force_smem_bytes(a.prec), s);

@@ -4,6 +4,7 @@
 // interpolation, corrector, a0 <- a1, Aarseth timestep in powers of two),
 // the first timesteps and the energy diagnostic.
 #include <cfloat>
+#include <math_constants.h>
 #include <cstring>
 
 #include "nb_device.cuh"
@@ -30,15 +31,19 @@ __device__ __forceinline__ double dkey_decode(unsigned long long k)
 template <int PREC>
 __global__ void predict_kernel(const StateDev st, const JLayout jl, const double G,
                                const unsigned long long* t_bits, const double t_host,
-                               const int32_t* n_act_dev)
+                               const int32_t* n_act_dev, const int32_t* jsrc,
+                               const int32_t* cluster_of)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= st.n_pad) return;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // j-layout slot
+    if (q >= st.n_pad) return;
     if (n_act_dev && *n_act_dev == 0) return;
     const int64_t n = st.n;
+    // particle in this slot (-1: a ghost that pads its system to the tile)
+    const int64_t i = jsrc ? jsrc[q] : (q < n ? q : -1);
     double xp[3], vp[3], gm;
-    if (i < n) {
-        const double t = t_bits ? dkey_decode(*t_bits) : t_host;
+    if (i >= 0) {
+        const double t =
+            t_bits ? dkey_decode(t_bits[cluster_of ? cluster_of[i] : 0]) : t_host;
         const double h = t - st.t[i];
         gm = G * st.m[i];
 #pragma unroll
@@ -54,8 +59,8 @@ __global__ void predict_kernel(const StateDev st, const JLayout jl, const double
         gm = 0.0;
     }
     if (PREC == static_cast<int>(Prec::FP64)) {
-        double2* P = static_cast<double2*>(jl.arr[0]) + 2 * i;
-        double2* V = static_cast<double2*>(jl.arr[1]) + 2 * i;
+        double2* P = static_cast<double2*>(jl.arr[0]) + 2 * q;
+        double2* V = static_cast<double2*>(jl.arr[1]) + 2 * q;
         P[0] = make_double2(xp[0], xp[1]);
         P[1] = make_double2(xp[2], gm);
         V[0] = make_double2(vp[0], vp[1]);
@@ -68,11 +73,11 @@ __global__ void predict_kernel(const StateDev st, const JLayout jl, const double
             lo[c] = __double2float_rn(xp[c] - static_cast<double>(hi[c]));
         }
         if (PREC == static_cast<int>(Prec::MIXED)) {
-            static_cast<float4*>(jl.arr[0])[i] =
+            static_cast<float4*>(jl.arr[0])[q] =
                 make_float4(hi[0], hi[1], hi[2], __double2float_rn(gm));
-            static_cast<float4*>(jl.arr[1])[i] =
+            static_cast<float4*>(jl.arr[1])[q] =
                 make_float4(lo[0], lo[1], lo[2], __double2float_rn(vp[0]));
-            static_cast<float2*>(jl.arr[2])[i] =
+            static_cast<float2*>(jl.arr[2])[q] =
                 make_float2(__double2float_rn(vp[1]), __double2float_rn(vp[2]));
         } else {
             const float gh = __double2float_rn(gm);
@@ -83,30 +88,32 @@ __global__ void predict_kernel(const StateDev st, const JLayout jl, const double
                 vh[c] = __double2float_rn(vp[c]);
                 vl[c] = __double2float_rn(vp[c] - static_cast<double>(vh[c]));
             }
-            static_cast<float4*>(jl.arr[0])[i] = make_float4(hi[0], hi[1], hi[2], gh);
-            static_cast<float4*>(jl.arr[1])[i] = make_float4(lo[0], lo[1], lo[2], gl);
-            static_cast<float4*>(jl.arr[2])[i] = make_float4(vh[0], vh[1], vh[2], 0.f);
-            static_cast<float4*>(jl.arr[3])[i] = make_float4(vl[0], vl[1], vl[2], 0.f);
+            static_cast<float4*>(jl.arr[0])[q] = make_float4(hi[0], hi[1], hi[2], gh);
+            static_cast<float4*>(jl.arr[1])[q] = make_float4(lo[0], lo[1], lo[2], gl);
+            static_cast<float4*>(jl.arr[2])[q] = make_float4(vh[0], vh[1], vh[2], 0.f);
+            static_cast<float4*>(jl.arr[3])[q] = make_float4(vl[0], vl[1], vl[2], 0.f);
         }
     }
 }
 
 cudaError_t predict_launch(const StateDev& st, Prec p, const JLayout& jl, double G,
                            const unsigned long long* t_bits, double t_host,
-                           const int32_t* n_act_dev, cudaStream_t s)
+                           const int32_t* n_act_dev, cudaStream_t s, const ClusterDev* cl)
 {
     if (st.n_pad <= 0) return cudaSuccess;
     const int threads = 256;
     const unsigned blocks = static_cast<unsigned>((st.n_pad + threads - 1) / threads);
+    const int32_t* jsrc = cl ? cl->jsrc : nullptr;
+    const int32_t* cof = cl ? cl->cluster_of : nullptr;
     switch (p) {
     case Prec::FP64:
-        predict_kernel<0><<<blocks, threads, 0, s>>>(st, jl, G, t_bits, t_host, n_act_dev);
+        predict_kernel<0><<<blocks, threads, 0, s>>>(st, jl, G, t_bits, t_host, n_act_dev, jsrc, cof);
         break;
     case Prec::MIXED:
-        predict_kernel<1><<<blocks, threads, 0, s>>>(st, jl, G, t_bits, t_host, n_act_dev);
+        predict_kernel<1><<<blocks, threads, 0, s>>>(st, jl, G, t_bits, t_host, n_act_dev, jsrc, cof);
         break;
     case Prec::DS:
-        predict_kernel<2><<<blocks, threads, 0, s>>>(st, jl, G, t_bits, t_host, n_act_dev);
+        predict_kernel<2><<<blocks, threads, 0, s>>>(st, jl, G, t_bits, t_host, n_act_dev, jsrc, cof);
         break;
     }
     return cudaGetLastError();
@@ -146,10 +153,15 @@ __global__ void tmin_kernel(const double* __restrict__ t, const double* __restri
     }
 }
 
+// Particle i is in the block when its system's next time t_next (key in
+// tkeys, per cluster when cluster_of is given) is within t_end and t_i + dt_i
+// equals it.
 __device__ __forceinline__ bool is_active(const double* t, const double* dt, int64_t i,
-                                          double tn)
+                                          const unsigned long long* tkeys,
+                                          const int32_t* cluster_of, double t_end)
 {
-    return t[i] + dt[i] == tn;
+    const double tn = dkey_decode(tkeys[cluster_of ? cluster_of[i] : 0]);
+    return tn <= t_end && t[i] + dt[i] == tn;
 }
 
 // Block-wide exclusive scan of one int per thread (SCHED_THREADS threads).
@@ -183,18 +195,15 @@ __device__ int block_exclusive_scan(int v, int* total)
 
 __global__ void __launch_bounds__(SCHED_THREADS)
     count_kernel(const double* __restrict__ t, const double* __restrict__ dt, int64_t n,
-                 const unsigned long long* tmin_bits, double t_end, SchedDev sd)
+                 const unsigned long long* tkeys, const int32_t* cluster_of, double t_end,
+                 SchedDev sd)
 {
-    const double tn = dkey_decode(*tmin_bits);
-    const bool live = tn <= t_end;
     int c = 0;
     const int64_t base = (int64_t)blockIdx.x * SCHED_CHUNK + (int64_t)threadIdx.x * SCHED_PER_THREAD;
-    if (live) {
 #pragma unroll
-        for (int e = 0; e < SCHED_PER_THREAD; ++e) {
-            const int64_t i = base + e;
-            if (i < n && is_active(t, dt, i, tn)) ++c;
-        }
+    for (int e = 0; e < SCHED_PER_THREAD; ++e) {
+        const int64_t i = base + e;
+        if (i < n && is_active(t, dt, i, tkeys, cluster_of, t_end)) ++c;
     }
     int total;
     block_exclusive_scan(c, &total);
@@ -226,17 +235,16 @@ __global__ void __launch_bounds__(SCHED_THREADS)
 
 __global__ void __launch_bounds__(SCHED_THREADS)
     scatter_kernel(const double* __restrict__ t, const double* __restrict__ dt, int64_t n,
-                   const unsigned long long* tmin_bits, double t_end, SchedDev sd)
+                   const unsigned long long* tkeys, const int32_t* cluster_of, double t_end,
+                   SchedDev sd)
 {
-    const double tn = dkey_decode(*tmin_bits);
-    if (!(tn <= t_end)) return;
     const int64_t base = (int64_t)blockIdx.x * SCHED_CHUNK + (int64_t)threadIdx.x * SCHED_PER_THREAD;
     unsigned flags = 0;
     int c = 0;
 #pragma unroll
     for (int e = 0; e < SCHED_PER_THREAD; ++e) {
         const int64_t i = base + e;
-        if (i < n && is_active(t, dt, i, tn)) {
+        if (i < n && is_active(t, dt, i, tkeys, cluster_of, t_end)) {
             flags |= 1u << e;
             ++c;
         }
@@ -258,8 +266,147 @@ cudaError_t select_launch(const StateDev& st, const SchedDev& sd, double t_end, 
     const int nb = static_cast<int>(nb64);
     int tb = nb < 1024 ? nb : 1024;
     tmin_kernel<<<tb, 256, 0, s>>>(st.t, st.dt, st.n, sd.tmin_bits);
-    count_kernel<<<nb, SCHED_THREADS, 0, s>>>(st.t, st.dt, st.n, sd.tmin_bits, t_end, sd);
-    scatter_kernel<<<nb, SCHED_THREADS, 0, s>>>(st.t, st.dt, st.n, sd.tmin_bits, t_end, sd);
+    count_kernel<<<nb, SCHED_THREADS, 0, s>>>(st.t, st.dt, st.n, sd.tmin_bits, nullptr, t_end, sd);
+    scatter_kernel<<<nb, SCHED_THREADS, 0, s>>>(st.t, st.dt, st.n, sd.tmin_bits, nullptr, t_end, sd);
+    return cudaGetLastError();
+}
+
+// Ensemble step 1: block c finds the next time of cluster c.
+__global__ void cluster_tmin_kernel(const double* __restrict__ t, const double* __restrict__ dt,
+                                    const int64_t* off, unsigned long long* tkey)
+{
+    const int c = blockIdx.x;
+    unsigned long long best = ~0ull;
+    for (int64_t i = off[c] + threadIdx.x; i < off[c + 1]; i += blockDim.x) {
+        const unsigned long long k = dkey(t[i] + dt[i]);
+        best = k < best ? k : best;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+        best = other < best ? other : best;
+    }
+    __shared__ unsigned long long wbest[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) wbest[wid] = best;
+    __syncthreads();
+    if (wid == 0) {
+        best = lane < (int)(blockDim.x >> 5) ? wbest[lane] : ~0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+            best = other < best ? other : best;
+        }
+        if (lane == 0) tkey[c] = best;
+    }
+}
+
+cudaError_t cluster_select_launch(const StateDev& st, const ClusterDev& cl, const SchedDev& sd,
+                                  double t_end, cudaStream_t s)
+{
+    if (st.n <= 0 || cl.k <= 0) return cudaMemsetAsync(sd.n_act, 0, sizeof(int32_t), s);
+    const int64_t nb64 = (st.n + SCHED_CHUNK - 1) / SCHED_CHUNK;
+    if (nb64 > sd.max_blocks) return cudaErrorInvalidValue;
+    const int nb = static_cast<int>(nb64);
+    cluster_tmin_kernel<<<cl.k, 256, 0, s>>>(st.t, st.dt, cl.off, cl.tkey);
+    count_kernel<<<nb, SCHED_THREADS, 0, s>>>(st.t, st.dt, st.n, cl.tkey, cl.cluster_of, t_end, sd);
+    scatter_kernel<<<nb, SCHED_THREADS, 0, s>>>(st.t, st.dt, st.n, cl.tkey, cl.cluster_of, t_end, sd);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Ensemble force plan: the active list (ascending, so each cluster's block
+// is contiguous) cut into i-groups of at most gi entries that never mix
+// clusters, each with its cluster's j tiles, laid end to end.  One CTA.
+// ---------------------------------------------------------------------------
+constexpr int PLAN_THREADS = 1024;
+
+__device__ int64_t lower_bound_i32(const int32_t* a, int64_t n, int64_t x)
+{
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Block-wide exclusive scan of one int64 per thread (PLAN_THREADS threads).
+__device__ int64_t plan_scan(int64_t v, int64_t* total)
+{
+    __shared__ int64_t ws[PLAN_THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t z = lane < PLAN_THREADS / 32 ? ws[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, z, o);
+            if (lane >= o) z += y;
+        }
+        if (lane < PLAN_THREADS / 32) ws[lane] = z;
+    }
+    __syncthreads();
+    const int64_t before = wid > 0 ? ws[wid - 1] : 0;
+    *total = ws[PLAN_THREADS / 32 - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(PLAN_THREADS)
+    plan_kernel(const ClusterDev cl, const int32_t* idx, const int32_t* n_act_dev, int gi)
+{
+    const int64_t n_act = *n_act_dev;
+    const int K = cl.k;
+    const int per = (K + PLAN_THREADS - 1) / PLAN_THREADS;
+    const int c0 = threadIdx.x * per;
+    const int c1 = c0 + per < K ? c0 + per : K;
+    int64_t gsum = 0, tsum = 0;
+    for (int c = c0; c < c1; ++c) {
+        const int64_t b = lower_bound_i32(idx, n_act, cl.off[c]);
+        const int64_t e = lower_bound_i32(idx, n_act, cl.off[c + 1]);
+        const int64_t gc = (e - b + gi - 1) / gi;
+        gsum += gc;
+        tsum += gc * ((cl.joff[c + 1] - cl.joff[c]) / TJ);
+    }
+    int64_t G, T;
+    int64_t gbase = plan_scan(gsum, &G);
+    int64_t tbase = plan_scan(tsum, &T);
+    if (G > cl.max_groups) {  // cannot happen for a sorted active list
+        if (threadIdx.x == 0) cl.plan_scalars[0] = cl.plan_scalars[1] = 0;
+        return;
+    }
+    for (int c = c0; c < c1; ++c) {
+        const int64_t b = lower_bound_i32(idx, n_act, cl.off[c]);
+        const int64_t e = lower_bound_i32(idx, n_act, cl.off[c + 1]);
+        const int64_t nt = (cl.joff[c + 1] - cl.joff[c]) / TJ;
+        for (int64_t a = b; a < e; a += gi) {
+            cl.grp_cluster[gbase] = c;
+            cl.grp_act_begin[gbase] = static_cast<int32_t>(a);
+            cl.grp_act_count[gbase] = static_cast<int32_t>(e - a < gi ? e - a : gi);
+            cl.grp_tile0[gbase] = tbase;
+            ++gbase;
+            tbase += nt;
+        }
+    }
+    if (threadIdx.x == 0) {
+        cl.grp_tile0[G] = T;
+        cl.plan_scalars[0] = G;
+        cl.plan_scalars[1] = T;
+    }
+}
+
+cudaError_t plan_launch(const ClusterDev& cl, const int32_t* idx, const int32_t* n_act_dev,
+                        int gi, cudaStream_t s)
+{
+    plan_kernel<<<1, PLAN_THREADS, 0, s>>>(cl, idx, n_act_dev, gi);
     return cudaGetLastError();
 }
 
@@ -289,11 +436,27 @@ __global__ void correct_kernel(const StateDev st, const CorrectArgs c)
 {
     const int n_act = *c.n_act_dev;
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k == 0 && n_act > 0) {
-        if (c.step_counter) atomicAdd(c.step_counter, 1ull);
-        if (c.inter_counter)
-            atomicAdd(c.inter_counter,
-                      static_cast<unsigned long long>(n_act) * static_cast<unsigned long long>(st.n));
+    if (k == 0 && n_act > 0 && c.step_counter) atomicAdd(c.step_counter, 1ull);
+    if (c.inter_counter) {
+        // interactions: n_act * n for one system; each active particle adds
+        // its own system's size in an ensemble (summed per warp)
+        if (!c.cluster_of) {
+            if (k == 0 && n_act > 0)
+                atomicAdd(c.inter_counter, static_cast<unsigned long long>(n_act) *
+                                               static_cast<unsigned long long>(st.n));
+        } else {
+            unsigned long long mine = 0;
+            if (k < n_act) {
+                const int64_t i = c.idx[k];
+                if (i >= 0 && i < st.n) {
+                    const int cc = c.cluster_of[i];
+                    mine = static_cast<unsigned long long>(c.cl_off[cc + 1] - c.cl_off[cc]);
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+            if ((threadIdx.x & 31) == 0 && mine) atomicAdd(c.inter_counter, mine);
+        }
     }
     if (k >= n_act) return;
     const int64_t n = st.n;
@@ -302,7 +465,7 @@ __global__ void correct_kernel(const StateDev st, const CorrectArgs c)
         atomicOr(c.status, ST_BADINDEX);
         return;
     }
-    const double tn = dkey_decode(*c.t_bits);
+    const double tn = dkey_decode(c.t_bits[c.cluster_of ? c.cluster_of[i] : 0]);
     const double h = st.dt[i];
     if (DADD(st.t[i], h) != tn) {
         atomicOr(c.status, ST_NOTDUE);
@@ -357,8 +520,10 @@ __global__ void correct_kernel(const StateDev st, const CorrectArgs c)
     const double J = norm3_rn(j1[0], j1[1], j1[2]);
     const double S = norm3_rn(sn[0], sn[1], sn[2]);
     const double C = norm3_rn(c0[0], c0[1], c0[2]);
-    const double dta = DMUL(c.eta, __dsqrt_rn(DDIV(DADD(DMUL(A, S), DMUL(J, J)),
-                                                   DADD(DMUL(J, C), DMUL(S, S)))));
+    // a zero denominator (a particle that feels nothing) sets no constraint
+    const double den = DADD(DMUL(J, C), DMUL(S, S));
+    const double dta = den == 0.0 ? CUDART_INF
+                                  : DMUL(c.eta, __dsqrt_rn(DDIV(DADD(DMUL(A, S), DMUL(J, J)), den)));
     if (isnan(dta)) {
         atomicOr(c.status, ST_NONFINITE);
         return;
@@ -394,7 +559,7 @@ __global__ void init_dt_kernel(const StateDev st, const double* acc, const doubl
     if (i >= st.n) return;
     const double A = norm3_rn(acc[3 * i], acc[3 * i + 1], acc[3 * i + 2]);
     const double J = norm3_rn(jerk[3 * i], jerk[3 * i + 1], jerk[3 * i + 2]);
-    double raw = DDIV(DMUL(eta_start, A), J);
+    double raw = J == 0.0 ? CUDART_INF : DDIV(DMUL(eta_start, A), J);
     st.t[i] = t0;
     if (isnan(raw)) {
         atomicOr(status, ST_NONFINITE);
@@ -506,6 +671,43 @@ double time_from_key(unsigned long long k)
     static_assert(sizeof(x) == sizeof(b), "double is 64-bit");
     memcpy(&x, &b, sizeof(x));
     return x;
+}
+
+// Per-cluster energies (block c sums cluster c in a fixed order).
+__global__ void cluster_energy_kernel(const StateDev st, const int64_t* off, const double* pot_all,
+                                      double* out)
+{
+    __shared__ double sk[256], sw[256];
+    const int c = blockIdx.x;
+    const int64_t n = st.n;
+    double k = 0.0, w = 0.0;
+    for (int64_t i = off[c] + threadIdx.x; i < off[c + 1]; i += blockDim.x) {
+        const double vx = st.v[i], vy = st.v[n + i], vz = st.v[2 * n + i];
+        k += 0.5 * st.m[i] * (vx * vx + vy * vy + vz * vz);
+        w += 0.5 * st.m[i] * pot_all[i];
+    }
+    sk[threadIdx.x] = k;
+    sw[threadIdx.x] = w;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            sk[threadIdx.x] += sk[threadIdx.x + o];
+            sw[threadIdx.x] += sw[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[2 * c] = sk[0];
+        out[2 * c + 1] = sw[0];
+    }
+}
+
+cudaError_t cluster_energy_launch(const StateDev& st, const ClusterDev& cl, const double* pot_all,
+                                  double* out, cudaStream_t s)
+{
+    if (cl.k <= 0) return cudaSuccess;
+    cluster_energy_kernel<<<cl.k, 256, 0, s>>>(st, cl.off, pot_all, out);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

@@ -57,6 +57,38 @@ constexpr int SCHED_THREADS = 256;
 constexpr int SCHED_PER_THREAD = 8;
 constexpr int SCHED_CHUNK = SCHED_THREADS * SCHED_PER_THREAD;
 
+// Ensemble of independent systems ("clusters") in one context.  Cluster c
+// owns particles [off[c], off[c+1]) and j-layout slots [joff[c], joff[c+1])
+// (its particles, then zero-mass ghosts up to a multiple of the tile).
+struct ClusterDev {
+    int k = 0;
+    int64_t* off = nullptr;          // k + 1
+    int64_t* joff = nullptr;         // k + 1
+    double* eps2 = nullptr;          // k
+    int32_t* cluster_of = nullptr;   // n: cluster of each particle
+    int32_t* jsrc = nullptr;         // n_pad: particle of each j slot, -1 = ghost
+    unsigned long long* tkey = nullptr;  // k: next block time of each cluster (key)
+    // force plan written by plan_launch
+    int32_t* grp_cluster = nullptr;
+    int32_t* grp_act_begin = nullptr;
+    int32_t* grp_act_count = nullptr;
+    int64_t* grp_tile0 = nullptr;    // max_groups + 1
+    int64_t* plan_scalars = nullptr; // [0] groups, [1] tiles
+    int64_t max_groups = 0;
+};
+
+// Force plan arrays handed to the kernel (all null for one system).
+struct ForcePlan {
+    const int32_t* grp_cluster = nullptr;
+    const int32_t* grp_act_begin = nullptr;
+    const int32_t* grp_act_count = nullptr;
+    const int64_t* grp_tile0 = nullptr;
+    const int64_t* scalars = nullptr;
+    const int64_t* cl_off = nullptr;
+    const int64_t* cl_joff = nullptr;
+    const double* cl_eps2 = nullptr;
+};
+
 // Force launch (step 4): active list -> acc, jerk, pot.
 struct ForceArgs {
     Prec prec = Prec::MIXED;
@@ -75,6 +107,7 @@ struct ForceArgs {
     uint32_t* status = nullptr;
     double eps2 = 0.0;
     int grid = 0;        // CTAs (persistent)
+    ForcePlan plan;      // ensemble plan (empty: one system)
 };
 
 cudaError_t force_setup(Prec p, int it);  // one-time attribute setup
@@ -90,11 +123,23 @@ int64_t force_counter_stride(int64_t n_act_max, int warps);
 int64_t force_counter_entries(int64_t n_act_max, int warps);
 cudaError_t force_launch(const ForceArgs& f, cudaStream_t s);
 
-// Predictor (steps 2-3) to the time in *t_bits (if non-null) else t_host.
-// With n_act_dev non-null nothing is done when *n_act_dev == 0.
+// Predictor (steps 2-3) to the time in t_bits (per cluster when cl is
+// given, else t_bits[0]) or, with t_bits null, to t_host.  With n_act_dev
+// non-null nothing is done when *n_act_dev == 0.
 cudaError_t predict_launch(const StateDev& st, Prec p, const JLayout& jl, double G,
                            const unsigned long long* t_bits, double t_host,
-                           const int32_t* n_act_dev, cudaStream_t s);
+                           const int32_t* n_act_dev, cudaStream_t s,
+                           const ClusterDev* cl = nullptr);
+
+// Ensemble step 1 (per-cluster next times, then one global compaction) and
+// the force plan of the active list (idx ascending, clusters contiguous).
+cudaError_t cluster_select_launch(const StateDev& st, const ClusterDev& cl, const SchedDev& sd,
+                                  double t_end, cudaStream_t s);
+cudaError_t plan_launch(const ClusterDev& cl, const int32_t* idx, const int32_t* n_act_dev,
+                        int gi, cudaStream_t s);
+// Per-cluster energies: out[2c] = sum 1/2 m v^2, out[2c+1] = sum 1/2 m phi.
+cudaError_t cluster_energy_launch(const StateDev& st, const ClusterDev& cl, const double* pot_all,
+                                  double* out, cudaStream_t s);
 
 // Stream-ordered scalar stores: *i32 = v (if i32), *t_bits = key(t) (if t_bits).
 cudaError_t set_scalars_launch(int32_t* i32, int32_t v, unsigned long long* t_bits,
@@ -117,7 +162,9 @@ struct CorrectArgs {
     double eta = 0.02, dt_max = 1.0 / 16, dt_min = 0x1p-40;
     uint32_t* status = nullptr;
     unsigned long long* step_counter = nullptr;   // +1 per non-empty block
-    unsigned long long* inter_counter = nullptr;  // += n_act * n
+    unsigned long long* inter_counter = nullptr;  // += n_act * n (per cluster)
+    const int32_t* cluster_of = nullptr;          // ensemble: t_bits per cluster
+    const int64_t* cl_off = nullptr;
 };
 cudaError_t correct_launch(const StateDev& st, const CorrectArgs& c, cudaStream_t s);
 

@@ -76,6 +76,9 @@ def load(path: str = LIB_PATH):
         "nb_status_string": (c_char_p, [c_int32]),
         "nb_force_static": (c_int32, [c_int64, P, P, P, c_double, c_double, c_int32, P, P, P,
                                       P, P]),
+        "nb_set_ensemble": (c_int32, [P, c_int32, P, P, P, P, P, c_double]),
+        "nb_energy_systems": (c_int32, [P, c_int32, P, P]),
+        "nb_num_systems": (c_int32, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -172,6 +175,18 @@ def nb_status_string(st: int) -> str:
     return load().nb_status_string(st).decode()
 
 
+def nb_set_ensemble(ctx, k, offsets, m, r, v, eps, eta):
+    return load().nb_set_ensemble(ctx, k, offsets, m, r, v, eps, eta)
+
+
+def nb_energy_systems(ctx, fp64_potential, kin, pot):
+    return load().nb_energy_systems(ctx, fp64_potential, kin, pot)
+
+
+def nb_num_systems(ctx) -> int:
+    return load().nb_num_systems(ctx)
+
+
 def nb_force_static(n, m, r, v, eps, G, n_act, idx, acc, jerk, pot, stream):
     """Allocation-free force evaluation on device pointers (see nbody.h)."""
     return load().nb_force_static(n, m, r, v, eps, G, n_act, idx, acc, jerk, pot, stream)
@@ -266,6 +281,28 @@ class Context:
         p = {k: out[k].ctypes.data_as(c_void_p) for k in out}
         self._ck(nb_get_state(self.handle, p["r"], p["v"], p["a"], p["j"], p["t"], p["dt"], 0))
         return out
+
+    def set_ensemble(self, offsets, m, r, v, eps, eta):
+        """k independent systems: system q is [offsets[q], offsets[q+1])."""
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        k = len(off) - 1
+        n = int(off[-1])
+        pm, km, _ = _ptr(m, np.float64)
+        pr, kr, _ = _ptr(r, np.float64, (n, 3))
+        pv, kv, _ = _ptr(v, np.float64, (n, 3))
+        pe, ke, _ = _ptr(eps, np.float64)
+        self._ck(nb_set_ensemble(self.handle, k, off.ctypes.data_as(c_void_p), pm, pr, pv, pe,
+                                 float(eta)))
+        self.n = n
+        self.k = k
+
+    def energy_systems(self, fp64_potential=True):
+        k = nb_num_systems(self.handle)
+        kin = np.empty(k)
+        pot = np.empty(k)
+        self._ck(nb_energy_systems(self.handle, int(bool(fp64_potential)),
+                                   kin.ctypes.data_as(c_void_p), pot.ctypes.data_as(c_void_p)))
+        return kin, pot
 
     def predict(self, t):
         self._ck(nb_predict(self.handle, float(t)))

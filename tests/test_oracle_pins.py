@@ -258,6 +258,18 @@ def test_initial_dt_power_of_two(orc):
     assert dt == 1 / 16
 
 
+def test_isolated_particle_steps_at_dt_max(orc):
+    """Reading R5: a particle that feels nothing (a = j = s = c = 0) has no
+    timestep constraint; a one-particle system moves in a straight line."""
+    z = np.zeros(3)
+    assert orc.aarseth_dt(0.02, z, z, z, z) == float("inf")
+    st, dt = orc.initial_dt(0.01, z, z, 1 / 16)
+    assert st == 0 and dt == 1 / 16
+    s = orc.State([1.0], [[0.5, 0.0, 0.0]], [[0.25, -1.0, 2.0]], 0.0, 0.02)
+    assert s.run(1.0) == 0 and s.n_steps == 16
+    np.testing.assert_allclose(s.r[0], [0.75, -1.0, 2.0], rtol=0, atol=1e-15)
+
+
 def test_select_against_brute_force(orc):
     rng = np.random.default_rng(8)
     n = 500
