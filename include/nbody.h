@@ -61,12 +61,39 @@ typedef struct nb_config {
     double dt_min;        /* smallest timestep allowed (NB_EDTMIN below it)     */
     void* stream;         /* cudaStream_t to run on; NULL = a private stream    */
     int32_t i_per_thread; /* force kernel register blocking; 0 = default        */
-    int32_t ctas_per_sm;  /* persistent force CTAs per SM; 0 = from occupancy   */
+    int32_t ctas_per_sm;  /* persistent force CTAs per SM; 0 = default          */
+    int32_t autotune;     /* 1: run nb_autotune after every load                */
 } nb_config;
 
 /* Fill *cfg with the defaults: NB_MIXED, device 0, G = 1, eta_start = 0.01,
- * dt_max = 1/16, dt_min = 2^-40, private stream, automatic launch shape. */
+ * dt_max = 1/16, dt_min = 2^-40, private stream, default launch shapes, no
+ * autotuning. */
 void nb_config_init(nb_config* cfg);
+
+/* Launch shapes of the force kernel (SURVEY's i-tile / j-split): blocks of
+ * fewer than nact_split active particles use the "small" shape, others the
+ * "large" one.  i_per_thread is the i-tile per lane (an i-group is 32 times
+ * that); ctas_per_sm sets the persistent grid, which fixes how far each
+ * i-group's j range is split across warps.  The *_us fields give the force
+ * time the autotuner measured for the chosen shapes on its probe blocks. */
+typedef struct nb_tuning {
+    int32_t small_i_per_thread;
+    int32_t small_ctas_per_sm;
+    int32_t large_i_per_thread;
+    int32_t large_ctas_per_sm;
+    int32_t nact_split;
+    double small_us;
+    double large_us;
+} nb_tuning;
+
+/* Autotuner: time every candidate launch shape of the force kernel on the
+ * loaded system (probe blocks of 32 and 256 particles for "small", 2048 and
+ * min(n, 16384) for "large"; the first particles by index) and keep the
+ * fastest for each bucket.  Predicts all particles to the time of particle
+ * 0 first, so call nb_predict again before nb_force.  *out (may be NULL)
+ * receives the choice.  Blocks.  Errors: NB_ESTATE (nothing loaded),
+ * NB_ECUDA. */
+nb_status nb_autotune(nb_ctx* ctx, nb_tuning* out);
 
 /* Create a context on cfg->device.  *out receives the handle.
  * Errors: NB_EINVAL (NULL pointer, dt_max not a power of two, unknown

@@ -24,9 +24,16 @@ struct nb_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int num_sms = 0;
-    int it = 1;          // i particles per thread in the context precision
-    int grid = 0;        // persistent force CTAs, context precision
-    int grid64 = 0;      // the same for the FP64 energy pass
+    // Force launch variants of the context precision: [0] for blocks with
+    // n_act < nact_split, [1] for larger ones (i per thread, persistent CTAs).
+    struct Variant {
+        int it = 1;
+        int grid = 0;
+    } var[2];
+    int32_t nact_split = 1024;
+    int grid64 = 0;      // persistent CTAs of the FP64 energy pass (1 i per thread)
+    size_t scratch_cap = 0;    // doubles allocated for split-group partials
+    int64_t counter_cap = 0;   // counter words allocated
     int64_t n = 0, n_pad = 0, cap = 0;
     double eps = 0.0, eta = 0.02;
     nb::StateDev st;
@@ -142,6 +149,43 @@ nb_status alloc_layout(nb_ctx* c, Prec p, nb::JLayout& jl, int64_t n_pad)
     return NB_OK;
 }
 
+// Scratch for the split-group partials and reduction counters, enough for
+// the launch variants with the given grids (and the FP64 energy pass) on up
+// to cap particles in cap_k systems.  Grows only; drops the step graph when
+// the buffers move.
+nb_status ensure_force_scratch(nb_ctx* c, int grid0, int grid1)
+{
+    const int64_t n = c->cap, k = c->cap_k;
+    const int64_t groups_bound = n + 32 * k;  // i-groups never mix systems
+    size_t need = nb::force_scratch_doubles(1, groups_bound, c->grid64 * nb::FORCE_WARPS);
+    int max_grid = c->grid64;
+    const int grids[2] = {grid0, grid1};
+    for (int v = 0; v < 2; ++v) {
+        const int it = c->var[v].it;
+        need = std::max(need, nb::force_scratch_doubles(it, groups_bound + 32 * it * k,
+                                                        grids[v] * nb::FORCE_WARPS));
+        max_grid = std::max(max_grid, grids[v]);
+    }
+    const int64_t stride = nb::force_counter_stride(groups_bound, max_grid * nb::FORCE_WARPS);
+    const int64_t words = nb::force_counter_entries(groups_bound, max_grid * nb::FORCE_WARPS);
+    if (need > c->scratch_cap) {
+        dfree(c->scratch);
+        NB_CK(c, cudaMalloc(&c->scratch, need * sizeof(double)));
+        c->scratch_cap = need;
+        drop_graph(c);
+    }
+    if (words > c->counter_cap) {
+        dfree(c->counters);
+        NB_CK(c, cudaMalloc(&c->counters, words * sizeof(uint32_t)));
+        NB_CK(c, cudaMemset(c->counters, 0, words * sizeof(uint32_t)));
+        c->counter_cap = words;
+        drop_graph(c);
+    }
+    c->counter_stride = stride;
+    c->counter_words = words;
+    return NB_OK;
+}
+
 // Size every n-dependent buffer for n particles in k systems (k = 0: one
 // system without cluster arrays) whose j layout has n_pad slots.
 nb_status ensure_capacity(nb_ctx* c, int64_t n, int64_t n_pad, int64_t k)
@@ -186,16 +230,9 @@ nb_status ensure_capacity(nb_ctx* c, int64_t n, int64_t n_pad, int64_t k)
     NB_CK(c, cudaMalloc(&c->jerk1, 3 * n * d));
     NB_CK(c, cudaMalloc(&c->pot1, n * d));
     NB_CK(c, cudaMalloc(&c->staging, 3 * n * d));
-    // Scratch for the split-group partials of both force precisions.
-    const size_t s1 = nb::force_scratch_doubles(c->it, groups_bound + 32 * c->it * k,
-                                                c->grid * nb::FORCE_WARPS);
-    const size_t s2 = nb::force_scratch_doubles(1, groups_bound, c->grid64 * nb::FORCE_WARPS);
-    NB_CK(c, cudaMalloc(&c->scratch, (s1 > s2 ? s1 : s2) * d));
-    const int max_warps = nb::FORCE_WARPS * std::max(c->grid, c->grid64);
-    c->counter_stride = nb::force_counter_stride(groups_bound, max_warps);
-    c->counter_words = nb::force_counter_entries(groups_bound, max_warps);
-    NB_CK(c, cudaMalloc(&c->counters, c->counter_words * sizeof(uint32_t)));
-    NB_CK(c, cudaMemset(c->counters, 0, c->counter_words * sizeof(uint32_t)));
+    c->scratch_cap = 0;
+    c->counter_cap = 0;
+    (void)groups_bound;
     c->energy_blocks = static_cast<int>(std::min<int64_t>((n + 255) / 256, 1024));
     NB_CK(c, cudaMalloc(&c->energy_partials, 2 * c->energy_blocks * d));
     NB_CK(c, cudaMalloc(&c->energy_out, 2 * d));
@@ -221,6 +258,8 @@ nb_status ensure_capacity(nb_ctx* c, int64_t n, int64_t n_pad, int64_t k)
     c->cap_pad = n_pad;
     c->cap_k = k;
     c->cap = n;
+    s = ensure_force_scratch(c, c->var[0].grid, c->var[1].grid);
+    if (s != NB_OK) return s;
     c->n = n;
     c->n_pad = n_pad;
     c->st.n = n;
@@ -260,12 +299,40 @@ nb_status check_status(nb_ctx* c)
     return fail(c, NB_ECUDA, "unknown device status 0x%x", st);
 }
 
+// Force on the active list idx[0..*n_act_dev).  In the context precision the
+// two launch variants go out back to back, each working only inside its
+// n_act window (the block size is read on the device); when the caller
+// knows n_act (n_act_host >= 0) only the matching variant is launched.
+nb::ForceArgs force_args(nb_ctx* c, Prec p, const nb::JLayout& jl, const int32_t* idx,
+                         const int32_t* n_act_dev);
+
 nb_status run_force(nb_ctx* c, Prec p, const nb::JLayout& jl, const int32_t* idx,
-                    const int32_t* n_act_dev)
+                    const int32_t* n_act_dev, int32_t n_act_host = -1)
+{
+    nb::ForceArgs f = force_args(c, p, jl, idx, n_act_dev);
+    if (p != c->prec) {  // the FP64 energy pass of a lower-precision context
+        f.it = 1;
+        f.grid = c->grid64;
+        NB_CK(c, nb::force_launch(f, c->stream));
+        return NB_OK;
+    }
+    for (int v = 0; v < 2; ++v) {
+        f.it = c->var[v].it;
+        f.grid = c->var[v].grid;
+        f.nact_lo = v == 0 ? 0 : c->nact_split;
+        f.nact_hi = v == 0 ? c->nact_split : 0x7fffffff;
+        if (n_act_host >= 0 && (n_act_host < f.nact_lo || n_act_host >= f.nact_hi)) continue;
+        NB_CK(c, nb::force_launch(f, c->stream));
+    }
+    return NB_OK;
+}
+
+// Launch arguments shared by every force launch of the context.
+nb::ForceArgs force_args(nb_ctx* c, Prec p, const nb::JLayout& jl, const int32_t* idx,
+                         const int32_t* n_act_dev)
 {
     nb::ForceArgs f;
     f.prec = p;
-    f.it = p == c->prec ? c->it : 1;
     f.jl = jl;
     f.n = c->n;
     f.n_pad = c->n_pad;
@@ -279,7 +346,6 @@ nb_status run_force(nb_ctx* c, Prec p, const nb::JLayout& jl, const int32_t* idx
     f.counter_stride = c->counter_stride;
     f.status = c->status_dev;
     f.eps2 = c->eps * c->eps;
-    f.grid = p == c->prec ? c->grid : c->grid64;
     if (c->ens) {
         // the plan for this active list must have been written by plan_launch
         f.plan.grp_cluster = c->cl.grp_cluster;
@@ -291,19 +357,19 @@ nb_status run_force(nb_ctx* c, Prec p, const nb::JLayout& jl, const int32_t* idx
         f.plan.cl_joff = c->cl.joff;
         f.plan.cl_eps2 = c->cl.eps2;
     }
-    NB_CK(c, nb::force_launch(f, c->stream));
-    return NB_OK;
+    return f;
 }
 
 // Force on a sorted active list: in ensemble mode the plan comes first.
 nb_status run_force_list(nb_ctx* c, Prec p, const nb::JLayout& jl, const int32_t* idx,
-                         const int32_t* n_act_dev)
+                         const int32_t* n_act_dev, int32_t n_act_host = -1)
 {
     if (c->ens) {
-        const int gi = 32 * (p == c->prec ? c->it : 1);
+        // both variants of an ensemble context share one i per thread
+        const int gi = 32 * (p == c->prec ? c->var[0].it : 1);
         NB_CK(c, nb::plan_launch(c->cl, idx, n_act_dev, gi, c->stream));
     }
-    return run_force(c, p, jl, idx, n_act_dev);
+    return run_force(c, p, jl, idx, n_act_dev, n_act_host);
 }
 
 nb_status upload_vec3(nb_ctx* c, const double* src, double* dst_soa, int on_device)
@@ -432,6 +498,7 @@ void nb_config_init(nb_config* cfg)
     cfg->stream = nullptr;
     cfg->i_per_thread = 0;
     cfg->ctas_per_sm = 0;
+    cfg->autotune = 0;
 }
 
 nb_status nb_create(const nb_config* cfg, nb_ctx** out)
@@ -460,15 +527,21 @@ nb_status nb_create(const nb_config* cfg, nb_ctx** out)
             return bail(NB_ECUDA);
         c->own_stream = true;
     }
-    int it = cfg->i_per_thread;
-    if (it == 0) it = c->prec == Prec::MIXED ? 2 : 1;
-    if (!nb::force_variant_exists(c->prec, it)) return bail(NB_EINVAL);
-    c->it = it;
-    if (nb::force_setup(c->prec, it) != cudaSuccess) return bail(NB_ECUDA);
+    // Default launch shapes (measured on GB300 for N = 16384): one i per
+    // thread for small blocks, two for large MIXED blocks; at most 4
+    // persistent CTAs per SM.  nb_autotune replaces them by measurement.
+    for (int v = 0; v < 2; ++v) {
+        int it = cfg->i_per_thread;
+        if (it == 0) it = (v == 1 && c->prec == Prec::MIXED) ? 2 : 1;
+        if (!nb::force_variant_exists(c->prec, it)) return bail(NB_EINVAL);
+        if (nb::force_setup(c->prec, it) != cudaSuccess) return bail(NB_ECUDA);
+        const int occ = nb::force_ctas_per_sm(c->prec, it);
+        if (occ < 1) return bail(NB_ECUDA);
+        const int per_sm = cfg->ctas_per_sm > 0 ? cfg->ctas_per_sm : std::min(occ, 4);
+        c->var[v].it = it;
+        c->var[v].grid = per_sm * c->num_sms;
+    }
     if (nb::force_setup(Prec::FP64, 1) != cudaSuccess) return bail(NB_ECUDA);
-    int per_sm = cfg->ctas_per_sm > 0 ? cfg->ctas_per_sm : nb::force_ctas_per_sm(c->prec, it);
-    if (per_sm < 1) return bail(NB_ECUDA);
-    c->grid = per_sm * c->num_sms;
     const int per_sm64 = nb::force_ctas_per_sm(Prec::FP64, 1);
     if (per_sm64 < 1) return bail(NB_ECUDA);
     c->grid64 = per_sm64 * c->num_sms;
@@ -512,11 +585,14 @@ nb_status nb_set_particles(nb_ctx* c, int64_t n, const double* m, const double* 
     // Forces on every particle at t = 0, then the first timesteps.
     NB_CK(c, nb::predict_launch(c->st, c->prec, c->jl, c->cfg.G, nullptr, 0.0, nullptr, c->stream));
     NB_CK(c, nb::iota_launch(c->idx_user, n, c->n_act_user, c->stream));
-    if ((s = run_force(c, c->prec, c->jl, c->idx_user, c->n_act_user)) != NB_OK) return s;
+    if ((s = run_force(c, c->prec, c->jl, c->idx_user, c->n_act_user, static_cast<int32_t>(n))) !=
+        NB_OK)
+        return s;
     NB_CK(c, nb::init_dt_launch(c->st, c->acc1, c->jerk1, c->cfg.eta_start, c->cfg.dt_max,
                                 c->cfg.dt_min, 0.0, c->status_dev, c->stream));
     if ((s = check_status(c)) != NB_OK) return s;
     c->loaded = true;
+    if (c->cfg.autotune) return nb_autotune(c, nullptr);
     return NB_OK;
 }
 
@@ -619,7 +695,8 @@ nb_status nb_force(nb_ctx* c, int32_t n_act, const int32_t* idx, double* acc, do
         idx_dev = c->idx_user;
     }
     NB_CK(c, nb::set_scalars_launch(c->n_act_user, n_act, nullptr, 0.0, c->stream));
-    if (n_act > 0 && (s = run_force_list(c, c->prec, c->jl, idx_dev, c->n_act_user)) != NB_OK)
+    if (n_act > 0 &&
+        (s = run_force_list(c, c->prec, c->jl, idx_dev, c->n_act_user, n_act)) != NB_OK)
         return s;
     c->last_force_n_act = n_act;
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -732,7 +809,9 @@ nb_status nb_energy(nb_ctx* c, int32_t fp64_potential, double* kin, double* pot)
     NB_CK(c, nb::predict_launch(c->st, p, jl, c->cfg.G, nullptr, *ht, nullptr, c->stream,
                                 c->ens ? &c->cl : nullptr));
     NB_CK(c, nb::iota_launch(c->idx_user, c->n, c->n_act_user, c->stream));
-    if ((s = run_force_list(c, p, jl, c->idx_user, c->n_act_user)) != NB_OK) return s;
+    if ((s = run_force_list(c, p, jl, c->idx_user, c->n_act_user, static_cast<int32_t>(c->n))) !=
+        NB_OK)
+        return s;
     NB_CK(c, nb::energy_launch(c->st, c->pot1, c->energy_partials, c->energy_blocks,
                                c->energy_out, c->energy_ticket, c->stream));
     if (c->ens)
@@ -793,6 +872,11 @@ nb_status nb_set_ensemble(nb_ctx* c, int32_t k, const int64_t* offsets, const do
     c->ens = true;
     nb_status s = ensure_capacity(c, n, n_pad, k);
     if (s != NB_OK) return s;
+    // the ensemble plan cuts i-groups for one i-per-thread value
+    if (c->var[1].it != c->var[0].it) {
+        c->var[1].it = c->var[0].it;
+        if ((s = ensure_force_scratch(c, c->var[0].grid, c->var[1].grid)) != NB_OK) return s;
+    }
     c->eps = 0.0;  // per system: cl.eps2
     c->eta = eta;
     c->h_off.assign(offsets, offsets + k + 1);
@@ -814,12 +898,15 @@ nb_status nb_set_ensemble(nb_ctx* c, int32_t k, const int64_t* offsets, const do
     NB_CK(c, nb::predict_launch(c->st, c->prec, c->jl, c->cfg.G, nullptr, 0.0, nullptr, c->stream,
                                 &c->cl));
     NB_CK(c, nb::iota_launch(c->idx_user, n, c->n_act_user, c->stream));
-    if ((s = run_force_list(c, c->prec, c->jl, c->idx_user, c->n_act_user)) != NB_OK) return s;
+    if ((s = run_force_list(c, c->prec, c->jl, c->idx_user, c->n_act_user,
+                            static_cast<int32_t>(n))) != NB_OK)
+        return s;
     NB_CK(c, nb::init_dt_launch(c->st, c->acc1, c->jerk1, c->cfg.eta_start, c->cfg.dt_max,
                                 c->cfg.dt_min, 0.0, c->status_dev, c->stream));
     if ((s = check_status(c)) != NB_OK) return s;
     c->last_force_n_act = -1;
     c->loaded = true;
+    if (c->cfg.autotune) return nb_autotune(c, nullptr);
     return NB_OK;
 }
 
@@ -847,6 +934,101 @@ nb_status nb_energy_systems(nb_ctx* c, int32_t fp64_potential, double* kin, doub
 }
 
 int32_t nb_num_systems(const nb_ctx* c) { return c && c->loaded ? (c->ens ? c->cl.k : 1) : 0; }
+
+nb_status nb_autotune(nb_ctx* c, nb_tuning* out)
+{
+    nb_status s = enter(c, true);
+    if (s != NB_OK) return s;
+    const int64_t n = c->n;
+    const int32_t probes[4] = {static_cast<int32_t>(std::min<int64_t>(32, n)),
+                               static_cast<int32_t>(std::min<int64_t>(256, n)),
+                               static_cast<int32_t>(std::min<int64_t>(2048, n)),
+                               static_cast<int32_t>(std::min<int64_t>(16384, n))};
+    // candidates: i per thread (two only for MIXED single systems) x CTAs per SM
+    std::vector<int> its = {1};
+    if (c->prec == Prec::MIXED && !c->ens) its.push_back(2);
+    struct Cand {
+        int it, cps;
+        double us[4];
+    };
+    std::vector<Cand> cands;
+    int max_grid = 0;
+    for (int it : its) {
+        const int occ = nb::force_ctas_per_sm(c->prec, it);
+        for (int cps : {1, 2, 3, 4, 6, 8})
+            if (cps <= occ) {
+                cands.push_back({it, cps, {0, 0, 0, 0}});
+                max_grid = std::max(max_grid, cps * c->num_sms);
+            }
+    }
+    if (cands.empty()) return fail(c, NB_ECUDA, "no force launch shape fits on this device");
+    // scratch for the largest candidate grid with either i per thread
+    const nb_ctx::Variant keep0 = c->var[0], keep1 = c->var[1];
+    c->var[0] = {1, max_grid};
+    c->var[1] = {its.back(), max_grid};
+    s = ensure_force_scratch(c, max_grid, max_grid);
+    c->var[0] = keep0;
+    c->var[1] = keep1;
+    if (s != NB_OK) return s;
+    double* ht = reinterpret_cast<double*>(c->pinned + 48);
+    NB_CK(c, cudaMemcpyAsync(ht, c->st.t, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    NB_CK(c, cudaStreamSynchronize(c->stream));
+    NB_CK(c, nb::predict_launch(c->st, c->prec, c->jl, c->cfg.G, nullptr, *ht, nullptr, c->stream,
+                                c->ens ? &c->cl : nullptr));
+    NB_CK(c, nb::iota_launch(c->idx_user, n, c->n_act_user, c->stream));
+    cudaEvent_t e0, e1;
+    NB_CK(c, cudaEventCreate(&e0));
+    NB_CK(c, cudaEventCreate(&e1));
+    nb_status st = NB_OK;
+    for (int q = 0; q < 4 && st == NB_OK; ++q) {
+        if (cudaSuccess != nb::set_scalars_launch(c->n_act_user, probes[q], nullptr, 0.0, c->stream))
+            st = fail(c, NB_ECUDA, "autotune: set n_act");
+        for (auto& cd : cands) {
+            if (st != NB_OK) break;
+            if (c->ens && cudaSuccess != nb::plan_launch(c->cl, c->idx_user, c->n_act_user, 32 * cd.it,
+                                                         c->stream))
+                st = fail(c, NB_ECUDA, "autotune: plan");
+            nb::ForceArgs f = force_args(c, c->prec, c->jl, c->idx_user, c->n_act_user);
+            f.it = cd.it;
+            f.grid = cd.cps * c->num_sms;
+            const int reps = 3;
+            cudaError_t e = nb::force_launch(f, c->stream);  // warm-up
+            if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+            for (int k = 0; k < reps && e == cudaSuccess; ++k) e = nb::force_launch(f, c->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) st = fail(c, NB_ECUDA, "autotune: %s", cudaGetErrorString(e));
+            cd.us[q] = 1e3 * ms / reps;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != NB_OK) return st;
+    if ((s = check_status(c)) != NB_OK) return s;
+    // best shape per bucket; ties go to the smaller grid (listed first)
+    const Cand* best[2] = {&cands[0], &cands[0]};
+    for (const auto& cd : cands) {
+        if (cd.us[0] + cd.us[1] < best[0]->us[0] + best[0]->us[1]) best[0] = &cd;
+        if (cd.us[2] + cd.us[3] < best[1]->us[2] + best[1]->us[3]) best[1] = &cd;
+    }
+    c->var[0] = {best[0]->it, best[0]->cps * c->num_sms};
+    c->var[1] = {best[1]->it, best[1]->cps * c->num_sms};
+    c->nact_split = 1024;
+    drop_graph(c);
+    c->last_force_n_act = -1;
+    if (out) {
+        out->small_i_per_thread = best[0]->it;
+        out->small_ctas_per_sm = best[0]->cps;
+        out->large_i_per_thread = best[1]->it;
+        out->large_ctas_per_sm = best[1]->cps;
+        out->nact_split = c->nact_split;
+        out->small_us = best[0]->us[0] + best[0]->us[1];
+        out->large_us = best[1]->us[2] + best[1]->us[3];
+    }
+    return NB_OK;
+}
 
 int64_t nb_num_particles(const nb_ctx* c) { return c && c->loaded ? c->n : 0; }
 

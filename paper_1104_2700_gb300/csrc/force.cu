@@ -38,6 +38,7 @@ struct ForceParams {
     int64_t counter_stride;  // >= warps + groups
     uint32_t* status;
     double eps2;
+    int32_t nact_lo, nact_hi;  // the launch works only for n_act in [lo, hi)
     // Ensemble plan (all null for one system): i-groups built by
     // plan_launch, and per-cluster particle / j-layout offsets and eps^2.
     const int32_t* grp_cluster;
@@ -518,6 +519,13 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
     const int64_t P = (int64_t)gridDim.x * FORCE_WARPS;
 
     constexpr int GI = 32 * IT;
+    {
+        // Launch variants tuned for different block sizes share one stream:
+        // each works only inside its n_act window (read on the device, so
+        // the host need not know the block size).
+        const int na = *f.n_act_dev;
+        if (na < f.nact_lo || na >= f.nact_hi) return;
+    }
     Plan plan;
     plan.init(f, GI);
     const int64_t T = plan.T;
@@ -801,6 +809,8 @@ cudaError_t force_launch(const ForceArgs& a, cudaStream_t s)
     f.counter_stride = a.counter_stride;
     f.status = a.status;
     f.eps2 = a.eps2;
+    f.nact_lo = a.nact_lo;
+    f.nact_hi = a.nact_hi;
     f.grp_cluster = a.plan.grp_cluster;
     f.grp_act_begin = a.plan.grp_act_begin;
     f.grp_act_count = a.plan.grp_act_count;

@@ -107,6 +107,8 @@ struct ForceArgs {
     uint32_t* status = nullptr;
     double eps2 = 0.0;
     int grid = 0;        // CTAs (persistent)
+    int32_t nact_lo = 0;           // the launch does nothing unless
+    int32_t nact_hi = 0x7fffffff;  // nact_lo <= n_act < nact_hi
     ForcePlan plan;      // ensemble plan (empty: one system)
 };
 

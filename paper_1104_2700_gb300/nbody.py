@@ -33,6 +33,19 @@ class NbConfig(ctypes.Structure):
         ("stream", c_void_p),
         ("i_per_thread", c_int32),
         ("ctas_per_sm", c_int32),
+        ("autotune", c_int32),
+    ]
+
+
+class NbTuning(ctypes.Structure):
+    _fields_ = [
+        ("small_i_per_thread", c_int32),
+        ("small_ctas_per_sm", c_int32),
+        ("large_i_per_thread", c_int32),
+        ("large_ctas_per_sm", c_int32),
+        ("nact_split", c_int32),
+        ("small_us", c_double),
+        ("large_us", c_double),
     ]
 
 
@@ -79,6 +92,7 @@ def load(path: str = LIB_PATH):
         "nb_set_ensemble": (c_int32, [P, c_int32, P, P, P, P, P, c_double]),
         "nb_energy_systems": (c_int32, [P, c_int32, P, P]),
         "nb_num_systems": (c_int32, [P]),
+        "nb_autotune": (c_int32, [P, POINTER(NbTuning)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -187,6 +201,10 @@ def nb_num_systems(ctx) -> int:
     return load().nb_num_systems(ctx)
 
 
+def nb_autotune(ctx, out_ref):
+    return load().nb_autotune(ctx, out_ref)
+
+
 def nb_force_static(n, m, r, v, eps, G, n_act, idx, acc, jerk, pot, stream):
     """Allocation-free force evaluation on device pointers (see nbody.h)."""
     return load().nb_force_static(n, m, r, v, eps, G, n_act, idx, acc, jerk, pot, stream)
@@ -218,7 +236,7 @@ class Context:
 
     def __init__(self, precision="mixed", device=0, G=1.0, eta_start=0.01,
                  dt_max=1.0 / 16, dt_min=2.0 ** -40, stream=None, i_per_thread=0,
-                 ctas_per_sm=0):
+                 ctas_per_sm=0, autotune=False):
         cfg = nb_config_init()
         cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         cfg.device = int(device)
@@ -230,6 +248,7 @@ class Context:
             cfg.stream = c_void_p(int(getattr(stream, "cuda_stream", stream)))
         cfg.i_per_thread = int(i_per_thread)
         cfg.ctas_per_sm = int(ctas_per_sm)
+        cfg.autotune = int(bool(autotune))
         self.cfg = cfg
         self.handle = nb_create(cfg)
         self.n = 0
@@ -303,6 +322,12 @@ class Context:
         self._ck(nb_energy_systems(self.handle, int(bool(fp64_potential)),
                                    kin.ctypes.data_as(c_void_p), pot.ctypes.data_as(c_void_p)))
         return kin, pot
+
+    def autotune(self):
+        """Measure and set the force launch shapes; returns them as a dict."""
+        tun = NbTuning()
+        self._ck(nb_autotune(self.handle, ctypes.byref(tun)))
+        return {name: getattr(tun, name) for name, _ in NbTuning._fields_}
 
     def predict(self, t):
         self._ck(nb_predict(self.handle, float(t)))

@@ -35,7 +35,9 @@ def test_config_defaults(nbody_lib):
     assert cfg.precision == nbody_lib.NB_MIXED
     assert cfg.G == 1.0 and cfg.eta_start == 0.01
     assert cfg.dt_max == 1.0 / 16 and cfg.dt_min == 2.0 ** -40
-    assert ctypes.sizeof(nbody_lib.NbConfig) == 56
+    assert cfg.autotune == 0
+    assert ctypes.sizeof(nbody_lib.NbConfig) == 64
+    assert ctypes.sizeof(nbody_lib.NbTuning) == 40
 
 
 @pytest.mark.parametrize("field,value", [("dt_max", 0.1), ("dt_max", -1.0),

@@ -253,6 +253,35 @@ def test_block_step_equals_manual_sequence(gpu):
         assert np.array_equal(s1[k], s2[k]), k
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "ds"])
+def test_autotune_picks_valid_shapes_and_keeps_results(gpu, orc, prec):
+    n = 3000
+    m, r, v = ics.plummer(n, 31)
+    eps = 4.0 / n
+    idx = np.arange(n, dtype=np.int32)
+    a0, j0, p0 = orc.force(m, r, v, eps, idx=idx, nthreads=NTHREADS)
+    with gpu.Context(prec, autotune=True) as ctx:
+        ctx.set_particles(m, r, v, eps, 0.02)  # tunes on load
+        tun = ctx.autotune()
+        for b in ("small", "large"):
+            assert tun[f"{b}_i_per_thread"] in (1, 2)
+            assert 1 <= tun[f"{b}_ctas_per_sm"] <= 8
+            assert tun[f"{b}_us"] > 0
+        ctx.set_state(**_state_at_rest(n, m, r, v), eps=eps, eta=0.02)
+        ctx.predict(0.0)
+        for k in (17, n):  # one block in each bucket
+            acc, jerk, pot = ctx.force(idx[:k])
+            if prec == "mixed":
+                sa, sj, _ = _magnitude_sums(m, r, v, eps, idx[:k])
+                assert np.all(np.linalg.norm(acc - a0[:k], axis=1) <= 8 * U32 * sa)
+            else:
+                tol = 1e-10 if prec == "fp64" else 1e-6
+                assert np.max(_rel(acc, a0[:k])) < tol and np.max(_rel(jerk, j0[:k])) < tol
+        ctx.set_particles(m, r, v, eps, 0.02)
+        steps, inter = ctx.step_until(1.0 / 32)  # both launch variants in the graph
+        assert steps > 0 and inter > 0
+
+
 def test_errors_are_reported(gpu):
     m = np.array([1.0, 1.0])
     r = np.zeros((2, 3))
