@@ -63,6 +63,11 @@ typedef struct nb_config {
     int32_t i_per_thread; /* force kernel register blocking; 0 = default        */
     int32_t ctas_per_sm;  /* persistent force CTAs per SM; 0 = default          */
     int32_t autotune;     /* 1: run nb_autotune after every load                */
+    int64_t wait_limit_cycles; /* GPU clock cycles a force kernel waits for
+                              * one staged j tile before it gives up and the
+                              * call fails with NB_ETIMEOUT; 0 = about one
+                              * second.  Tests set it tiny to exercise the
+                              * failure path without faulting the GPU. */
 } nb_config;
 
 /* Fill *cfg with the defaults: NB_MIXED, device 0, G = 1, eta_start = 0.01,
@@ -94,6 +99,16 @@ typedef struct nb_tuning {
  * receives the choice.  Blocks.  Errors: NB_ESTATE (nothing loaded),
  * NB_ECUDA. */
 nb_status nb_autotune(nb_ctx* ctx, nb_tuning* out);
+
+/* Self-test of failure detection (no counterpart in the paper): run one
+ * force launch in which no warp stages its first j tile, so that tile's
+ * bounded wait runs out (~0.1 ms), exactly as it would if a copy never
+ * arrived.  Each warp then lets its other copies land and returns.  Returns
+ * NB_ETIMEOUT when the kernel reported the timeout (the expected outcome),
+ * NB_OK if it did not.  The context stays usable (status and counters are
+ * cleared; the error is not sticky); the force outputs are not meaningful.
+ * Blocks. */
+nb_status nb_selftest_timeout(nb_ctx* ctx);
 
 /* Create a context on cfg->device.  *out receives the handle.
  * Errors: NB_EINVAL (NULL pointer, dt_max not a power of two, unknown

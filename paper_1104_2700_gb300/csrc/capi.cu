@@ -346,6 +346,7 @@ nb::ForceArgs force_args(nb_ctx* c, Prec p, const nb::JLayout& jl, const int32_t
     f.counter_stride = c->counter_stride;
     f.status = c->status_dev;
     f.eps2 = c->eps * c->eps;
+    f.wait_limit = c->cfg.wait_limit_cycles;
     if (c->ens) {
         // the plan for this active list must have been written by plan_launch
         f.plan.grp_cluster = c->cl.grp_cluster;
@@ -499,6 +500,7 @@ void nb_config_init(nb_config* cfg)
     cfg->i_per_thread = 0;
     cfg->ctas_per_sm = 0;
     cfg->autotune = 0;
+    cfg->wait_limit_cycles = 0;
 }
 
 nb_status nb_create(const nb_config* cfg, nb_ctx** out)
@@ -934,6 +936,32 @@ nb_status nb_energy_systems(nb_ctx* c, int32_t fp64_potential, double* kin, doub
 }
 
 int32_t nb_num_systems(const nb_ctx* c) { return c && c->loaded ? (c->ens ? c->cl.k : 1) : 0; }
+
+nb_status nb_selftest_timeout(nb_ctx* c)
+{
+    nb_status s = enter(c, true);
+    if (s != NB_OK) return s;
+    uint32_t* h = reinterpret_cast<uint32_t*>(c->pinned);
+    NB_CK(c, cudaMemsetAsync(c->status_dev, 0, sizeof(uint32_t), c->stream));
+    NB_CK(c, nb::iota_launch(c->idx_user, c->n, c->n_act_user, c->stream));
+    if (c->ens) NB_CK(c, nb::plan_launch(c->cl, c->idx_user, c->n_act_user, 32 * c->var[0].it,
+                                         c->stream));
+    nb::ForceArgs f = force_args(c, c->prec, c->jl, c->idx_user, c->n_act_user);
+    f.it = c->var[0].it;
+    f.grid = c->var[0].grid;
+    f.wait_limit = 200000;  // ~0.1 ms per warp
+    f.unfed_first_tile = 1;
+    NB_CK(c, nb::force_launch(f, c->stream));
+    NB_CK(c, cudaMemcpyAsync(h, c->status_dev, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+    NB_CK(c, cudaStreamSynchronize(c->stream));
+    const uint32_t st = *h;
+    // leave the context as it was: clean status and reduction counters
+    NB_CK(c, cudaMemsetAsync(c->status_dev, 0, sizeof(uint32_t), c->stream));
+    NB_CK(c, cudaMemsetAsync(c->counters, 0, c->counter_words * sizeof(uint32_t), c->stream));
+    NB_CK(c, cudaStreamSynchronize(c->stream));
+    c->last_force_n_act = -1;
+    return (st & nb::ST_TIMEOUT) ? NB_ETIMEOUT : NB_OK;
+}
 
 nb_status nb_autotune(nb_ctx* c, nb_tuning* out)
 {

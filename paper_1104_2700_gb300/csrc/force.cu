@@ -39,6 +39,8 @@ struct ForceParams {
     uint32_t* status;
     double eps2;
     int32_t nact_lo, nact_hi;  // the launch works only for n_act in [lo, hi)
+    long long wait_limit;      // cycles before a tile wait gives up
+    int32_t unfed_first_tile;  // self-test: never stage each warp's first tile
     // Ensemble plan (all null for one system): i-groups built by
     // plan_launch, and per-cluster particle / j-layout offsets and eps^2.
     const int32_t* grp_cluster;
@@ -554,7 +556,9 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
     int64_t tl = t0;
     auto issue_next = [&](int s) {
         while (tl >= lgi.tile0 + lgi.ntiles) lgi = plan.group(++lg);
-        if (lane == 0)
+        // (self-test: with unfed_first_tile the first tile is never staged,
+        // so its barrier never completes and the bounded wait runs out)
+        if (lane == 0 && !(f.unfed_first_tile && tl == t0))
             issue_tile<K>(f, ring + s * K::TILE_BYTES, &bars[s], lgi.jtile0 + (tl - lgi.tile0));
         ++tl;
     };
@@ -591,9 +595,17 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
                 ac[q].zero();
             }
         }
-        const bool ok = mbar_wait_bounded(&bars[s], parity);
+        const bool ok = mbar_wait_bounded(&bars[s], parity, f.wait_limit);
         if (!__all_sync(0xffffffffu, ok)) {
             if (lane == 0) atomicOr(f.status, ST_TIMEOUT);
+            // Give up on this launch, but first let every bulk copy this warp
+            // still has in flight (tiles k .. tl - t0 - 1) land, each wait
+            // bounded again, so no copy outlives the CTA.
+            for (int64_t kk = k; kk < tl - t0; ++kk) {
+                if (f.unfed_first_tile && kk == 0) continue;  // never issued
+                mbar_wait_bounded(&bars[kk % K::STAGES],
+                                  static_cast<uint32_t>((kk / K::STAGES) & 1));
+            }
             return;
         }
         const int64_t jt = t - gi.tile0;
@@ -811,6 +823,8 @@ cudaError_t force_launch(const ForceArgs& a, cudaStream_t s)
     f.eps2 = a.eps2;
     f.nact_lo = a.nact_lo;
     f.nact_hi = a.nact_hi;
+    f.wait_limit = a.wait_limit > 0 ? a.wait_limit : WAIT_LIMIT_CYCLES;
+    f.unfed_first_tile = a.unfed_first_tile;
     f.grp_cluster = a.plan.grp_cluster;
     f.grp_act_begin = a.plan.grp_act_begin;
     f.grp_act_count = a.plan.grp_act_count;

@@ -109,6 +109,8 @@ struct ForceArgs {
     int grid = 0;        // CTAs (persistent)
     int32_t nact_lo = 0;           // the launch does nothing unless
     int32_t nact_hi = 0x7fffffff;  // nact_lo <= n_act < nact_hi
+    long long wait_limit = 0;      // cycles per tile wait; 0 = about one second
+    int32_t unfed_first_tile = 0;  // self-test of the timeout path only
     ForcePlan plan;      // ensemble plan (empty: one system)
 };
 

@@ -34,6 +34,7 @@ class NbConfig(ctypes.Structure):
         ("i_per_thread", c_int32),
         ("ctas_per_sm", c_int32),
         ("autotune", c_int32),
+        ("wait_limit_cycles", c_int64),
     ]
 
 
@@ -93,6 +94,7 @@ def load(path: str = LIB_PATH):
         "nb_energy_systems": (c_int32, [P, c_int32, P, P]),
         "nb_num_systems": (c_int32, [P]),
         "nb_autotune": (c_int32, [P, POINTER(NbTuning)]),
+        "nb_selftest_timeout": (c_int32, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -205,6 +207,10 @@ def nb_autotune(ctx, out_ref):
     return load().nb_autotune(ctx, out_ref)
 
 
+def nb_selftest_timeout(ctx):
+    return load().nb_selftest_timeout(ctx)
+
+
 def nb_force_static(n, m, r, v, eps, G, n_act, idx, acc, jerk, pot, stream):
     """Allocation-free force evaluation on device pointers (see nbody.h)."""
     return load().nb_force_static(n, m, r, v, eps, G, n_act, idx, acc, jerk, pot, stream)
@@ -236,7 +242,7 @@ class Context:
 
     def __init__(self, precision="mixed", device=0, G=1.0, eta_start=0.01,
                  dt_max=1.0 / 16, dt_min=2.0 ** -40, stream=None, i_per_thread=0,
-                 ctas_per_sm=0, autotune=False):
+                 ctas_per_sm=0, autotune=False, wait_limit_cycles=0):
         cfg = nb_config_init()
         cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         cfg.device = int(device)
@@ -249,6 +255,7 @@ class Context:
         cfg.i_per_thread = int(i_per_thread)
         cfg.ctas_per_sm = int(ctas_per_sm)
         cfg.autotune = int(bool(autotune))
+        cfg.wait_limit_cycles = int(wait_limit_cycles)
         self.cfg = cfg
         self.handle = nb_create(cfg)
         self.n = 0

@@ -36,7 +36,8 @@ def test_config_defaults(nbody_lib):
     assert cfg.G == 1.0 and cfg.eta_start == 0.01
     assert cfg.dt_max == 1.0 / 16 and cfg.dt_min == 2.0 ** -40
     assert cfg.autotune == 0
-    assert ctypes.sizeof(nbody_lib.NbConfig) == 64
+    assert cfg.wait_limit_cycles == 0
+    assert ctypes.sizeof(nbody_lib.NbConfig) == 72
     assert ctypes.sizeof(nbody_lib.NbTuning) == 40
 
 
