@@ -59,6 +59,8 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-extra", action="store_true",
+                   help="skip the N = 65536 roofline and the ensemble measurement")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--modes", default="mixed,ds,fp64",
                    help="comma-separated precision modes to time")
@@ -413,6 +415,10 @@ def run_ours(args):
     for ctx, _ in contexts.values():
         ctx.close()
 
+    extra = {}
+    if not args.no_extra:
+        extra = extra_measurements(nbody, torch, dev, stream, world, peak32)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(m, r, v, eps, args.cpu_seconds)
@@ -422,7 +428,7 @@ def run_ours(args):
             "metric": METRIC, "value": hm["value"], "unit": UNIT, "n_gpus": world,
             "steps": hm["steps"], "warmup": args.warmup, "ms_per_step": hm["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
+            "dtype": DTYPES[head], "data": "synthetic",
             "config": {"workload": WL.name, "n": n, "n_act": list(NACTS), "eps": eps,
                        "seed": WL.seed, "precision": head, "parallelism": f"replicas{world}",
                        "step": "select+predict+force+correct per n_act, state restored on "
@@ -437,10 +443,103 @@ def run_ours(args):
             "fp64_speedup": (hm["value"] / modes["fp64"]["value"]) if "fp64" in modes else None,
             "e2e": e2e,
             "cpu_baseline": cpu,
-            "gpu_launches": 10 * len(NACTS) * hm["steps"],
+            "gpu_launches": LAUNCHES_PER_BLOCK_STEP * len(NACTS) * hm["steps"],
             "clocks": clk,
+            **extra,
         }
         print(json.dumps(line), flush=True)
+
+
+# Kernels of one graph-replayed block step of the sweep: 4 layout conversions
+# (state restore), tmin + count + scatter (select), predict, the two force
+# launch variants (each returns at once outside its n_act window), correct.
+LAUNCHES_PER_BLOCK_STEP = 11
+DTYPES = {"ds": "f32x2 (double-single on the FP32 pipes)", "mixed": "f32", "fp64": "f64"}
+
+
+def extra_measurements(nbody, torch, dev, stream, world, peak32):
+    """Context beside the headline (not part of `value`):
+    * the force kernel at N = 65536, n_act = N (the size the FP32-roofline
+      target is stated for), MIXED and DS, CUDA events;
+    * the 256-system ensemble (log-uniform N in [256, 8192], eps = 4/N)
+      integrated from t = 0 to 1/32 in one context, DS: total interactions
+      per second of the whole integration;
+    * block steps, smallest timestep and energy drift of short integrations
+      in all three modes (MIXED's timestep collapse)."""
+    out = {}
+    wl = ics.MIXED_N64K
+    m, r, v = wl.particles()
+    n = wl.n
+    idx = torch.arange(n, dtype=torch.int32, device=dev)
+    roof = {}
+    for prec in ("mixed", "ds"):
+        with nbody.Context(prec, device=dev.index, stream=stream) as ctx:
+            ctx.set_particles(m, r, v, wl.eps, wl.eta)
+            tun = ctx.autotune()
+            ctx.predict(0.0)
+            ctx.force(idx)
+            reps = 5
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                ctx.force(idx)
+            e1.record(stream)
+            e1.synchronize()
+            t = e0.elapsed_time(e1) / 1e3 / reps
+            ach = FLOPS_PER_INTERACTION * n * n / t / 1e12
+            roof[prec] = {"bound": "alu", "achieved": ach, "peak": peak32, "unit": "TFLOP/s",
+                          "frac": ach / peak32, "launch_ms": t * 1e3,
+                          "interactions_per_s": n * n / t, "autotuned_launch": tun}
+    out["roofline_n65536"] = roof
+    sizes, off, ms, rs, vs, eps = ics.ensemble(**{k: ics.ENSEMBLE_K256[k]
+                                                  for k in ("k", "size_seed", "member_seed0")})
+    ens = {"systems": int(len(sizes)), "particles": int(off[-1]), "t_end": 1.0 / 32,
+           "precision_note": "DS only: with FP32 pair arithmetic (MIXED) the Aarseth "
+                             "timesteps collapse (see precision_ablation)"}
+    for prec in ("ds",):
+        with nbody.Context(prec, device=dev.index, stream=stream) as ctx:
+            ctx.set_ensemble(off, ms, rs, vs, eps, ics.ENSEMBLE_K256["eta"])
+            ctx.autotune()
+            ctx.set_ensemble(off, ms, rs, vs, eps, ics.ENSEMBLE_K256["eta"])
+            torch.cuda.synchronize(dev)
+            w0 = time.perf_counter()
+            steps, inter = ctx.step_until(1.0 / 32)
+            torch.cuda.synchronize(dev)
+            w = time.perf_counter() - w0
+            ens[prec] = {"value": world * inter / w, "unit": UNIT, "block_steps": int(steps),
+                         "interactions": int(inter), "wall_s": w,
+                         "us_per_block_step": 1e6 * w / max(steps, 1)}
+    out["ensemble_k256"] = ens
+    # Precision ablation of the integration (Sec. 4 measures energy error
+    # against step count in mixed and DP): block steps, smallest timestep and
+    # energy drift from t = 0 to 1/64 in each mode.  The N = 256 system is
+    # member 119 of the ensemble: a particle there with |a| = 0.1, |j| = 80
+    # (nearly cancelling pair forces) drives MIXED into a timestep collapse.
+    abl = {"t_end": 1.0 / 64}
+    wl1 = ics.FP64_N1K
+    m1, r1, v1 = wl1.particles()
+    q = 119
+    cases = {"plummer_n1024_eps1/64": (m1, r1, v1, wl1.eps),
+             "plummer_n%d_eps4/n_ensemble_member%d" % (sizes[q], q):
+                 (ms[off[q]:off[q + 1]], rs[off[q]:off[q + 1]], vs[off[q]:off[q + 1]], float(eps[q]))}
+    for name, (m1, r1, v1, e1) in cases.items():
+        row = {}
+        for prec in ("fp64", "ds", "mixed"):
+            # dt_max = t_end, so that every particle ends synchronised at t_end
+            with nbody.Context(prec, device=dev.index, stream=stream, dt_max=1.0 / 64) as ctx:
+                ctx.set_particles(m1, r1, v1, e1, 0.02)
+                k0, w0 = ctx.energy(fp64_potential=True)
+                s0 = ctx.get_state()
+                steps, inter = ctx.step_until(1.0 / 64)
+                k1, w1 = ctx.energy(fp64_potential=True)
+                s1 = ctx.get_state()
+                row[prec] = {"block_steps": int(steps), "interactions": int(inter),
+                             "log2_min_dt_start": float(np.log2(s0["dt"].min())),
+                             "log2_min_dt_end": float(np.log2(s1["dt"].min())),
+                             "rel_energy_drift": abs((k1 + w1) - (k0 + w0)) / abs(k0 + w0)}
+        abl[name] = row
+    out["precision_ablation"] = abl
+    return out
 
 
 def ctypes_ptr(t):

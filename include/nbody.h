@@ -70,12 +70,12 @@ typedef struct nb_config {
                               * failure path without faulting the GPU. */
 } nb_config;
 
-/* Fill *cfg with the defaults: NB_MIXED, device 0, G = 1, eta_start = 0.01,
+/* Fill *cfg with the defaults: NB_DS, device 0, G = 1, eta_start = 0.01,
  * dt_max = 1/16, dt_min = 2^-40, private stream, default launch shapes, no
  * autotuning. */
 void nb_config_init(nb_config* cfg);
 
-/* Launch shapes of the force kernel (SURVEY's i-tile / j-split): blocks of
+/* Launch shapes of the force kernel (i-tile per lane, j-split over warps): blocks of
  * fewer than nact_split active particles use the "small" shape, others the
  * "large" one.  i_per_thread is the i-tile per lane (an i-group is 32 times
  * that); ctas_per_sm sets the persistent grid, which fixes how far each

@@ -490,7 +490,7 @@ void nb_config_init(nb_config* cfg)
 {
     if (!cfg) return;
     std::memset(cfg, 0, sizeof(*cfg));
-    cfg->precision = NB_MIXED;
+    cfg->precision = NB_DS;
     cfg->device = 0;
     cfg->G = 1.0;
     cfg->eta_start = 0.01;
