@@ -68,6 +68,11 @@ def parse_args():
                    help="only run --launches force launches (for ncu), no timing")
     p.add_argument("--profile-nact", type=int, default=16384)
     p.add_argument("--launches", type=int, default=3)
+    p.add_argument("--integrate", choices=sorted(INTEGRATIONS), default=None,
+                   help="instead of the sweep: integrate one workload in --modes "
+                        "(default ds,fp64) to --t-end and report steps, rate, energy drift")
+    p.add_argument("--t-end", type=float, default=None,
+                   help="end time for --integrate (a multiple of dt_max = 1/16)")
     return p.parse_args()
 
 
@@ -80,16 +85,17 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(prec):
-    """DRAM bytes per force launch (n_act = N) from the committed ncu summary,
-    or None when the kernel sources changed since it was captured."""
+def profiled_metric(prec, key="traffic_bytes_per_launch"):
+    """A figure of the force launch at n_act = N from the committed ncu summary
+    (DRAM bytes per launch, thread instructions per interaction), or None when
+    the kernel sources changed since it was captured."""
     import re
     path = os.path.join(ROOT, "profiles", f"force_{prec}_n16384.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
     h = re.search(r"source_hash:\s*([0-9a-f]+)", text)
-    t = re.search(r"traffic_bytes_per_launch:\s*([0-9.]+)", text)
+    t = re.search(key + r":\s*([0-9.]+)", text)
     if not h or not t or h.group(1) != kernel_source_hash():
         return None
     return float(t.group(1))
@@ -359,23 +365,51 @@ def run_ours(args):
     clk = hm["clocks"]
     sm_max = clk.get("sm_max_mhz") or 2070.0
     peak32 = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+    # Measured FMA throughput (FP32 and FP64 chains on every SM), outside any
+    # timed region: a cross-check of the derived peak, and the FP64 denominator.
+    meas = {}
+    try:
+        meas["fp32"], meas["fp64"] = nbody.measure_peaks(dev.index)
+    except nbody.NbError as exc:
+        meas["error"] = str(exc)
 
     def roofline_of(p, kernel):
         ach = FLOPS_PER_INTERACTION * modes[p]["force_interactions_per_s"] / 1e12
+        ipi = profiled_metric(p, "thread_instructions_per_interaction")
+        issue = None
+        if ipi:
+            # one warp instruction per clock per SM sub-partition (4 per SM)
+            peak_ti = props.multi_processor_count * 4 * 32 * sm_max * 1e6
+            ach_ti = ipi * modes[p]["force_interactions_per_s"]
+            issue = {"thread_instructions_per_interaction": ipi,
+                     "achieved_per_s": ach_ti, "peak_per_s": peak_ti, "frac": ach_ti / peak_ti,
+                     "basis": "ncu smsp__inst_executed.sum x 32 / interactions (same kernel "
+                              "source hash); peak = SMs x 4 schedulers x 32 lanes x max clock"}
+        if p == "fp64":
+            pk, basis = meas.get("fp64"), "measured DFMA throughput (nb_measure_peaks, this run)"
+            return {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                    "frac": (ach / pk) if pk else None, "kernel": kernel, "peak_basis": basis,
+                    "launch_ms": modes[p]["force_launch_ms_nact_N"], "issue": issue}
         return {"bound": "alu", "achieved": ach, "peak": peak32, "unit": "TFLOP/s",
-                "frac": ach / peak32, "traffic": profiled_traffic(p), "kernel": kernel,
+                "frac": ach / peak32, "traffic": profiled_metric(p), "kernel": kernel,
+                "peak_measured": meas.get("fp32"),
+                "frac_of_measured": (ach / meas["fp32"]) if meas.get("fp32") else None,
+                "issue": issue,
                 "traffic_source": f"profiles/force_{p}_n16384.md (ncu, kernel source "
                                   f"hash {kernel_source_hash()}; null if the kernel changed)",
                 "algorithmic_bytes_per_launch": n * {"mixed": 40, "ds": 64, "fp64": 64}[p],
                 "launch_ms": modes[p]["force_launch_ms_nact_N"],
                 "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x "
-                              f"{sm_max:.0f} MHz max SM clock (derived, not measured); "
+                              f"{sm_max:.0f} MHz max SM clock (derived; peak_measured is this "
+                              f"run's FFMA-chain throughput); "
                               f"60 flop per interaction (paper convention)"}
 
     kname = {"mixed": "force_kernel<PolicyMixed<2>,2>", "ds": "force_kernel<PolicyDS<1>,1>",
              "fp64": "force_kernel<PolicyFP64<1>,1>"}
     roofline = roofline_of(head, kname[head])
     roofline_mixed = roofline_of("mixed", kname["mixed"]) if "mixed" in modes else None
+    if "fp64" in modes:
+        modes["fp64"]["roofline"] = roofline_of("fp64", kname["fp64"])
 
     # End to end through the public API with host buffers: every step copies
     # the state in from pinned host memory and the corrected state back out.
@@ -450,10 +484,11 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
 
 
-# Kernels of one graph-replayed block step of the sweep: 4 layout conversions
-# (state restore), tmin + count + scatter (select), predict, the two force
-# launch variants (each returns at once outside its n_act window), correct.
-LAUNCHES_PER_BLOCK_STEP = 11
+# Kernels of one graph-replayed block step of the sweep: the state restore
+# (4 layout conversions and the split bounds), tmin + count + scatter
+# (select), predict, the two force launch variants (each returns at once
+# outside its n_act window), correct.
+LAUNCHES_PER_BLOCK_STEP = 12
 DTYPES = {"ds": "f32x2 (double-single on the FP32 pipes)", "mixed": "f32", "fp64": "f64"}
 
 
@@ -568,10 +603,42 @@ def cpu_baseline(m, r, v, eps, seconds):
         if dt >= 0.5 * seconds:
             break
     inter = reps * k * n
+    # one core: the same oracle on a sample sized for ~3 s at the measured
+    # per-core rate
+    per_particle_1core = dt * cores / (reps * k)
+    k1 = int(max(16, min(n, 3.0 / max(per_particle_1core, 1e-12))))
+    t0 = time.perf_counter()
+    oracle.force(m, r, v, eps, idx=perm[:k1], nthreads=1)
+    dt1 = time.perf_counter() - t0
     return {"value": inter / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"FP64 oracle force (Eqs. acc, jrk, pot) on {k} of the {n} particles "
                       f"against all {n} j, x{reps}, OpenMP over i, {dt:.1f} s",
-            "gflops_60flop": inter / dt * FLOPS_PER_INTERACTION / 1e9}
+            "gflops_60flop": inter / dt * FLOPS_PER_INTERACTION / 1e9,
+            "one_core": {"value": k1 * n / dt1, "unit": UNIT,
+                         "gflops_60flop": k1 * n / dt1 * FLOPS_PER_INTERACTION / 1e9,
+                         "sample": f"{k1} of the {n} particles against all j, 1 thread, "
+                                   f"{dt1:.1f} s"},
+            "cpu_model": cpu_model()}
+
+
+def cpu_model():
+    """The host CPU's name: lscpu's model name, else /proc/cpuinfo."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def run_reference(args):
@@ -615,9 +682,72 @@ def run_reference(args):
     }), flush=True)
 
 
+# Integration workloads (Plummer, standard N-body units) and their end times.
+INTEGRATIONS = {"c1": ("FP64_N1K", 0.5), "c3": ("MIXED_N64K", 1.0),
+                "c5": ("SALPETER_N256K", 0.25)}
+
+
+def run_integration(args):
+    """Block-step integration of one workload from t = 0 to t_end in each
+    precision mode: block steps, interactions per second of the whole run
+    (wall clock around nb_step_until, CUDA-synchronised), the smallest
+    timestep reached and the relative energy drift with the FP64 potential
+    (Sec. 4 measures the energy error the same way).  For the N = 1024
+    workload the FP64 oracle runs the same integration on the host cores."""
+    name, t_default = INTEGRATIONS[args.integrate]
+    wl = getattr(ics, name)
+    t_end = args.t_end if args.t_end is not None else t_default
+    if t_end <= 0 or (t_end * 16) != int(t_end * 16):
+        raise SystemExit("--t-end must be a positive multiple of 1/16")
+    import torch
+    from paper_1104_2700_gb300 import build as nb_build
+    from paper_1104_2700_gb300 import nbody
+    nb_build.build()
+    modes = [x for x in args.modes.split(",") if x] if args.modes != "mixed,ds,fp64" \
+        else ["ds", "fp64"]
+    m, r, v = wl.particles()
+    out = {"metric": "block-step integration interactions/s", "unit": UNIT,
+           "workload": wl.name, "n": wl.n, "eps": wl.eps, "eta": wl.eta, "t_end": t_end,
+           "data": "synthetic", "modes": {}}
+    for prec in modes:
+        with nbody.Context(prec) as ctx:
+            ctx.set_particles(m, r, v, wl.eps, wl.eta)
+            k0, w0 = ctx.energy(fp64_potential=True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            steps, inter = ctx.step_until(t_end)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            k1, w1 = ctx.energy(fp64_potential=True)
+            st = ctx.get_state()
+            out["modes"][prec] = {
+                "block_steps": int(steps), "interactions": int(inter), "wall_s": wall,
+                "value": inter / wall, "log2_min_dt": float(np.log2(st["dt"].min())),
+                "mean_steps_per_particle": inter / wl.n / wl.n,
+                "rel_energy_drift": abs((k1 + w1) - (k0 + w0)) / abs(k0 + w0)}
+        print(json.dumps({"partial": prec, **out["modes"][prec]}), file=sys.stderr, flush=True)
+    if wl.n <= 4096:
+        from oracle import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        s = oracle.State(m, r, v, wl.eps, wl.eta, nthreads=os.cpu_count() or 1)
+        e0 = s.energy()
+        status = s.run(t_end)
+        e1 = s.energy()
+        wall = time.perf_counter() - t0
+        out["oracle"] = {"status": int(status), "block_steps": s.n_steps,
+                         "interactions": s.n_inter, "wall_s": wall,
+                         "value": s.n_inter / wall,
+                         "rel_energy_drift": abs(e1 - e0) / abs(e0),
+                         "cores": os.cpu_count() or 1}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse_args()
-    if args.profile:
+    if args.integrate:
+        run_integration(args)
+    elif args.profile:
         run_profile(args)
     elif args.impl == "reference":
         run_reference(args)

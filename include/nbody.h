@@ -261,6 +261,15 @@ nb_status nb_force_static(int64_t n, const double* m, const double* r, const dou
                           double eps, double G, int32_t n_act, const int32_t* idx,
                           double* acc, double* jerk, double* pot, void* stream);
 
+/* Calibration, with no counterpart in the paper: the measured FP32 and FP64
+ * fused-multiply-add throughput of `device` in TFLOP/s (an FMA counts as 2
+ * flop), from independent FMA chains on every SM, best of 3 timed launches
+ * (~20 ms each on GB300).  These are the denominators for the
+ * force kernels' ALU roofline.  Blocks; allocates and frees its own scratch;
+ * restores the caller's current device.  Errors: NB_EINVAL (NULL output or
+ * bad device), NB_ECUDA. */
+nb_status nb_measure_peaks(int32_t device, double* fp32_tflops, double* fp64_tflops);
+
 #ifdef __cplusplus
 }
 #endif

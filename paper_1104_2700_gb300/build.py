@@ -27,7 +27,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2",
 PER_FILE = {
     "force.cu": ["-ftz=true"],
 }
-SOURCES = ["capi.cu", "force.cu", "hermite.cu", "static_force.cu"]
+SOURCES = ["capi.cu", "force.cu", "hermite.cu", "static_force.cu", "peak.cu"]
 
 
 def nvcc() -> str:

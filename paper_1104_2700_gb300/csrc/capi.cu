@@ -459,6 +459,15 @@ nb_status build_step_graph(nb_ctx* c, double t_end)
     return NB_OK;
 }
 
+// Bounds of the grid-aligned j-layout split, from the loaded positions and
+// velocities (the corrector raises them from then on).
+nb_status refresh_bounds(nb_ctx* c)
+{
+    NB_CK(c, cudaMemsetAsync(c->st.bound, 0, 2 * sizeof(uint32_t), c->stream));
+    NB_CK(c, nb::bounds_launch(c->st.x, c->st.v, 3 * c->n, c->st.bound, c->stream));
+    return NB_OK;
+}
+
 // Set-up shared by nb_set_particles / nb_set_state.
 nb_status begin_load(nb_ctx* c, int64_t n, double eps, double eta)
 {
@@ -549,6 +558,8 @@ nb_status nb_create(const nb_config* cfg, nb_ctx** out)
     c->grid64 = per_sm64 * c->num_sms;
     if (cudaMalloc(&c->status_dev, sizeof(uint32_t)) != cudaSuccess) return bail(NB_ENOMEM);
     if (cudaMemset(c->status_dev, 0, sizeof(uint32_t)) != cudaSuccess) return bail(NB_ECUDA);
+    if (cudaMalloc(&c->st.bound, 2 * sizeof(uint32_t)) != cudaSuccess) return bail(NB_ENOMEM);
+    if (cudaMemset(c->st.bound, 0, 2 * sizeof(uint32_t)) != cudaSuccess) return bail(NB_ECUDA);
     if (cudaMalloc(&c->ctr64, 2 * sizeof(unsigned long long)) != cudaSuccess) return bail(NB_ENOMEM);
     if (cudaMemset(c->ctr64, 0, 2 * sizeof(unsigned long long)) != cudaSuccess) return bail(NB_ECUDA);
     if (cudaMallocHost(&c->pinned, PINNED_BYTES) != cudaSuccess) return bail(NB_ENOMEM);
@@ -564,6 +575,7 @@ nb_status nb_destroy(nb_ctx* c)
     drop_graph(c);
     free_buffers(c);
     if (c->status_dev) cudaFree(c->status_dev);
+    if (c->st.bound) cudaFree(c->st.bound);
     if (c->ctr64) cudaFree(c->ctr64);
     if (c->pinned) cudaFreeHost(c->pinned);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -584,6 +596,7 @@ nb_status nb_set_particles(nb_ctx* c, int64_t n, const double* m, const double* 
     NB_CK(c, cudaMemsetAsync(c->st.a, 0, 3 * n * sizeof(double), c->stream));
     NB_CK(c, cudaMemsetAsync(c->st.j, 0, 3 * n * sizeof(double), c->stream));
     NB_CK(c, cudaMemsetAsync(c->st.t, 0, n * sizeof(double), c->stream));
+    if ((s = refresh_bounds(c)) != NB_OK) return s;
     // Forces on every particle at t = 0, then the first timesteps.
     NB_CK(c, nb::predict_launch(c->st, c->prec, c->jl, c->cfg.G, nullptr, 0.0, nullptr, c->stream));
     NB_CK(c, nb::iota_launch(c->idx_user, n, c->n_act_user, c->stream));
@@ -614,6 +627,7 @@ nb_status nb_set_state(nb_ctx* c, int64_t n, const double* m, const double* r, c
     if ((s = upload_vec3(c, j, c->st.j, on_device)) != NB_OK) return s;
     NB_CK(c, cudaMemcpyAsync(c->st.t, t, n * sizeof(double), k, c->stream));
     NB_CK(c, cudaMemcpyAsync(c->st.dt, dt, n * sizeof(double), k, c->stream));
+    if ((s = refresh_bounds(c)) != NB_OK) return s;
     if (!on_device) NB_CK(c, cudaStreamSynchronize(c->stream));
     c->loaded = true;
     return NB_OK;
@@ -896,6 +910,7 @@ nb_status nb_set_ensemble(nb_ctx* c, int32_t k, const int64_t* offsets, const do
     NB_CK(c, cudaMemsetAsync(c->st.a, 0, 3 * n * sizeof(double), c->stream));
     NB_CK(c, cudaMemsetAsync(c->st.j, 0, 3 * n * sizeof(double), c->stream));
     NB_CK(c, cudaMemsetAsync(c->st.t, 0, n * sizeof(double), c->stream));
+    if ((s = refresh_bounds(c)) != NB_OK) return s;
     // forces on every particle of every system at t = 0, first timesteps
     NB_CK(c, nb::predict_launch(c->st, c->prec, c->jl, c->cfg.G, nullptr, 0.0, nullptr, c->stream,
                                 &c->cl));

@@ -235,22 +235,8 @@ struct PolicyMixed {
 // only second-order terms (lo * lo) are dropped.  The result carries about
 // 44 bits, so cancellation among pair terms (near neighbours around a
 // particle with a small net acceleration or jerk) costs no accuracy at the
-// 1e-6 level.
-// (jh + jl) - (ih + il) as a normalised double-single pair.  s = fl(jh - ih)
-// and its error e are exact (TwoSum); the correction t = (jl - il) + e is no
-// larger in exponent than s whenever s != 0 (the lo parts are at most half
-// an ulp of their hi parts), and with s == 0 the sum is t itself, so the
-// final renormalisation can be Fast2Sum.
-__device__ __forceinline__ void ds_diff(float jh, float jl, float ih, float il, float& dh,
-                                        float& dl)
-{
-    float s, e;
-    two_sum(jh, -ih, s, e);
-    const float t = __fadd_rn(__fsub_rn(jl, il), e);
-    dh = __fadd_rn(s, t);
-    dl = __fsub_rn(t, __fsub_rn(dh, s));
-}
-
+// 1e-6 level.  Positions and velocities arrive as grid-aligned splits, so
+// their differences take one exact subtraction and a Fast2Sum (grid_diff).
 // (ah + al) * (bh + bl) to first order: (p, e) with p = fl(ah * bh).
 __device__ __forceinline__ void ds_mul(float ah, float al, float bh, float bl, float& p,
                                        float& e)
@@ -317,13 +303,13 @@ struct PolicyDS {
             for (int q = 0; q < IT; ++q) {
                 const I& s = is[q];
                 float dxh, dxl, dyh, dyl, dzh, dzl;
-                ds_diff(A.x, B.x, s.xh, s.xl, dxh, dxl);
-                ds_diff(A.y, B.y, s.yh, s.yl, dyh, dyl);
-                ds_diff(A.z, B.z, s.zh, s.zl, dzh, dzl);
+                grid_diff(A.x, B.x, s.xh, s.xl, dxh, dxl);
+                grid_diff(A.y, B.y, s.yh, s.yl, dyh, dyl);
+                grid_diff(A.z, B.z, s.zh, s.zl, dzh, dzl);
                 float vxh, vxl, vyh, vyl, vzh, vzl;
-                ds_diff(C.x, D.x, s.vxh, s.vxl, vxh, vxl);
-                ds_diff(C.y, D.y, s.vyh, s.vyl, vyh, vyl);
-                ds_diff(C.z, D.z, s.vzh, s.vzl, vzh, vzl);
+                grid_diff(C.x, D.x, s.vxh, s.vxl, vxh, vxl);
+                grid_diff(C.y, D.y, s.vyh, s.vyl, vyh, vyl);
+                grid_diff(C.z, D.z, s.vzh, s.vzl, vzh, vzl);
                 // r^2 = dx^2 + dy^2 + dz^2 + eps^2 (all terms >= 0)
                 float px, pxe, py, pye, pz, pze;
                 ds_mul(dxh, dxl, dxh, dxl, px, pxe);

@@ -66,11 +66,17 @@ __global__ void predict_kernel(const StateDev st, const JLayout jl, const double
         V[0] = make_double2(vp[0], vp[1]);
         V[1] = make_double2(vp[2], 0.0);
     } else {
+        // grid-aligned splits; ghosts keep their far-away marker (zero mass)
+        const GridQuantum gx = grid_quantum(st.bound[0]);
         float hi[3], lo[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            hi[c] = __double2float_rn(xp[c]);
-            lo[c] = __double2float_rn(xp[c] - static_cast<double>(hi[c]));
+            if (i >= 0) {
+                grid_split(xp[c], gx, hi[c], lo[c]);
+            } else {
+                hi[c] = static_cast<float>(GHOST_POS);
+                lo[c] = 0.f;
+            }
         }
         if (PREC == static_cast<int>(Prec::MIXED)) {
             static_cast<float4*>(jl.arr[0])[q] =
@@ -82,18 +88,48 @@ __global__ void predict_kernel(const StateDev st, const JLayout jl, const double
         } else {
             const float gh = __double2float_rn(gm);
             const float gl = __double2float_rn(gm - static_cast<double>(gh));
+            const GridQuantum gv = grid_quantum(st.bound[1]);
             float vh[3], vl[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                vh[c] = __double2float_rn(vp[c]);
-                vl[c] = __double2float_rn(vp[c] - static_cast<double>(vh[c]));
-            }
+            for (int c = 0; c < 3; ++c) grid_split(vp[c], gv, vh[c], vl[c]);
             static_cast<float4*>(jl.arr[0])[q] = make_float4(hi[0], hi[1], hi[2], gh);
             static_cast<float4*>(jl.arr[1])[q] = make_float4(lo[0], lo[1], lo[2], gl);
             static_cast<float4*>(jl.arr[2])[q] = make_float4(vh[0], vh[1], vh[2], 0.f);
             static_cast<float4*>(jl.arr[3])[q] = make_float4(vl[0], vl[1], vl[2], 0.f);
         }
     }
+}
+
+// Bounds of the grid-aligned split: max |a_k| and max |b_k| (float bits,
+// rounded up so the bound is never below the value).
+__global__ void bounds_kernel(const double* __restrict__ a, const double* __restrict__ b,
+                              int64_t count, uint32_t* bound)
+{
+    uint32_t ma = 0, mb = 0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t ea = __float_as_uint(__double2float_ru(fabs(a[k])));
+        const uint32_t eb = __float_as_uint(__double2float_ru(fabs(b[k])));
+        ma = ea > ma ? ea : ma;
+        mb = eb > mb ? eb : mb;
+    }
+    ma = __reduce_max_sync(0xffffffffu, ma);
+    mb = __reduce_max_sync(0xffffffffu, mb);
+    if ((threadIdx.x & 31) == 0) {
+        if (ma) atomicMax(&bound[0], ma);
+        if (mb) atomicMax(&bound[1], mb);
+    }
+}
+
+cudaError_t bounds_launch(const double* a, const double* b, int64_t count, uint32_t* bound,
+                          cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    const int threads = 256;
+    const int64_t want = (count + threads - 1) / threads;
+    const unsigned blocks = static_cast<unsigned>(want < 1024 ? want : 1024);
+    bounds_kernel<<<blocks, threads, 0, s>>>(a, b, count, bound);
+    return cudaGetLastError();
 }
 
 cudaError_t predict_launch(const StateDev& st, Prec p, const JLayout& jl, double G,
@@ -477,7 +513,7 @@ __global__ void correct_kernel(const StateDev st, const CorrectArgs c)
     // h is a power of two, so dividing by h^2 or h^3 (and by 2) is an exact
     // scaling: multiplying by the exact reciprocal gives the quotient's bits.
     const double ih2 = DDIV(1.0, h2), ih3 = DDIV(1.0, h3);
-    double a1[3], j1[3], s0[3], c0[3];
+    double a1[3], j1[3], s0[3], c0[3], xmax = 0.0, vmax = 0.0;
     bool finite = true;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -509,8 +545,15 @@ __global__ void correct_kernel(const StateDev st, const CorrectArgs c)
         st.v[q] = v1;
         st.a[q] = a1[d];
         st.j[q] = j1[d];
+        xmax = fmax(xmax, fabs(r1));
+        vmax = fmax(vmax, fabs(v1));
     }
     st.t[i] = tn;
+    // raise the layout bounds if this particle moved past them (rare)
+    const uint32_t xb = __float_as_uint(__double2float_ru(xmax));
+    const uint32_t vb = __float_as_uint(__double2float_ru(vmax));
+    if (xb > st.bound[0]) atomicMax(&st.bound[0], xb);
+    if (vb > st.bound[1]) atomicMax(&st.bound[1], vb);
     // Step 8: Eq. timestep at the new time (a1, j1, snap carried to t_next,
     // crackle), then the power-of-two rule of the hierarchical scheme.
     double sn[3];

@@ -116,6 +116,43 @@ __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e)
     e = __fmaf_rn(a, b, -p);
 }
 
+// Grid-aligned double-single split.  Given a bound B on every |x| of one
+// layout, q = P 2^-23 with P the least power of two above 2B.  hi is x
+// rounded to a multiple of q (|hi| <= 2^23 q, so it fits a float exactly) and
+// lo = x - hi (|lo| <= q/2, kept to 24 bits: hi + lo is x to ~B 2^-47).  Since
+// every hi part lies on the same grid and |hi_j - hi_i| <= 2^24 q, the FP32
+// difference of two hi parts is exact.  The factor 2 leaves room for values
+// that grow past B before the bound is raised; a value beyond 2B still splits
+// into hi + lo = x, only its hi part leaves the grid.
+struct GridQuantum {
+    double q, inv_q;  // both powers of two, so x * inv_q and k * q are exact
+};
+
+__device__ __forceinline__ GridQuantum grid_quantum(uint32_t bound_bits)
+{
+    int e;
+    frexp(2.0 * static_cast<double>(__uint_as_float(bound_bits)), &e);
+    return {ldexp(1.0, e - 23), ldexp(1.0, 23 - e)};
+}
+
+__device__ __forceinline__ void grid_split(double x, const GridQuantum& g, float& hi, float& lo)
+{
+    hi = __double2float_rn(rint(x * g.inv_q) * g.q);
+    lo = __double2float_rn(x - static_cast<double>(hi));
+}
+
+// (jh + jl) - (ih + il) for grid-aligned splits, as a normalised (dh, dl):
+// jh - ih is exact, and its magnitude is 0 or at least q >= |jl - il|, so
+// Fast2Sum renormalises exactly.
+__device__ __forceinline__ void grid_diff(float jh, float jl, float ih, float il, float& dh,
+                                          float& dl)
+{
+    const float s = __fsub_rn(jh, ih);
+    const float t = __fsub_rn(jl, il);
+    dh = __fadd_rn(s, t);
+    dl = __fsub_rn(t, __fsub_rn(dh, s));
+}
+
 // Running double-single accumulator: hi carries the sum, lo the collected
 // rounding errors of every fold.
 struct DSAcc {

@@ -28,12 +28,24 @@ struct StateDev {
     double* j = nullptr;
     double* t = nullptr;
     double* dt = nullptr;
+    // [0] bound on every |position component|, [1] on every |velocity
+    // component| (float bits, never decreasing): set from the whole state at
+    // load, raised by the corrector.  They fix the grid of the j layout's
+    // double-single split (grid_split).
+    uint32_t* bound = nullptr;
 };
+
+// bound[0] = max |a_k|, bound[1] = max |b_k| over k < count (float bits,
+// rounded up), atomically raised; the caller zeroes bound first.
+cudaError_t bounds_launch(const double* a, const double* b, int64_t count, uint32_t* bound,
+                          cudaStream_t s);
 
 // Predicted j particles in the layout a force kernel streams.
 //   FP64 : arr[0] = double4 (x, y, z, G m), arr[1] = double4 (vx, vy, vz, 0)
 //   MIXED: arr[0] = float4 (x_hi, y_hi, z_hi, G m), arr[1] = float4 (x_lo,
 //          y_lo, z_lo, vx), arr[2] = float2 (vy, vz)
+//   Position (and DS velocity) hi/lo pairs are grid-aligned splits
+//   (grid_split): every hi part of the layout lies on one power-of-two grid.
 //   DS   : arr[0] = float4 (x_hi, y_hi, z_hi, Gm_hi), arr[1] = float4 (x_lo,
 //          y_lo, z_lo, Gm_lo), arr[2] = float4 (vx_hi, vy_hi, vz_hi, 0),
 //          arr[3] = float4 (vx_lo, vy_lo, vz_lo, 0)

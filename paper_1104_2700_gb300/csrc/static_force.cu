@@ -28,7 +28,7 @@ static __device__ __align__(256) unsigned char nb_static_scratch[NB_STATIC_SCRAT
 
 constexpr int STATIC_CTAS_PER_SM = 4;  // fixes the number of warps, hence the scratch size
 constexpr int MAX_DEVICES = 64;
-constexpr size_t CONTROL_BYTES = 256;  // status word and n_act
+constexpr size_t CONTROL_BYTES = 256;  // status word, n_act, layout bounds
 
 struct DeviceSetup {
     bool ready = false;
@@ -59,11 +59,12 @@ Plan plan_for(int64_t n, int grid)
     return p;
 }
 
-// Predicted particles (device, n x 3 doubles) -> the double-single j layout,
-// with zero-mass ghosts far away up to n_pad.
+// Predicted particles (device, n x 3 doubles) -> the double-single j layout
+// (grid-aligned splits on the grids of `bound`), with zero-mass ghosts far
+// away up to n_pad.
 __global__ void static_layout_kernel(int64_t n, int64_t n_pad, const double* m, const double* r,
-                                     const double* v, double G, float4* A, float4* B, float4* C,
-                                     float4* D)
+                                     const double* v, double G, const uint32_t* bound, float4* A,
+                                     float4* B, float4* C, float4* D)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_pad) return;
@@ -80,13 +81,17 @@ __global__ void static_layout_kernel(int64_t n, int64_t n_pad, const double* m, 
         u[0] = u[1] = u[2] = 0.0;
         gm = 0.0;
     }
+    const nb::GridQuantum gx = nb::grid_quantum(bound[0]), gv = nb::grid_quantum(bound[1]);
     float xh[3], xl[3], vh[3], vl[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        xh[c] = __double2float_rn(x[c]);
-        xl[c] = __double2float_rn(x[c] - static_cast<double>(xh[c]));
-        vh[c] = __double2float_rn(u[c]);
-        vl[c] = __double2float_rn(u[c] - static_cast<double>(vh[c]));
+        if (i < n) {
+            nb::grid_split(x[c], gx, xh[c], xl[c]);
+        } else {
+            xh[c] = static_cast<float>(x[c]);
+            xl[c] = 0.f;
+        }
+        nb::grid_split(u[c], gv, vh[c], vl[c]);
     }
     const float gh = __double2float_rn(gm);
     const float gl = __double2float_rn(gm - static_cast<double>(gh));
@@ -154,17 +159,19 @@ extern "C" nb_status nb_force_static(int64_t n, const double* m, const double* r
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     uint32_t* status = reinterpret_cast<uint32_t*>(s->base);
     int32_t* n_act_dev = reinterpret_cast<int32_t*>(s->base + 4);
+    uint32_t* bound = reinterpret_cast<uint32_t*>(s->base + 8);
     uint32_t* counters = reinterpret_cast<uint32_t*>(s->base + p.counters);
     float4* L = reinterpret_cast<float4*>(s->base + p.layout);
     double* scratch = reinterpret_cast<double*>(s->base + p.scratch);
-    // The array keeps whatever the previous call left: the status word and
-    // the arrival counters must start from zero.
-    if (cudaMemsetAsync(status, 0, sizeof(uint32_t), cs) != cudaSuccess) return NB_ECUDA;
+    // The array keeps whatever the previous call left: the status word, the
+    // layout bounds and the arrival counters must start from zero.
+    if (cudaMemsetAsync(status, 0, 4 * sizeof(uint32_t), cs) != cudaSuccess) return NB_ECUDA;
     if (cudaMemsetAsync(counters, 0, p.counter_words * sizeof(uint32_t), cs) != cudaSuccess)
         return NB_ECUDA;
     if (nb::set_scalars_launch(n_act_dev, n_act, nullptr, 0.0, cs) != cudaSuccess) return NB_ECUDA;
+    if (nb::bounds_launch(r, v, 3 * n, bound, cs) != cudaSuccess) return NB_ECUDA;
     static_layout_kernel<<<static_cast<unsigned>((p.n_pad + 255) / 256), 256, 0, cs>>>(
-        n, p.n_pad, m, r, v, G, L, L + p.n_pad, L + 2 * p.n_pad, L + 3 * p.n_pad);
+        n, p.n_pad, m, r, v, G, bound, L, L + p.n_pad, L + 2 * p.n_pad, L + 3 * p.n_pad);
     if (cudaGetLastError() != cudaSuccess) return NB_ECUDA;
     nb::ForceArgs f;
     f.prec = nb::Prec::DS;

@@ -95,6 +95,7 @@ def load(path: str = LIB_PATH):
         "nb_num_systems": (c_int32, [P]),
         "nb_autotune": (c_int32, [P, POINTER(NbTuning)]),
         "nb_selftest_timeout": (c_int32, [P]),
+        "nb_measure_peaks": (c_int32, [c_int32, POINTER(c_double), POINTER(c_double)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -214,6 +215,19 @@ def nb_selftest_timeout(ctx):
 def nb_force_static(n, m, r, v, eps, G, n_act, idx, acc, jerk, pot, stream):
     """Allocation-free force evaluation on device pointers (see nbody.h)."""
     return load().nb_force_static(n, m, r, v, eps, G, n_act, idx, acc, jerk, pot, stream)
+
+
+def nb_measure_peaks(device, fp32_ref, fp64_ref):
+    return load().nb_measure_peaks(device, fp32_ref, fp64_ref)
+
+
+def measure_peaks(device=0):
+    """Measured (FP32, FP64) FMA throughput of the device in TFLOP/s."""
+    f32, f64 = c_double(), c_double()
+    st = nb_measure_peaks(int(device), ctypes.byref(f32), ctypes.byref(f64))
+    if st != NB_OK:
+        raise NbError(st, "nb_measure_peaks failed")
+    return f32.value, f64.value
 
 
 # --- marshalling helpers ------------------------------------------------------
