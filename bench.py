@@ -62,9 +62,9 @@ def parse_args():
     p.add_argument("--no-extra", action="store_true",
                    help="skip the N = 65536 roofline and the ensemble measurement")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
-    p.add_argument("--modes", default="mixed,ds,fp64",
+    p.add_argument("--modes", default="mixed,hybrid,ds,fp64",
                    help="comma-separated precision modes to time")
-    p.add_argument("--profile", choices=["mixed", "ds", "fp64"], default=None,
+    p.add_argument("--profile", choices=["mixed", "hybrid", "ds", "fp64"], default=None,
                    help="only run --launches force launches (for ncu), no timing")
     p.add_argument("--profile-nact", type=int, default=16384)
     p.add_argument("--launches", type=int, default=3)
@@ -111,8 +111,9 @@ def run_profile(args):
     m, r, v = WL.particles()
     idx = torch.from_numpy(ics.permutation(n, WL.seed)[:args.profile_nact].astype(np.int32)).cuda()
     with nbody.Context(args.profile) as ctx:
-        z = np.zeros((n, 3))
-        ctx.set_state(m, r, v, z, z, np.zeros(n), np.full(n, 1.0 / 16), eps, WL.eta)
+        # loading evaluates every force once (the launch ncu skips with -s 1)
+        # and leaves a, j in the state for the hybrid near-pair test
+        ctx.set_particles(m, r, v, eps, WL.eta)
         ctx.predict(0.0)
         for _ in range(args.launches):
             ctx.force(idx)
@@ -241,19 +242,20 @@ def run_ours(args):
     inter_per_step = sum(k * n for k in NACTS)
     all_idx = np.arange(n, dtype=np.int32)
 
-    def forces_at_t0(ctx):
-        ctx.set_state(m, r, v, np.zeros((n, 3)), np.zeros((n, 3)), np.zeros(n),
-                      np.full(n, 1.0 / 16), eps, eta)
+    def forces_at_t0(ctx, a0, j0):
+        # the state's a, j matter only to the hybrid precision's near-pair test
+        ctx.set_state(m, r, v, a0, j0, np.zeros(n), np.full(n, 1.0 / 16), eps, eta)
         ctx.predict(0.0)
         return ctx.force(all_idx)
 
     # Accuracy reference for every particle: the FP64 GPU path (which the
     # parity tests hold within 1e-10 of the FP64 CPU oracle on this workload).
     with nbody.Context("fp64", device=local, stream=stream) as ref_ctx:
-        a_ref, j_ref, p_ref = forces_at_t0(ref_ctx)
+        z3 = np.zeros((n, 3))
+        a_ref, j_ref, p_ref = forces_at_t0(ref_ctx, z3, z3)
 
     def accuracy(ctx):
-        a, j, p = forces_at_t0(ctx)
+        a, j, p = forces_at_t0(ctx, a_ref, j_ref)
         ea = np.linalg.norm(a - a_ref, axis=1) / np.linalg.norm(a_ref, axis=1)
         ej = np.linalg.norm(j - j_ref, axis=1) / np.linalg.norm(j_ref, axis=1)
         ep = np.abs(p - p_ref) / np.abs(p_ref)
@@ -326,6 +328,54 @@ def run_ours(args):
         e1.synchronize()
         return e0.elapsed_time(e1) / 1e3 / reps
 
+    def breakdown(ctx, dstates, reps=50):
+        """Per block size, warm CUDA-event times (us) of: the state restore
+        alone (bench scaffolding), restore + one block step, and the force
+        launch alone on that block's active list."""
+        out = {}
+        for k, s in zip(NACTS, dstates):
+            def restore():
+                ctx.set_state(s["m"], s["r"], s["v"], s["a"], s["j"], s["t"], s["dt"], eps, eta)
+
+            def step():
+                restore()
+                ctx.block_step(1.0)
+
+            row = {}
+            for name, fn in (("restore_us", restore), ("restore_and_block_step_us", step)):
+                fn()
+                ctx.synchronize()
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=stream):
+                    fn()
+                torch.cuda.set_stream(stream)
+                for _ in range(3):
+                    g.replay()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps):
+                    g.replay()
+                e1.record(stream)
+                e1.synchronize()
+                row[name] = e0.elapsed_time(e1) * 1e3 / reps
+                del g
+            restore()
+            ctx.predict(0.0)
+            idx_k = torch.from_numpy(np.sort(perm[:k]).astype(np.int32)).to(dev)
+            for _ in range(3):
+                ctx.force(idx_k)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                ctx.force(idx_k)
+            e1.record(stream)
+            e1.synchronize()
+            row["force_us"] = e0.elapsed_time(e1) * 1e3 / reps
+            row["block_step_us"] = row["restore_and_block_step_us"] - row["restore_us"]
+            row["non_force_us"] = row["block_step_us"] - row["force_us"]
+            out[str(k)] = row
+        return out
+
     modes = {}
     contexts = {}
     clocks = ClockSampler(local)
@@ -341,12 +391,14 @@ def run_ours(args):
         ctx, states, dstates, total = measure(prec, k, args.warmup)
         c = sampler.stop()
         t_force = force_launch_time(ctx, dstates[-1])
+        per_nact = breakdown(ctx, dstates) if prec != "fp64" else None
         acc = accuracy(ctx)
         modes[prec] = {"value": world * inter_per_step * k / total, "unit": UNIT, "steps": k,
                        "ms_per_step": 1e3 * total / k,
                        "force_launch_ms_nact_N": t_force * 1e3,
                        "autotuned_launch": ctx.tuning,
                        "force_interactions_per_s": n * n / t_force,
+                       "per_block_size": per_nact,
                        "accuracy_vs_fp64": acc, "clocks": c}
         contexts[prec] = (ctx, states)
     gate = {p: max(mo["accuracy_vs_fp64"][q] for q in ("acc_rel_max", "jerk_rel_max",
@@ -397,7 +449,8 @@ def run_ours(args):
                 "issue": issue,
                 "traffic_source": f"profiles/force_{p}_n16384.md (ncu, kernel source "
                                   f"hash {kernel_source_hash()}; null if the kernel changed)",
-                "algorithmic_bytes_per_launch": n * {"mixed": 40, "ds": 64, "fp64": 64}[p],
+                "algorithmic_bytes_per_launch": n * {"mixed": 40, "ds": 64, "hybrid": 64,
+                                                     "fp64": 64}[p],
                 "launch_ms": modes[p]["force_launch_ms_nact_N"],
                 "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x "
                               f"{sm_max:.0f} MHz max SM clock (derived; peak_measured is this "
@@ -405,6 +458,7 @@ def run_ours(args):
                               f"60 flop per interaction (paper convention)"}
 
     kname = {"mixed": "force_kernel<PolicyMixed<2>,2>", "ds": "force_kernel<PolicyDS<1>,1>",
+             "hybrid": "force_kernel<PolicyHybrid<1>,1>",
              "fp64": "force_kernel<PolicyFP64<1>,1>"}
     roofline = roofline_of(head, kname[head])
     roofline_mixed = roofline_of("mixed", kname["mixed"]) if "mixed" in modes else None
@@ -489,7 +543,8 @@ def run_ours(args):
 # (select), predict, the two force launch variants (each returns at once
 # outside its n_act window), correct.
 LAUNCHES_PER_BLOCK_STEP = 12
-DTYPES = {"ds": "f32x2 (double-single on the FP32 pipes)", "mixed": "f32", "fp64": "f64"}
+DTYPES = {"ds": "f32x2 (double-single on the FP32 pipes)", "mixed": "f32", "fp64": "f64",
+          "hybrid": "f32 (far pairs) + f32x2 double-single (near pairs)"}
 
 
 def extra_measurements(nbody, torch, dev, stream, world, peak32):
@@ -507,7 +562,7 @@ def extra_measurements(nbody, torch, dev, stream, world, peak32):
     n = wl.n
     idx = torch.arange(n, dtype=torch.int32, device=dev)
     roof = {}
-    for prec in ("mixed", "ds"):
+    for prec in ("mixed", "hybrid", "ds"):
         with nbody.Context(prec, device=dev.index, stream=stream) as ctx:
             ctx.set_particles(m, r, v, wl.eps, wl.eta)
             tun = ctx.autotune()
@@ -529,9 +584,9 @@ def extra_measurements(nbody, torch, dev, stream, world, peak32):
     sizes, off, ms, rs, vs, eps = ics.ensemble(**{k: ics.ENSEMBLE_K256[k]
                                                   for k in ("k", "size_seed", "member_seed0")})
     ens = {"systems": int(len(sizes)), "particles": int(off[-1]), "t_end": 1.0 / 32,
-           "precision_note": "DS only: with FP32 pair arithmetic (MIXED) the Aarseth "
-                             "timesteps collapse (see precision_ablation)"}
-    for prec in ("ds",):
+           "precision_note": "hybrid and DS: with FP32 pair arithmetic (MIXED) the "
+                             "Aarseth timesteps collapse (see precision_ablation)"}
+    for prec in ("hybrid", "ds"):
         with nbody.Context(prec, device=dev.index, stream=stream) as ctx:
             ctx.set_ensemble(off, ms, rs, vs, eps, ics.ENSEMBLE_K256["eta"])
             ctx.autotune()
@@ -559,7 +614,7 @@ def extra_measurements(nbody, torch, dev, stream, world, peak32):
                  (ms[off[q]:off[q + 1]], rs[off[q]:off[q + 1]], vs[off[q]:off[q + 1]], float(eps[q]))}
     for name, (m1, r1, v1, e1) in cases.items():
         row = {}
-        for prec in ("fp64", "ds", "mixed"):
+        for prec in ("fp64", "ds", "hybrid", "mixed"):
             # dt_max = t_end, so that every particle ends synchronised at t_end
             with nbody.Context(prec, device=dev.index, stream=stream, dt_max=1.0 / 64) as ctx:
                 ctx.set_particles(m1, r1, v1, e1, 0.02)
@@ -703,8 +758,8 @@ def run_integration(args):
     from paper_1104_2700_gb300 import build as nb_build
     from paper_1104_2700_gb300 import nbody
     nb_build.build()
-    modes = [x for x in args.modes.split(",") if x] if args.modes != "mixed,ds,fp64" \
-        else ["ds", "fp64"]
+    modes = [x for x in args.modes.split(",") if x] if args.modes != "mixed,hybrid,ds,fp64" \
+        else ["hybrid", "ds", "fp64"]
     m, r, v = wl.particles()
     out = {"metric": "block-step integration interactions/s", "unit": UNIT,
            "workload": wl.name, "n": wl.n, "eps": wl.eps, "eta": wl.eta, "t_end": t_end,

@@ -342,6 +342,9 @@ nb::ForceArgs force_args(nb_ctx* c, Prec p, const nb::JLayout& jl, const int32_t
     f.jerk = c->jerk1;
     f.pot = c->pot1;
     f.scratch = c->scratch;
+    f.st_a = c->st.a;
+    f.st_j = c->st.j;
+    f.bound_v = c->st.bound + 1;
     f.counters = c->counters;
     f.counter_stride = c->counter_stride;
     f.status = c->status_dev;
@@ -516,7 +519,7 @@ nb_status nb_create(const nb_config* cfg, nb_ctx** out)
 {
     if (!cfg || !out) return NB_EINVAL;
     *out = nullptr;
-    if (cfg->precision < NB_FP64 || cfg->precision > NB_DS) return NB_EINVAL;
+    if (cfg->precision < NB_FP64 || cfg->precision > NB_HYBRID) return NB_EINVAL;
     if (!is_pow2(cfg->dt_max) || !(cfg->dt_min > 0.0) || cfg->dt_min > cfg->dt_max) return NB_EINVAL;
     if (!(cfg->eta_start > 0.0) || !std::isfinite(cfg->G)) return NB_EINVAL;
     nb_ctx* c = new (std::nothrow) nb_ctx;
@@ -998,7 +1001,7 @@ nb_status nb_autotune(nb_ctx* c, nb_tuning* out)
     int max_grid = 0;
     for (int it : its) {
         const int occ = nb::force_ctas_per_sm(c->prec, it);
-        for (int cps : {1, 2, 3, 4, 6, 8})
+        for (int cps : {1, 2, 3, 4, 5, 6, 8})
             if (cps <= occ) {
                 cands.push_back({it, cps, {0, 0, 0, 0}});
                 max_grid = std::max(max_grid, cps * c->num_sms);

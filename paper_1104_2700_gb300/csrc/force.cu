@@ -51,6 +51,11 @@ struct ForceParams {
     const int64_t* cl_off;
     const int64_t* cl_joff;
     const double* cl_eps2;
+    // Hybrid precision: the state's a, j (SoA, [c*n + i]) and the velocity
+    // bound of the layout split (float bits).
+    const double* st_a;
+    const double* st_j;
+    const uint32_t* bound_v;
 };
 
 // ---------------------------------------------------------------------------
@@ -75,7 +80,7 @@ struct PolicyFP64 {
         __device__ void zero() { ax = ay = az = jx = jy = jz = ph = 0.0; }
     };
 
-    __device__ static void load_i(const ForceParams& f, int p, I& s)
+    __device__ static void load_i(const ForceParams& f, int p, int, I& s)
     {
         s.p = p;
         if (p < 0) {
@@ -155,7 +160,7 @@ struct PolicyMixed {
         }
     };
 
-    __device__ static void load_i(const ForceParams& f, int p, I& s)
+    __device__ static void load_i(const ForceParams& f, int p, int, I& s)
     {
         s.p = p;
         if (p < 0) {
@@ -245,6 +250,130 @@ __device__ __forceinline__ void ds_mul(float ah, float al, float bh, float bl, f
     e = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, e));
 }
 
+// i state and accumulators of the double-single pair (DS and HYBRID).
+struct DSI {
+    float xh, yh, zh, xl, yl, zl;
+    float vxh, vyh, vzh, vxl, vyl, vzl;
+    int p;
+};
+struct DSAccs {
+    DSAcc ax, ay, az, jx, jy, jz, ph;
+    __device__ void zero()
+    {
+        ax.zero(), ay.zero(), az.zero(), jx.zero(), jy.zero(), jz.zero(), ph.zero();
+    }
+    __device__ void values(double (&v)[7]) const
+    {
+        v[0] = ax.value(), v[1] = ay.value(), v[2] = az.value();
+        v[3] = jx.value(), v[4] = jy.value(), v[5] = jz.value();
+        v[6] = -ph.value();
+    }
+};
+
+__device__ __forceinline__ void ds_load_i(const ForceParams& f, int p, DSI& s)
+{
+    s.p = p;
+    if (p < 0) {
+        s.xh = s.yh = s.zh = s.xl = s.yl = s.zl = 0.f;
+        s.vxh = s.vyh = s.vzh = s.vxl = s.vyl = s.vzl = 0.f;
+        return;
+    }
+    const float4 A = __ldg(static_cast<const float4*>(f.jl0) + p);
+    const float4 B = __ldg(static_cast<const float4*>(f.jl1) + p);
+    const float4 C = __ldg(static_cast<const float4*>(f.jl2) + p);
+    const float4 D = __ldg(static_cast<const float4*>(f.jl3) + p);
+    s.xh = A.x, s.yh = A.y, s.zh = A.z;
+    s.xl = B.x, s.yl = B.y, s.zl = B.z;
+    s.vxh = C.x, s.vyh = C.y, s.vzh = C.z;
+    s.vxl = D.x, s.vyl = D.y, s.vzl = D.z;
+}
+
+// One pair (i = s, j = layout record A..D at slot j) in double-single,
+// added to the accumulators.  With MASK the self pair (j == s.p) adds zero.
+template <bool MASK>
+__device__ __forceinline__ void ds_pair(const float4& A, const float4& B, const float4& C,
+                                        const float4& D, const DSI& s, float e2h, float e2l,
+                                        int64_t j, DSAccs& ac)
+{
+    float dxh, dxl, dyh, dyl, dzh, dzl;
+    grid_diff(A.x, B.x, s.xh, s.xl, dxh, dxl);
+    grid_diff(A.y, B.y, s.yh, s.yl, dyh, dyl);
+    grid_diff(A.z, B.z, s.zh, s.zl, dzh, dzl);
+    float vxh, vxl, vyh, vyl, vzh, vzl;
+    grid_diff(C.x, D.x, s.vxh, s.vxl, vxh, vxl);
+    grid_diff(C.y, D.y, s.vyh, s.vyl, vyh, vyl);
+    grid_diff(C.z, D.z, s.vzh, s.vzl, vzh, vzl);
+    // r^2 = dx^2 + dy^2 + dz^2 + eps^2 (all terms >= 0)
+    float px, pxe, py, pye, pz, pze;
+    ds_mul(dxh, dxl, dxh, dxl, px, pxe);
+    ds_mul(dyh, dyl, dyh, dyl, py, pye);
+    ds_mul(dzh, dzl, dzh, dzl, pz, pze);
+    float s1, e1, s2, e2, r2h, e3;
+    two_sum(px, py, s1, e1);
+    two_sum(s1, pz, s2, e2);
+    two_sum(s2, e2h, r2h, e3);
+    const float r2l = __fadd_rn(__fadd_rn(__fadd_rn(pxe, pye), __fadd_rn(pze, e1)),
+                                __fadd_rn(__fadd_rn(e2, e3), e2l));
+    // 1/r: hardware estimate y, refined by the exact residual
+    // h = 1 - r^2 y^2, 1/r = y (1 + h/2 + O(h^2)).
+    float y = rsqrtf(r2h);
+    if (MASK) y = (j == s.p) ? 0.f : y;
+    float y2, ey2;
+    two_prod(y, y, y2, ey2);
+    float h = __fmaf_rn(-r2h, y2, 1.f);
+    h = __fmaf_rn(-r2h, ey2, h);
+    h = __fmaf_rn(-r2l, y2, h);
+    if (MASK) h = (j == s.p) ? 0.f : h;
+    const float ril = __fmul_rn(0.5f, __fmul_rn(y, h));
+    // m / r and 1 / r^2, then g = m / r^3
+    float mrh, mrl;
+    ds_mul(A.w, B.w, y, ril, mrh, mrl);
+    const float ri2h = y2;
+    const float ri2l = __fmaf_rn(__fadd_rn(y, y), ril, ey2);
+    float gh, gl;
+    ds_mul(mrh, mrl, ri2h, ri2l, gh, gl);
+    // acceleration terms g * dr
+    float t0, t1;
+    ds_mul(gh, gl, dxh, dxl, t0, t1);
+    ac.ax.add(t0, t1);
+    ds_mul(gh, gl, dyh, dyl, t0, t1);
+    ac.ay.add(t0, t1);
+    ds_mul(gh, gl, dzh, dzl, t0, t1);
+    ac.az.add(t0, t1);
+    ac.ph.add(mrh, mrl);
+    // r.v, then tau = -3 (r.v) / r^2
+    float qx, qxe, qy, qye, qz, qze;
+    ds_mul(dxh, dxl, vxh, vxl, qx, qxe);
+    ds_mul(dyh, dyl, vyh, vyl, qy, qye);
+    ds_mul(dzh, dzl, vzh, vzl, qz, qze);
+    float u1, f1, rvh, f2;
+    two_sum(qx, qy, u1, f1);
+    two_sum(u1, qz, rvh, f2);
+    const float rvl = __fadd_rn(__fadd_rn(qxe, qye), __fadd_rn(__fadd_rn(qze, f1), f2));
+    float ch, cl;
+    two_prod(-3.f, ri2h, ch, cl);
+    cl = __fmaf_rn(-3.f, ri2l, cl);
+    float tauh, taul;
+    ds_mul(rvh, rvl, ch, cl, tauh, taul);
+    // jerk terms g * (dv + tau dr)
+    float wh, wl, th_, tl_, we;
+    ds_mul(tauh, taul, dxh, dxl, th_, tl_);
+    two_sum(vxh, th_, wh, we);
+    wl = __fadd_rn(we, __fadd_rn(vxl, tl_));
+    ds_mul(gh, gl, wh, wl, t0, t1);
+    ac.jx.add(t0, t1);
+    ds_mul(tauh, taul, dyh, dyl, th_, tl_);
+    two_sum(vyh, th_, wh, we);
+    wl = __fadd_rn(we, __fadd_rn(vyl, tl_));
+    ds_mul(gh, gl, wh, wl, t0, t1);
+    ac.jy.add(t0, t1);
+    ds_mul(tauh, taul, dzh, dzl, th_, tl_);
+    two_sum(vzh, th_, wh, we);
+    wl = __fadd_rn(we, __fadd_rn(vzl, tl_));
+    ds_mul(gh, gl, wh, wl, t0, t1);
+    ac.jz.add(t0, t1);
+}
+
 template <int IT>
 struct PolicyDS {
     static constexpr int NARR = 4;
@@ -252,36 +381,10 @@ struct PolicyDS {
     static constexpr int TILE_BYTES = TJ * 64;
     static constexpr int STAGES = 2;
 
-    struct I {
-        float xh, yh, zh, xl, yl, zl;
-        float vxh, vyh, vzh, vxl, vyl, vzl;
-        int p;
-    };
-    struct Acc {
-        DSAcc ax, ay, az, jx, jy, jz, ph;
-        __device__ void zero()
-        {
-            ax.zero(), ay.zero(), az.zero(), jx.zero(), jy.zero(), jz.zero(), ph.zero();
-        }
-    };
+    using I = DSI;
+    using Acc = DSAccs;
 
-    __device__ static void load_i(const ForceParams& f, int p, I& s)
-    {
-        s.p = p;
-        if (p < 0) {
-            s.xh = s.yh = s.zh = s.xl = s.yl = s.zl = 0.f;
-            s.vxh = s.vyh = s.vzh = s.vxl = s.vyl = s.vzl = 0.f;
-            return;
-        }
-        const float4 A = __ldg(static_cast<const float4*>(f.jl0) + p);
-        const float4 B = __ldg(static_cast<const float4*>(f.jl1) + p);
-        const float4 C = __ldg(static_cast<const float4*>(f.jl2) + p);
-        const float4 D = __ldg(static_cast<const float4*>(f.jl3) + p);
-        s.xh = A.x, s.yh = A.y, s.zh = A.z;
-        s.xl = B.x, s.yl = B.y, s.zl = B.z;
-        s.vxh = C.x, s.vyh = C.y, s.vzh = C.z;
-        s.vxl = D.x, s.vyl = D.y, s.vzl = D.z;
-    }
+    __device__ static void load_i(const ForceParams& f, int p, int, I& s) { ds_load_i(f, p, s); }
 
     template <bool MASK>
     __device__ static void tile(const unsigned char* buf, int64_t j0, const double eps2d,
@@ -300,95 +403,169 @@ struct PolicyDS {
             const float4 C = sC[k];
             const float4 D = sD[k];
 #pragma unroll
+            for (int q = 0; q < IT; ++q) ds_pair<MASK>(A, B, C, D, is[q], e2h, e2l, j0 + k, ac[q]);
+        }
+    }
+
+    __device__ static void values(const Acc& a, double (&v)[7]) { a.values(v); }
+};
+
+// Hybrid precision (no counterpart in the paper, which evaluates every pair
+// the same way): each pair in FP32 unless it is a near pair, which is
+// evaluated in double-single instead.  A pair is near when its acceleration
+// term could exceed THETA |a_i| or its jerk term THETA |j_i|:
+//   G m_j / r^2 <= THETA |a_i|          unless  r^2 < G m_j / (THETA |a_i|)
+//   4 G m_j |dv| / r^3 <= THETA |j_i|   unless  r^2 < (G m_j)^(2/3) (4 V_i / (THETA |j_i|))^(2/3)
+// with r^2 the softened distance, V_i = |v_i| + sqrt(3) B_v >= |v_j - v_i|,
+// and |a_i|, |j_i| the particle's values at its last correction (its state
+// a, j); a particle with no such values yet (a = j = 0) treats every pair as
+// near, so the first evaluation after a load is plain DS.  The FP32 terms of
+// the far pairs are summed in runs of HY_RUN consecutive j and each run is
+// folded into the double-single accumulators, so far-field rounding stays at
+// the FP32 level of each term and never accumulates; the rsqrt estimate is
+// refined once through its residual.  The near pairs, which carry the
+// cancellation that FP32 cannot resolve, are marked during the FP32 pass and
+// evaluated in DS after it, each lane walking its own list, so the warp runs
+// the DS pair about max-over-lanes(near pairs in the tile) times per tile.
+constexpr float HY_THETA = 0.1f;
+constexpr int HY_RUN = 8;
+
+struct HybridI : DSI {
+    float ca, cj;  // near test: r^2 < max(Gm_j * ca, (Gm_j)^(2/3) * cj)
+};
+
+template <int IT>
+struct PolicyHybrid {
+    static constexpr int NARR = 4;
+    __host__ __device__ static constexpr int elem(int a) { return a < 4 ? 16 : 0; }
+    static constexpr int TILE_BYTES = TJ * 64;
+    static constexpr int STAGES = 3;
+
+    using I = HybridI;
+    using Acc = DSAccs;
+
+    __device__ static void load_i(const ForceParams& f, int p, int particle, I& s)
+    {
+        ds_load_i(f, p, s);
+        s.ca = s.cj = 0.f;
+        if (p < 0) return;
+        const int64_t n = f.n;
+        double a2 = 0.0, j2 = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double a = f.st_a[c * n + particle], jj = f.st_j[c * n + particle];
+            a2 = fma(a, a, a2);
+            j2 = fma(jj, jj, j2);
+        }
+        const float A = static_cast<float>(sqrt(a2)), J = static_cast<float>(sqrt(j2));
+        const float vi = sqrtf(s.vxh * s.vxh + s.vyh * s.vyh + s.vzh * s.vzh);
+        const float V = vi + 1.7320509f * __uint_as_float(*f.bound_v) * 1.0001f;
+        // 1/0 = inf: no estimate yet, every pair is near
+        s.ca = 1.f / (HY_THETA * A);
+        const float x = 4.f * V / (HY_THETA * J);
+        const float cb = cbrtf(x);
+        s.cj = cb * cb;
+    }
+
+    template <bool MASK>
+    __device__ static void tile(const unsigned char* buf, int64_t j0, const double eps2d,
+                                I (&is)[IT], Acc (&ac)[IT])
+    {
+        static_assert(TJ == 64, "one 64-bit near mask per lane and tile");
+        const float4* sA = reinterpret_cast<const float4*>(buf);
+        const float4* sB = reinterpret_cast<const float4*>(buf + TJ * 16);
+        const float4* sC = reinterpret_cast<const float4*>(buf + TJ * 32);
+        const float4* sD = reinterpret_cast<const float4*>(buf + TJ * 48);
+        const float e2h = static_cast<float>(eps2d);
+        const float e2l = static_cast<float>(eps2d - static_cast<double>(e2h));
+        // Pass 1: every pair in FP32; near pairs add nothing here and are
+        // marked in a per-lane 64-bit mask (bit k = slot j0 + k).
+        uint32_t nlo[IT], nhi[IT];
+#pragma unroll
+        for (int q = 0; q < IT; ++q) nlo[q] = nhi[q] = 0u;
+#pragma unroll 1
+        for (int k0 = 0; k0 < TJ; k0 += HY_RUN) {
+            float ax[IT], ay[IT], az[IT], jx[IT], jy[IT], jz[IT], ph[IT];
+            uint32_t run[IT];
+#pragma unroll
             for (int q = 0; q < IT; ++q) {
-                const I& s = is[q];
-                float dxh, dxl, dyh, dyl, dzh, dzl;
-                grid_diff(A.x, B.x, s.xh, s.xl, dxh, dxl);
-                grid_diff(A.y, B.y, s.yh, s.yl, dyh, dyl);
-                grid_diff(A.z, B.z, s.zh, s.zl, dzh, dzl);
-                float vxh, vxl, vyh, vyl, vzh, vzl;
-                grid_diff(C.x, D.x, s.vxh, s.vxl, vxh, vxl);
-                grid_diff(C.y, D.y, s.vyh, s.vyl, vyh, vyl);
-                grid_diff(C.z, D.z, s.vzh, s.vzl, vzh, vzl);
-                // r^2 = dx^2 + dy^2 + dz^2 + eps^2 (all terms >= 0)
-                float px, pxe, py, pye, pz, pze;
-                ds_mul(dxh, dxl, dxh, dxl, px, pxe);
-                ds_mul(dyh, dyl, dyh, dyl, py, pye);
-                ds_mul(dzh, dzl, dzh, dzl, pz, pze);
-                float s1, e1, s2, e2, r2h, e3;
-                two_sum(px, py, s1, e1);
-                two_sum(s1, pz, s2, e2);
-                two_sum(s2, e2h, r2h, e3);
-                const float r2l = __fadd_rn(__fadd_rn(__fadd_rn(pxe, pye), __fadd_rn(pze, e1)),
-                                            __fadd_rn(__fadd_rn(e2, e3), e2l));
-                // 1/r: hardware estimate y, refined by the exact residual
-                // h = 1 - r^2 y^2, 1/r = y (1 + h/2 + O(h^2)).
-                float y = rsqrtf(r2h);
-                if (MASK) y = (j0 + k == s.p) ? 0.f : y;
-                float y2, ey2;
-                two_prod(y, y, y2, ey2);
-                float h = __fmaf_rn(-r2h, y2, 1.f);
-                h = __fmaf_rn(-r2h, ey2, h);
-                h = __fmaf_rn(-r2l, y2, h);
-                if (MASK) h = (j0 + k == s.p) ? 0.f : h;
-                const float ril = __fmul_rn(0.5f, __fmul_rn(y, h));
-                // m / r and 1 / r^2, then g = m / r^3
-                float mrh, mrl;
-                ds_mul(A.w, B.w, y, ril, mrh, mrl);
-                const float ri2h = y2;
-                const float ri2l = __fmaf_rn(__fadd_rn(y, y), ril, ey2);
-                float gh, gl;
-                ds_mul(mrh, mrl, ri2h, ri2l, gh, gl);
-                // acceleration terms g * dr
-                float t0, t1;
-                ds_mul(gh, gl, dxh, dxl, t0, t1);
-                ac[q].ax.add(t0, t1);
-                ds_mul(gh, gl, dyh, dyl, t0, t1);
-                ac[q].ay.add(t0, t1);
-                ds_mul(gh, gl, dzh, dzl, t0, t1);
-                ac[q].az.add(t0, t1);
-                ac[q].ph.add(mrh, mrl);
-                // r.v, then tau = -3 (r.v) / r^2
-                float qx, qxe, qy, qye, qz, qze;
-                ds_mul(dxh, dxl, vxh, vxl, qx, qxe);
-                ds_mul(dyh, dyl, vyh, vyl, qy, qye);
-                ds_mul(dzh, dzl, vzh, vzl, qz, qze);
-                float u1, f1, rvh, f2;
-                two_sum(qx, qy, u1, f1);
-                two_sum(u1, qz, rvh, f2);
-                const float rvl = __fadd_rn(__fadd_rn(qxe, qye), __fadd_rn(__fadd_rn(qze, f1), f2));
-                float ch, cl;
-                two_prod(-3.f, ri2h, ch, cl);
-                cl = __fmaf_rn(-3.f, ri2l, cl);
-                float tauh, taul;
-                ds_mul(rvh, rvl, ch, cl, tauh, taul);
-                // jerk terms g * (dv + tau dr)
-                float wh, wl, th_, tl_, we;
-                ds_mul(tauh, taul, dxh, dxl, th_, tl_);
-                two_sum(vxh, th_, wh, we);
-                wl = __fadd_rn(we, __fadd_rn(vxl, tl_));
-                ds_mul(gh, gl, wh, wl, t0, t1);
-                ac[q].jx.add(t0, t1);
-                ds_mul(tauh, taul, dyh, dyl, th_, tl_);
-                two_sum(vyh, th_, wh, we);
-                wl = __fadd_rn(we, __fadd_rn(vyl, tl_));
-                ds_mul(gh, gl, wh, wl, t0, t1);
-                ac[q].jy.add(t0, t1);
-                ds_mul(tauh, taul, dzh, dzl, th_, tl_);
-                two_sum(vzh, th_, wh, we);
-                wl = __fadd_rn(we, __fadd_rn(vzl, tl_));
-                ds_mul(gh, gl, wh, wl, t0, t1);
-                ac[q].jz.add(t0, t1);
+                ax[q] = ay[q] = az[q] = jx[q] = jy[q] = jz[q] = ph[q] = 0.f;
+                run[q] = 0u;
+            }
+#pragma unroll 4
+            for (int u = 0; u < HY_RUN; ++u) {
+                const int k = k0 + u;
+                const float4 A = sA[k];
+                const float4 B = sB[k];
+                const float4 C = sC[k];
+                const float4 D = sD[k];
+#pragma unroll
+                for (int q = 0; q < IT; ++q) {
+                    const DSI& s = is[q];
+                    // hi parts share one grid, so each hi difference is exact
+                    const float dx = (A.x - s.xh) + (B.x - s.xl);
+                    const float dy = (A.y - s.yh) + (B.y - s.yl);
+                    const float dz = (A.z - s.zh) + (B.z - s.zl);
+                    const float dvx = (C.x - s.vxh) + (D.x - s.vxl);
+                    const float dvy = (C.y - s.vyh) + (D.y - s.vyl);
+                    const float dvz = (C.z - s.vzh) + (D.z - s.vzl);
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, e2h)));
+                    bool near = r2 < fmaxf(A.w * is[q].ca, C.w * is[q].cj);
+                    const bool self = MASK && (j0 + k == s.p);
+                    near = near && !self;
+                    // rsqrt refined once: y (1 + h/2), h = 1 - r^2 y^2
+                    float y = rsqrtf(r2);
+                    const float yy = y * y;
+                    float h = fmaf(-r2, yy, 1.f);
+                    h = fmaf(-r2, fmaf(y, y, -yy), h);
+                    y = fmaf(0.5f * y, h, y);
+                    if (self || near) y = 0.f;
+                    const float mr = A.w * y;
+                    const float ri2 = y * y;
+                    const float g = mr * ri2;
+                    const float rv = fmaf(dx, dvx, fmaf(dy, dvy, dz * dvz));
+                    const float t = rv * (-3.f * ri2);
+                    ax[q] = fmaf(g, dx, ax[q]);
+                    ay[q] = fmaf(g, dy, ay[q]);
+                    az[q] = fmaf(g, dz, az[q]);
+                    jx[q] = fmaf(g, fmaf(t, dx, dvx), jx[q]);
+                    jy[q] = fmaf(g, fmaf(t, dy, dvy), jy[q]);
+                    jz[q] = fmaf(g, fmaf(t, dz, dvz), jz[q]);
+                    ph[q] += mr;
+                    run[q] |= static_cast<uint32_t>(near) << u;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < IT; ++q) {
+                ac[q].ax.fold(ax[q]), ac[q].ay.fold(ay[q]), ac[q].az.fold(az[q]);
+                ac[q].jx.fold(jx[q]), ac[q].jy.fold(jy[q]), ac[q].jz.fold(jz[q]);
+                ac[q].ph.fold(ph[q]);
+                if (k0 < 32) nlo[q] |= run[q] << k0;
+                else nhi[q] |= run[q] << (k0 - 32);
+            }
+        }
+        // Pass 2: the near pairs in double-single, each lane walking its own
+        // mask; the warp loops max_lane(popcount) times, not once per j.
+#pragma unroll
+        for (int q = 0; q < IT; ++q) {
+            uint32_t lo = nlo[q], hi = nhi[q];
+            while (__any_sync(0xffffffffu, (lo | hi) != 0u)) {
+                if ((lo | hi) != 0u) {
+                    int k;
+                    if (lo) {
+                        k = __ffs(lo) - 1;
+                        lo &= lo - 1u;
+                    } else {
+                        k = 32 + __ffs(hi) - 1;
+                        hi &= hi - 1u;
+                    }
+                    ds_pair<false>(sA[k], sB[k], sC[k], sD[k], is[q], e2h, e2l, j0 + k, ac[q]);
+                }
             }
         }
     }
 
-    __device__ static void values(const Acc& a, double (&v)[7])
-    {
-        v[0] = a.ax.value(), v[1] = a.ay.value(), v[2] = a.az.value();
-        v[3] = a.jx.value(), v[4] = a.jy.value(), v[5] = a.jz.value();
-        v[6] = -a.ph.value();
-    }
+    __device__ static void values(const Acc& a, double (&v)[7]) { a.values(v); }
 };
 
 template <class K>
@@ -567,17 +744,17 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
 #pragma unroll
             for (int q = 0; q < IT; ++q) {
                 const int64_t a = gi.act_begin + q * 32 + lane;
-                int p = -1;
+                int p = -1, particle = -1;
                 if (a < gi.act_begin + gi.act_count) {
-                    p = f.idx[a];
-                    if (p < 0 || p >= f.n) {
+                    particle = f.idx[a];
+                    if (particle < 0 || particle >= f.n) {
                         atomicOr(f.status, ST_BADINDEX);
-                        p = -1;
+                        particle = -1;
                     } else {
-                        p = static_cast<int>(p + gi.pj_shift);
+                        p = static_cast<int>(particle + gi.pj_shift);
                     }
                 }
-                K::load_i(f, p, is[q]);
+                K::load_i(f, p, particle, is[q]);
                 ac[q].zero();
             }
         }
@@ -708,6 +885,9 @@ const void* kernel_ptr(Prec p, int it, bool ens = false)
     case Prec::DS:
         if (it == 1) return kfn<PolicyDS<1>, 1>(ens);
         return nullptr;
+    case Prec::HYBRID:
+        if (it == 1) return kfn<PolicyHybrid<1>, 1>(ens);
+        return nullptr;
     }
     return nullptr;
 }
@@ -720,6 +900,7 @@ int jlayout_narr(Prec p)
     case Prec::FP64: return 2;
     case Prec::MIXED: return 3;
     case Prec::DS: return 4;
+    case Prec::HYBRID: return 4;
     }
     return 0;
 }
@@ -730,6 +911,7 @@ int jlayout_elem_bytes(Prec p, int k)
     case Prec::FP64: return k < 2 ? 32 : 0;
     case Prec::MIXED: return k < 2 ? 16 : (k == 2 ? 8 : 0);
     case Prec::DS: return k < 4 ? 16 : 0;
+    case Prec::HYBRID: return k < 4 ? 16 : 0;
     }
     return 0;
 }
@@ -740,6 +922,7 @@ size_t force_smem_bytes(Prec p)
     case Prec::FP64: return (size_t)FORCE_WARPS * WarpSmem<PolicyFP64<1>>::BYTES;
     case Prec::MIXED: return (size_t)FORCE_WARPS * WarpSmem<PolicyMixed<1>>::BYTES;
     case Prec::DS: return (size_t)FORCE_WARPS * WarpSmem<PolicyDS<1>>::BYTES;
+    case Prec::HYBRID: return (size_t)FORCE_WARPS * WarpSmem<PolicyHybrid<1>>::BYTES;
     }
     return 0;
 }
@@ -819,6 +1002,11 @@ cudaError_t force_launch(const ForceArgs& a, cudaStream_t s)
     f.cl_off = a.plan.cl_off;
     f.cl_joff = a.plan.cl_joff;
     f.cl_eps2 = a.plan.cl_eps2;
+    f.st_a = a.st_a;
+    f.st_j = a.st_j;
+    f.bound_v = a.bound_v;
+    if (a.prec == Prec::HYBRID && (!f.st_a || !f.st_j || !f.bound_v))
+        return cudaErrorInvalidValue;
     void* args[] = {&f};
     return cudaLaunchKernel(fn, dim3(a.grid), dim3(FORCE_WARPS * 32), args,
                             force_smem_bytes(a.prec), s);

@@ -94,7 +94,9 @@ __global__ void predict_kernel(const StateDev st, const JLayout jl, const double
             for (int c = 0; c < 3; ++c) grid_split(vp[c], gv, vh[c], vl[c]);
             static_cast<float4*>(jl.arr[0])[q] = make_float4(hi[0], hi[1], hi[2], gh);
             static_cast<float4*>(jl.arr[1])[q] = make_float4(lo[0], lo[1], lo[2], gl);
-            static_cast<float4*>(jl.arr[2])[q] = make_float4(vh[0], vh[1], vh[2], 0.f);
+            // (G m)^(2/3): the hybrid precision's near-pair test
+            const float g23 = cbrtf(gh);
+            static_cast<float4*>(jl.arr[2])[q] = make_float4(vh[0], vh[1], vh[2], g23 * g23);
             static_cast<float4*>(jl.arr[3])[q] = make_float4(vl[0], vl[1], vl[2], 0.f);
         }
     }
@@ -137,7 +139,9 @@ cudaError_t predict_launch(const StateDev& st, Prec p, const JLayout& jl, double
                            const int32_t* n_act_dev, cudaStream_t s, const ClusterDev* cl)
 {
     if (st.n_pad <= 0) return cudaSuccess;
-    const int threads = 256;
+    // Small blocks: the predictor is FP64-pipe bound per SM (GB300's FP64
+    // rate is a small fraction of FP32), so it should reach every SM.
+    const int threads = 64;
     const unsigned blocks = static_cast<unsigned>((st.n_pad + threads - 1) / threads);
     const int32_t* jsrc = cl ? cl->jsrc : nullptr;
     const int32_t* cof = cl ? cl->cluster_of : nullptr;
@@ -149,6 +153,7 @@ cudaError_t predict_launch(const StateDev& st, Prec p, const JLayout& jl, double
         predict_kernel<1><<<blocks, threads, 0, s>>>(st, jl, G, t_bits, t_host, n_act_dev, jsrc, cof);
         break;
     case Prec::DS:
+    case Prec::HYBRID:  // same j layout
         predict_kernel<2><<<blocks, threads, 0, s>>>(st, jl, G, t_bits, t_host, n_act_dev, jsrc, cof);
         break;
     }

@@ -14,7 +14,7 @@ namespace nb {
 //           into compensated (double-single) accumulators.
 //   DS    - the same pair formulas evaluated in double-single ("float-float")
 //           arithmetic on the FP32 pipes with error-free transforms.
-enum class Prec : int { FP64 = 0, MIXED = 1, DS = 2 };
+enum class Prec : int { FP64 = 0, MIXED = 1, DS = 2, HYBRID = 3 };
 
 // Device Hermite state of one context, structure of arrays.  x, v, a, j
 // hold 3*n doubles: component c of particle i at [c*n + i].
@@ -46,9 +46,9 @@ cudaError_t bounds_launch(const double* a, const double* b, int64_t count, uint3
 //          y_lo, z_lo, vx), arr[2] = float2 (vy, vz)
 //   Position (and DS velocity) hi/lo pairs are grid-aligned splits
 //   (grid_split): every hi part of the layout lies on one power-of-two grid.
-//   DS   : arr[0] = float4 (x_hi, y_hi, z_hi, Gm_hi), arr[1] = float4 (x_lo,
-//          y_lo, z_lo, Gm_lo), arr[2] = float4 (vx_hi, vy_hi, vz_hi, 0),
-//          arr[3] = float4 (vx_lo, vy_lo, vz_lo, 0)
+//   DS, HYBRID: arr[0] = float4 (x_hi, y_hi, z_hi, Gm_hi), arr[1] = float4
+//          (x_lo, y_lo, z_lo, Gm_lo), arr[2] = float4 (vx_hi, vy_hi, vz_hi,
+//          (Gm)^(2/3)), arr[3] = float4 (vx_lo, vy_lo, vz_lo, 0)
 struct JLayout {
     void* arr[4] = {nullptr, nullptr, nullptr, nullptr};
 };
@@ -124,6 +124,10 @@ struct ForceArgs {
     long long wait_limit = 0;      // cycles per tile wait; 0 = about one second
     int32_t unfed_first_tile = 0;  // self-test of the timeout path only
     ForcePlan plan;      // ensemble plan (empty: one system)
+    // HYBRID only: the state's a, j (near-pair test) and the velocity bound.
+    const double* st_a = nullptr;
+    const double* st_j = nullptr;
+    const uint32_t* bound_v = nullptr;
 };
 
 cudaError_t force_setup(Prec p, int it);  // one-time attribute setup

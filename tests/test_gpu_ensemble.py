@@ -32,7 +32,7 @@ def _rel(x, ref):
     return np.linalg.norm(x - ref, axis=1) / np.linalg.norm(ref, axis=1)
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("ds", 1e-9)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("ds", 1e-9), ("hybrid", 1e-6)])
 def test_ensemble_force_equals_each_system_alone(gpu, orc, prec, tol):
     sizes = [100, 333, 1000, 64, 2049, 1]
     off, m, r, v, eps = _systems(sizes, 300)

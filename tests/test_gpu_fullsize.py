@@ -73,3 +73,45 @@ def test_force_large_n_sampled(gpu, orc, wl):
         err = max(_rel(acc, a0).max(), _rel(jerk, j0).max(),
                   (np.abs(pot - p0) / np.abs(p0)).max())
         assert err < tol, (prec, err)
+
+
+def _ctx_with_state(gpu, prec, m, r, v, eps, a, j):
+    n = len(m)
+    ctx = gpu.Context(prec)
+    ctx.set_state(m, r, v, a, j, np.zeros(n), np.full(n, 1.0 / 16), eps=eps, eta=0.02)
+    ctx.predict(0.0)
+    return ctx
+
+
+def test_force_sweep_n16384_hybrid_all_particles(gpu, sweep):
+    """Hybrid precision with the state's a, j set (the near-pair test uses
+    them): every particle of every active block within 1e-6."""
+    wl, m, r, v, (a0, j0, p0) = sweep
+    perm = ics.permutation(wl.n, wl.seed).astype(np.int32)
+    with _ctx_with_state(gpu, "hybrid", m, r, v, wl.eps, a0, j0) as ctx:
+        for n_act in ics.FORCE_SWEEP_NACT:
+            idx = perm[:n_act]
+            acc, jerk, pot = ctx.force(idx)
+            ea, ej = _rel(acc, a0[idx]), _rel(jerk, j0[idx])
+            ep = np.abs(pot - p0[idx]) / np.abs(p0[idx])
+            assert max(ea.max(), ej.max(), ep.max()) < 1e-6, n_act
+            assert np.median(ea) < 1e-7 and np.median(ej) < 1e-7
+
+
+@pytest.mark.parametrize("wl", [ics.MIXED_N64K, ics.SALPETER_N256K], ids=lambda w: w.name)
+def test_force_large_n_sampled_hybrid(gpu, orc, wl):
+    """Random plus the most central particles (largest cancellation); the
+    state holds the oracle's a, j at the sampled particles."""
+    m, r, v = wl.particles()
+    rad = np.linalg.norm(r, axis=1)
+    samp = np.unique(np.concatenate([ics.permutation(wl.n, 3)[:192],
+                                     np.argsort(rad)[:64]])).astype(np.int32)
+    a0, j0, p0 = orc.force(m, r, v, wl.eps, idx=samp, nthreads=NTHREADS)
+    a = np.zeros((wl.n, 3))
+    j = np.zeros((wl.n, 3))
+    a[samp], j[samp] = a0, j0
+    with _ctx_with_state(gpu, "hybrid", m, r, v, wl.eps, a, j) as ctx:
+        acc, jerk, pot = ctx.force(samp)
+    err = max(_rel(acc, a0).max(), _rel(jerk, j0).max(),
+              (np.abs(pot - p0) / np.abs(p0)).max())
+    assert err < 1e-6, err

@@ -253,7 +253,7 @@ def test_block_step_equals_manual_sequence(gpu):
         assert np.array_equal(s1[k], s2[k]), k
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed", "ds"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "ds", "hybrid"])
 def test_autotune_picks_valid_shapes_and_keeps_results(gpu, orc, prec):
     n = 3000
     m, r, v = ics.plummer(n, 31)
