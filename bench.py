@@ -275,10 +275,19 @@ def run_ours(args):
         base["m"] = m
         states = block_states({k: base[k] for k in ("m", "r", "v", "a", "j")}, perm)
         dstates = [to_device(s, torch, dev) for s in states]
+        # one device snapshot per block: the step rolls the state back with
+        # nb_restore (a single copy kernel) before each block step
+        snaps = []
+        for s in dstates:
+            ctx.set_state(s["m"], s["r"], s["v"], s["a"], s["j"], s["t"], s["dt"], eps, eta)
+            buf = torch.empty(ctx.snapshot_bytes() // 8, dtype=torch.float64, device=dev)
+            ctx.snapshot(buf)
+            snaps.append(buf)
+        ctx.snaps = snaps
 
         def enqueue_step():
-            for s in dstates:
-                ctx.set_state(s["m"], s["r"], s["v"], s["a"], s["j"], s["t"], s["dt"], eps, eta)
+            for buf in snaps:
+                ctx.restore(buf)
                 ctx.block_step(1.0)
 
         # Every call above is stream-ordered and device-resident, so the whole
@@ -329,13 +338,13 @@ def run_ours(args):
         return e0.elapsed_time(e1) / 1e3 / reps
 
     def breakdown(ctx, dstates, reps=50):
-        """Per block size, warm CUDA-event times (us) of: the state restore
-        alone (bench scaffolding), restore + one block step, and the force
-        launch alone on that block's active list."""
+        """Per block size, warm CUDA-event times (us) of: the state roll-back
+        alone (nb_restore, bench scaffolding), roll-back + one block step, and
+        the force launch alone on that block's active list."""
         out = {}
-        for k, s in zip(NACTS, dstates):
+        for k, buf in zip(NACTS, ctx.snaps):
             def restore():
-                ctx.set_state(s["m"], s["r"], s["v"], s["a"], s["j"], s["t"], s["dt"], eps, eta)
+                ctx.restore(buf)
 
             def step():
                 restore()
@@ -519,8 +528,9 @@ def run_ours(args):
             "dtype": DTYPES[head], "data": "synthetic",
             "config": {"workload": WL.name, "n": n, "n_act": list(NACTS), "eps": eps,
                        "seed": WL.seed, "precision": head, "parallelism": f"replicas{world}",
-                       "step": "select+predict+force+correct per n_act, state restored on "
-                               "device, whole step replayed as one CUDA graph",
+                       "step": "select+predict+force+correct per n_act, state rolled back "
+                               "on the device (nb_restore) before each, whole step replayed "
+                               "as one CUDA graph",
                        "l2": "flushed (512 MiB write) between timed steps",
                        "interactions_per_step": inter_per_step,
                        "gflops_60flop": hm["value"] * FLOPS_PER_INTERACTION / 1e9,
@@ -538,11 +548,10 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
 
 
-# Kernels of one graph-replayed block step of the sweep: the state restore
-# (4 layout conversions and the split bounds), tmin + count + scatter
-# (select), predict, the two force launch variants (each returns at once
-# outside its n_act window), correct.
-LAUNCHES_PER_BLOCK_STEP = 12
+# Kernels of one graph-replayed block step of the sweep: the state roll-back
+# (nb_restore), tmin + count + scatter (select), predict, the two force launch
+# variants (each returns at once outside its n_act window), correct.
+LAUNCHES_PER_BLOCK_STEP = 8
 DTYPES = {"ds": "f32x2 (double-single on the FP32 pipes)", "mixed": "f32", "fp64": "f64",
           "hybrid": "f32 (far pairs) + f32x2 double-single (near pairs)"}
 

@@ -151,6 +151,20 @@ nb_status nb_set_state(nb_ctx* ctx, int64_t n, const double* m, const double* r,
 nb_status nb_get_state(nb_ctx* ctx, double* r, double* v, double* a, double* j,
                        double* t, double* dt, int32_t on_device);
 
+/* Device snapshot of the whole Hermite state (no counterpart in the paper):
+ * a rollback point that never leaves the GPU.  nb_snapshot_bytes() is the
+ * size of one snapshot of the loaded system (0 if none is loaded).
+ * nb_snapshot copies m, x, v, a, j, t, dt and the layout bounds into the
+ * caller's device buffer `buf` (at least nb_snapshot_bytes, 16-byte
+ * aligned); nb_restore copies such a snapshot back.  Both are one kernel on
+ * the context stream, asynchronous and capturable in a CUDA graph.  A
+ * snapshot belongs to the system it was taken from (same n and, for an
+ * ensemble, the same systems); restoring into another is undefined.
+ * Errors: NB_ESTATE (nothing loaded), NB_EINVAL (NULL or misaligned buf). */
+int64_t nb_snapshot_bytes(const nb_ctx* ctx);
+nb_status nb_snapshot(nb_ctx* ctx, void* buf);
+nb_status nb_restore(nb_ctx* ctx, const void* buf);
+
 /* Steps 2-3 (Eqs. xpred, vpred): predict every particle to time t into the
  * layout the force kernel streams.  Asynchronous. */
 nb_status nb_predict(nb_ctx* ctx, double t);

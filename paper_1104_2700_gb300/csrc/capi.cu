@@ -124,7 +124,7 @@ void dfree(T*& p)
 void free_buffers(nb_ctx* c)
 {
     dfree(c->st.m), dfree(c->st.x), dfree(c->st.v), dfree(c->st.a), dfree(c->st.j);
-    dfree(c->st.t), dfree(c->st.dt);
+    dfree(c->st.t), dfree(c->st.dt), dfree(c->st.hq);
     for (int k = 0; k < 4; ++k) {
         if (c->jl.arr[k]) cudaFree(c->jl.arr[k]);
         if (c->jl64.arr[k]) cudaFree(c->jl64.arr[k]);
@@ -207,6 +207,7 @@ nb_status ensure_capacity(nb_ctx* c, int64_t n, int64_t n_pad, int64_t k)
     NB_CK(c, cudaMalloc(&c->st.j, 3 * n * d));
     NB_CK(c, cudaMalloc(&c->st.t, n * d));
     NB_CK(c, cudaMalloc(&c->st.dt, n * d));
+    NB_CK(c, cudaMalloc(&c->st.hq, n * d));
     // i-groups never mix systems: at most n / 32 + k of them
     const int64_t groups_bound = n + 32 * k;
     nb_status s = alloc_layout(c, c->prec, c->jl, n_pad);
@@ -345,6 +346,9 @@ nb::ForceArgs force_args(nb_ctx* c, Prec p, const nb::JLayout& jl, const int32_t
     f.st_a = c->st.a;
     f.st_j = c->st.j;
     f.bound_v = c->st.bound + 1;
+    f.st_dt = c->st.dt;
+    f.st_hq = c->st.hq;
+    f.eta = c->eta;
     f.counters = c->counters;
     f.counter_stride = c->counter_stride;
     f.status = c->status_dev;
@@ -463,9 +467,12 @@ nb_status build_step_graph(nb_ctx* c, double t_end)
 }
 
 // Bounds of the grid-aligned j-layout split, from the loaded positions and
-// velocities (the corrector raises them from then on).
+// velocities (the corrector raises them from then on), and a cleared
+// far-field noise estimate.
 nb_status refresh_bounds(nb_ctx* c)
 {
+    // a fresh load has no far-field noise estimate yet
+    NB_CK(c, cudaMemsetAsync(c->st.hq, 0, c->n * sizeof(double), c->stream));
     NB_CK(c, cudaMemsetAsync(c->st.bound, 0, 2 * sizeof(uint32_t), c->stream));
     NB_CK(c, nb::bounds_launch(c->st.x, c->st.v, 3 * c->n, c->st.bound, c->stream));
     return NB_OK;
@@ -633,6 +640,31 @@ nb_status nb_set_state(nb_ctx* c, int64_t n, const double* m, const double* r, c
     if ((s = refresh_bounds(c)) != NB_OK) return s;
     if (!on_device) NB_CK(c, cudaStreamSynchronize(c->stream));
     c->loaded = true;
+    return NB_OK;
+}
+
+int64_t nb_snapshot_bytes(const nb_ctx* c)
+{
+    if (!c || !c->loaded) return 0;
+    return (16 * c->n + 1) * static_cast<int64_t>(sizeof(double));
+}
+
+nb_status nb_snapshot(nb_ctx* c, void* buf)
+{
+    nb_status s = enter(c, true);
+    if (s != NB_OK) return s;
+    if (!buf || (reinterpret_cast<uintptr_t>(buf) & 15u)) return fail(c, NB_EINVAL, "buf NULL or not 16-byte aligned");
+    NB_CK(c, nb::snapshot_launch(c->st, static_cast<double*>(buf), true, c->stream));
+    return NB_OK;
+}
+
+nb_status nb_restore(nb_ctx* c, const void* buf)
+{
+    nb_status s = enter(c, true);
+    if (s != NB_OK) return s;
+    if (!buf || (reinterpret_cast<uintptr_t>(buf) & 15u)) return fail(c, NB_EINVAL, "buf NULL or not 16-byte aligned");
+    NB_CK(c, nb::snapshot_launch(c->st, static_cast<double*>(const_cast<void*>(buf)), false,
+                                 c->stream));
     return NB_OK;
 }
 

@@ -56,6 +56,11 @@ struct ForceParams {
     const double* st_a;
     const double* st_j;
     const uint32_t* bound_v;
+    // and its integration guard: the state's dt, eta, and the far-field
+    // noise estimate of each particle's last evaluation (written here)
+    const double* st_dt;
+    double* st_hq;
+    double eta;
 };
 
 // ---------------------------------------------------------------------------
@@ -129,7 +134,8 @@ struct PolicyFP64 {
         }
     }
 
-    __device__ static void values(const Acc& a, double (&v)[7])
+    static constexpr int NV = 7;  // reduced values: acc (3), jerk (3), pot
+    __device__ static void values(const Acc& a, double (&v)[NV])
     {
         v[0] = a.ax, v[1] = a.ay, v[2] = a.az;
         v[3] = a.jx, v[4] = a.jy, v[5] = a.jz;
@@ -225,7 +231,8 @@ struct PolicyMixed {
         }
     }
 
-    __device__ static void values(const Acc& a, double (&v)[7])
+    static constexpr int NV = 7;  // reduced values: acc (3), jerk (3), pot
+    __device__ static void values(const Acc& a, double (&v)[NV])
     {
         v[0] = a.ax.value(), v[1] = a.ay.value(), v[2] = a.az.value();
         v[3] = a.jx.value(), v[4] = a.jy.value(), v[5] = a.jz.value();
@@ -407,7 +414,8 @@ struct PolicyDS {
         }
     }
 
-    __device__ static void values(const Acc& a, double (&v)[7]) { a.values(v); }
+    static constexpr int NV = 7;
+    __device__ static void values(const Acc& a, double (&v)[NV]) { a.values(v); }
 };
 
 // Hybrid precision (no counterpart in the paper, which evaluates every pair
@@ -429,9 +437,29 @@ struct PolicyDS {
 // the DS pair about max-over-lanes(near pairs in the tile) times per tile.
 constexpr float HY_THETA = 0.1f;
 constexpr int HY_RUN = 8;
+// Integration guard.  The Hermite interpolation divides a0 - a1 by dt^3
+// (crackle), so an absolute force noise da sets a floor 12 da / dt^3 under
+// the crackle that Eq. timestep sees; once that floor rivals the true value
+// the timestep shrinks and keeps shrinking.  Each evaluation estimates its
+// far-field noise as 2 u sqrt(sum of squared far-pair |a| bounds) (FP32
+// rounding of independent terms); when the last estimate exceeds
+// HY_GUARD * eta |j| dt / 12 (the crackle scale of the particle's current
+// step), the particle is evaluated entirely in double-single.
+constexpr double HY_GUARD = 0.01;
+constexpr double HY_U = 5.9604644775390625e-8;  // 2^-24
 
 struct HybridI : DSI {
-    float ca, cj;  // near test: r^2 < max(Gm_j * ca, (Gm_j)^(2/3) * cj)
+    float ca, cj;   // natural near test: r^2 < max(Gm_j * ca, (Gm_j)^(2/3) * cj)
+    bool all_near;  // integration guard: every pair in double-single
+    int particle;
+};
+struct HybridAcc : DSAccs {
+    float q;  // far-field noise estimate: sum of squared far-pair |a| bounds
+    __device__ void zero()
+    {
+        DSAccs::zero();
+        q = 0.f;
+    }
 };
 
 template <int IT>
@@ -440,14 +468,17 @@ struct PolicyHybrid {
     __host__ __device__ static constexpr int elem(int a) { return a < 4 ? 16 : 0; }
     static constexpr int TILE_BYTES = TJ * 64;
     static constexpr int STAGES = 3;
+    static constexpr int NV = 8;  // acc, jerk, pot and the noise estimate
 
     using I = HybridI;
-    using Acc = DSAccs;
+    using Acc = HybridAcc;
 
     __device__ static void load_i(const ForceParams& f, int p, int particle, I& s)
     {
         ds_load_i(f, p, s);
         s.ca = s.cj = 0.f;
+        s.all_near = false;
+        s.particle = particle;
         if (p < 0) return;
         const int64_t n = f.n;
         double a2 = 0.0, j2 = 0.0;
@@ -465,6 +496,22 @@ struct PolicyHybrid {
         const float x = 4.f * V / (HY_THETA * J);
         const float cb = cbrtf(x);
         s.cj = cb * cb;
+        const double noise = 2.0 * HY_U * sqrt(f.st_hq[particle]);
+        s.all_near = 12.0 * noise > HY_GUARD * f.eta * sqrt(j2) * f.st_dt[particle];
+    }
+
+    __device__ static void values(const Acc& a, double (&v)[NV])
+    {
+        double w[7];
+        a.values(w);
+#pragma unroll
+        for (int c = 0; c < 7; ++c) v[c] = w[c];
+        v[7] = static_cast<double>(a.q);
+    }
+
+    __device__ static void finish(const ForceParams& f, const I& s, const double (&v)[NV])
+    {
+        if (s.particle >= 0) f.st_hq[s.particle] = v[7];
     }
 
     template <bool MASK>
@@ -485,11 +532,11 @@ struct PolicyHybrid {
         for (int q = 0; q < IT; ++q) nlo[q] = nhi[q] = 0u;
 #pragma unroll 1
         for (int k0 = 0; k0 < TJ; k0 += HY_RUN) {
-            float ax[IT], ay[IT], az[IT], jx[IT], jy[IT], jz[IT], ph[IT];
+            float ax[IT], ay[IT], az[IT], jx[IT], jy[IT], jz[IT], ph[IT], qs[IT];
             uint32_t run[IT];
 #pragma unroll
             for (int q = 0; q < IT; ++q) {
-                ax[q] = ay[q] = az[q] = jx[q] = jy[q] = jz[q] = ph[q] = 0.f;
+                ax[q] = ay[q] = az[q] = jx[q] = jy[q] = jz[q] = ph[q] = qs[q] = 0.f;
                 run[q] = 0u;
             }
 #pragma unroll 4
@@ -510,15 +557,18 @@ struct PolicyHybrid {
                     const float dvy = (C.y - s.vyh) + (D.y - s.vyl);
                     const float dvz = (C.z - s.vzh) + (D.z - s.vzl);
                     const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, e2h)));
-                    bool near = r2 < fmaxf(A.w * is[q].ca, C.w * is[q].cj);
                     const bool self = MASK && (j0 + k == s.p);
-                    near = near && !self;
+                    const bool nat = r2 < fmaxf(A.w * is[q].ca, C.w * is[q].cj);
+                    const bool near = (nat || is[q].all_near) && !self;
                     // rsqrt refined once: y (1 + h/2), h = 1 - r^2 y^2
                     float y = rsqrtf(r2);
                     const float yy = y * y;
                     float h = fmaf(-r2, yy, 1.f);
                     h = fmaf(-r2, fmaf(y, y, -yy), h);
                     y = fmaf(0.5f * y, h, y);
+                    // noise estimate over the pairs the natural test calls far
+                    const float am = (nat || self) ? 0.f : A.w * y * y;
+                    qs[q] = fmaf(am, am, qs[q]);
                     if (self || near) y = 0.f;
                     const float mr = A.w * y;
                     const float ri2 = y * y;
@@ -540,6 +590,7 @@ struct PolicyHybrid {
                 ac[q].ax.fold(ax[q]), ac[q].ay.fold(ay[q]), ac[q].az.fold(az[q]);
                 ac[q].jx.fold(jx[q]), ac[q].jy.fold(jy[q]), ac[q].jz.fold(jz[q]);
                 ac[q].ph.fold(ph[q]);
+                ac[q].q += qs[q];
                 if (k0 < 32) nlo[q] |= run[q] << k0;
                 else nhi[q] |= run[q] << (k0 - 32);
             }
@@ -565,7 +616,6 @@ struct PolicyHybrid {
         }
     }
 
-    __device__ static void values(const Acc& a, double (&v)[7]) { a.values(v); }
 };
 
 template <class K>
@@ -593,6 +643,7 @@ __device__ __forceinline__ void issue_tile(const ForceParams& f, unsigned char* 
 // Radix of the deterministic reduction tree over the warps sharing a group.
 constexpr int RB = 16;
 constexpr int RLEVELS = 4;  // RB^RLEVELS >= any warp count
+constexpr int MAX_NV = 8;   // values a policy reduces (scratch is sized for the most)
 
 // Warp that owns flattened tile x when T tiles are cut into Pu ranges.
 __device__ __forceinline__ int64_t owner_warp(int64_t x, int64_t T, int64_t Pu)
@@ -797,7 +848,8 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
             // the chunk it replaces); each level has its own counters.
             const int64_t wf = owner_warp(gi.tile0, T, Pu);
             const int64_t wl = owner_warp(gi.tile0 + gi.ntiles - 1, T, Pu);
-            double v[IT][7];
+            constexpr int NV = K::NV;
+            double v[IT][NV];
 #pragma unroll
             for (int q = 0; q < IT; ++q) K::values(ac[q], v[q]);
             const int64_t key = wf + g;
@@ -806,11 +858,11 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
             int64_t stride = 1;
             bool final_here = true;
             for (int level = 0; kk > 1; ++level) {
-                double* mine = f.scratch + (size_t)(key + r * stride) * 7 * GI;
+                double* mine = f.scratch + (size_t)(key + r * stride) * NV * GI;
 #pragma unroll
                 for (int q = 0; q < IT; ++q)
 #pragma unroll
-                    for (int c = 0; c < 7; ++c) mine[c * GI + q * 32 + lane] = v[q][c];
+                    for (int c = 0; c < NV; ++c) mine[c * GI + q * 32 + lane] = v[q][c];
                 __threadfence();
                 __syncwarp();
                 const int64_t chunk = r / RB;
@@ -829,11 +881,11 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
 #pragma unroll
                 for (int q = 0; q < IT; ++q)
 #pragma unroll
-                    for (int c = 0; c < 7; ++c) {
+                    for (int c = 0; c < NV; ++c) {
                         double sum = 0.0;
 #pragma unroll 4
                         for (int64_t u = 0; u < cs; ++u)
-                            sum += __ldcg(f.scratch + (size_t)(key + (first + u) * stride) * 7 * GI +
+                            sum += __ldcg(f.scratch + (size_t)(key + (first + u) * stride) * NV * GI +
                                           c * GI + q * 32 + lane);
                         v[q][c] = sum;
                     }
@@ -853,6 +905,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
                         f.jerk[3 * a + 1] = v[q][4];
                         f.jerk[3 * a + 2] = v[q][5];
                         f.pot[a] = v[q][6];
+                        if constexpr (K::NV > 7) K::finish(f, is[q], v[q]);
                     }
                 }
             }
@@ -956,7 +1009,7 @@ size_t force_scratch_doubles(int it, int64_t n_act_max, int warps)
 {
     const int64_t GI = 32 * it;
     const int64_t G = (n_act_max + GI - 1) / GI;
-    return (size_t)(warps + G) * 7 * GI;
+    return (size_t)(warps + G) * MAX_NV * GI;
 }
 
 int64_t force_counter_stride(int64_t n_act_max, int warps)
@@ -1005,7 +1058,10 @@ cudaError_t force_launch(const ForceArgs& a, cudaStream_t s)
     f.st_a = a.st_a;
     f.st_j = a.st_j;
     f.bound_v = a.bound_v;
-    if (a.prec == Prec::HYBRID && (!f.st_a || !f.st_j || !f.bound_v))
+    f.st_dt = a.st_dt;
+    f.st_hq = a.st_hq;
+    f.eta = a.eta;
+    if (a.prec == Prec::HYBRID && (!f.st_a || !f.st_j || !f.bound_v || !f.st_dt || !f.st_hq))
         return cudaErrorInvalidValue;
     void* args[] = {&f};
     return cudaLaunchKernel(fn, dim3(a.grid), dim3(FORCE_WARPS * 32), args,

@@ -798,6 +798,39 @@ cudaError_t soa_to_aos_launch(const double* soa, double* aos, int64_t n, cudaStr
     return cudaGetLastError();
 }
 
+// Whole-state snapshot: buf = [m | x | v | a | j | t | dt | hq | bounds],
+// with the 16 n doubles of the state and one 8-byte slot for the two bounds.
+__global__ void snapshot_kernel(StateDev st, double* __restrict__ buf, int to_buf)
+{
+    const int64_t n = st.n;
+    double* arr[8] = {st.m, st.x, st.v, st.a, st.j, st.t, st.dt, st.hq};
+    const int64_t len[8] = {n, 3 * n, 3 * n, 3 * n, 3 * n, n, n, n};
+    const int64_t total = 16 * n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t off = e;
+        int k = 0;
+        while (off >= len[k]) off -= len[k++];
+        if (to_buf) buf[e] = arr[k][off];
+        else arr[k][off] = buf[e];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        uint32_t* b = reinterpret_cast<uint32_t*>(buf + total);
+        if (to_buf) b[0] = st.bound[0], b[1] = st.bound[1];
+        else st.bound[0] = b[0], st.bound[1] = b[1];
+    }
+}
+
+cudaError_t snapshot_launch(const StateDev& st, double* buf, bool to_buf, cudaStream_t s)
+{
+    if (st.n <= 0) return cudaSuccess;
+    const int threads = 256;
+    const int64_t want = (16 * st.n + threads - 1) / threads;
+    const unsigned blocks = static_cast<unsigned>(want < 2048 ? want : 2048);
+    snapshot_kernel<<<blocks, threads, 0, s>>>(st, buf, to_buf ? 1 : 0);
+    return cudaGetLastError();
+}
+
 cudaError_t iota_launch(int32_t* idx, int64_t n, int32_t* n_act_dev, cudaStream_t s)
 {
     const int64_t m = n > 0 ? n : 1;

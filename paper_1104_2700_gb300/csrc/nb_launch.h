@@ -33,6 +33,9 @@ struct StateDev {
     // load, raised by the corrector.  They fix the grid of the j layout's
     // double-single split (grid_split).
     uint32_t* bound = nullptr;
+    // Hybrid precision: per particle, the far-field noise estimate of its
+    // last force evaluation (sum of squared far-pair |a| bounds); 0 = none.
+    double* hq = nullptr;
 };
 
 // bound[0] = max |a_k|, bound[1] = max |b_k| over k < count (float bits,
@@ -128,6 +131,9 @@ struct ForceArgs {
     const double* st_a = nullptr;
     const double* st_j = nullptr;
     const uint32_t* bound_v = nullptr;
+    const double* st_dt = nullptr;  // integration guard (see PolicyHybrid)
+    double* st_hq = nullptr;
+    double eta = 0.0;
 };
 
 cudaError_t force_setup(Prec p, int it);  // one-time attribute setup
@@ -202,5 +208,8 @@ cudaError_t energy_launch(const StateDev& st, const double* pot_all, double* par
 cudaError_t aos_to_soa_launch(const double* aos, double* soa, int64_t n, cudaStream_t s);
 cudaError_t soa_to_aos_launch(const double* soa, double* aos, int64_t n, cudaStream_t s);
 cudaError_t iota_launch(int32_t* idx, int64_t n, int32_t* n_act_dev, cudaStream_t s);
+// Copy the whole state (16 n doubles: m, x, v, a, j, t, dt, hq, then the
+// two bounds) to (to_buf) or from a device buffer of 16 n + 1 doubles.
+cudaError_t snapshot_launch(const StateDev& st, double* buf, bool to_buf, cudaStream_t s);
 
 }  // namespace nb

@@ -96,6 +96,9 @@ def load(path: str = LIB_PATH):
         "nb_autotune": (c_int32, [P, POINTER(NbTuning)]),
         "nb_selftest_timeout": (c_int32, [P]),
         "nb_measure_peaks": (c_int32, [c_int32, POINTER(c_double), POINTER(c_double)]),
+        "nb_snapshot_bytes": (c_int64, [P]),
+        "nb_snapshot": (c_int32, [P, P]),
+        "nb_restore": (c_int32, [P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -215,6 +218,18 @@ def nb_selftest_timeout(ctx):
 def nb_force_static(n, m, r, v, eps, G, n_act, idx, acc, jerk, pot, stream):
     """Allocation-free force evaluation on device pointers (see nbody.h)."""
     return load().nb_force_static(n, m, r, v, eps, G, n_act, idx, acc, jerk, pot, stream)
+
+
+def nb_snapshot_bytes(ctx) -> int:
+    return load().nb_snapshot_bytes(ctx)
+
+
+def nb_snapshot(ctx, buf):
+    return load().nb_snapshot(ctx, buf)
+
+
+def nb_restore(ctx, buf):
+    return load().nb_restore(ctx, buf)
 
 
 def nb_measure_peaks(device, fp32_ref, fp64_ref):
@@ -393,6 +408,18 @@ class Context:
         pa, ka, _ = _ptr(acc, np.float64, (k, 3)) if acc is not None else (None, None, None)
         pj, kj, _ = _ptr(jerk, np.float64, (k, 3)) if jerk is not None else (None, None, None)
         self._ck(nb_correct(self.handle, float(t), k, idx.ctypes.data_as(c_void_p), pa, pj, 0))
+
+    def snapshot_bytes(self):
+        return nb_snapshot_bytes(self.handle)
+
+    def snapshot(self, buf):
+        """Copy the device state into `buf` (a device tensor of at least
+        snapshot_bytes() bytes)."""
+        self._ck(nb_snapshot(self.handle, c_void_p(buf.data_ptr())))
+
+    def restore(self, buf):
+        """Copy a snapshot taken by snapshot() back into the device state."""
+        self._ck(nb_restore(self.handle, c_void_p(buf.data_ptr())))
 
     def block_step(self, t_end):
         self._ck(nb_block_step(self.handle, float(t_end)))

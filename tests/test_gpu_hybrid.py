@@ -102,3 +102,24 @@ def test_integration_hybrid_plummer_n1024(gpu, orc):
     dE_gpu = abs(K1 + W1 - E0) / abs(E0)
     assert dE_gpu <= 2 * dE_orc + 2e-9
     assert steps == pytest.approx(s.n_steps, rel=0.05)
+
+
+def test_hybrid_integration_guard_prevents_step_collapse(gpu):
+    """Member 8 of the ensemble workload (Plummer N = 7461, eps = 4/N) holds a
+    particle with |a| = 0.045 and |j| = 39.  Its FP32 far field leaves
+    ~1.5e-8 absolute noise in a (3e-7 relative, inside the force bound), but
+    crackle divides a0 - a1 by dt^3, and without the integration guard its
+    timestep collapsed from 2^-17 to 2^-23 (43556 block steps to t = 1/64
+    against DS's 1292).  With the guard the schedules agree."""
+    sizes, off, ms, rs, vs, eps = ics.ensemble(256, 4, 1000)
+    q = 8
+    lo, hi = off[q], off[q + 1]
+    steps = {}
+    for prec in ("ds", "hybrid"):
+        with gpu.Context(prec) as ctx:
+            ctx.set_particles(ms[lo:hi], rs[lo:hi], vs[lo:hi], float(eps[q]), 0.02)
+            steps[prec], _ = ctx.step_until(1.0 / 64)
+            dt = ctx.get_state()["dt"]
+        if prec == "hybrid":
+            assert dt.min() >= 2.0 ** -17
+    assert steps["hybrid"] == pytest.approx(steps["ds"], rel=0.05)

@@ -56,3 +56,26 @@ def test_checkpoint_resume_is_bitwise(gpu, prec):
     for k in final_a:
         assert np.array_equal(final_a[k], final_b[k]), k
     assert np.all(final_a["t"] == t2)
+
+
+@pytest.mark.parametrize("prec", ["ds", "hybrid"])
+def test_snapshot_restore_replays_bitwise(gpu, prec):
+    """nb_snapshot / nb_restore: rolling back on the device and integrating
+    again reproduces the first run bit for bit."""
+    import torch
+    n = 1024
+    m, r, v = ics.plummer(n, 4)
+    with gpu.Context(prec) as ctx:
+        ctx.set_particles(m, r, v, 1.0 / 64, 0.02)
+        nbytes = ctx.snapshot_bytes()
+        assert nbytes == (16 * n + 1) * 8
+        buf = torch.empty(nbytes // 8, dtype=torch.float64, device="cuda")
+        ctx.snapshot(buf)
+        first = ctx.step_until(1.0 / 16)
+        s1 = ctx.get_state()
+        ctx.restore(buf)
+        again = ctx.step_until(1.0 / 16)
+        s2 = ctx.get_state()
+    assert first == again
+    for k in s1:
+        assert np.array_equal(s1[k], s2[k]), k
