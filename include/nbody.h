@@ -57,7 +57,12 @@ typedef enum nb_status {
  *             evaluated in double-single.  A particle whose state has
  *             a = j = 0 (the evaluation inside nb_set_particles) treats every
  *             pair as near.  Errors stay well inside 1e-6 per particle on the
- *             measured workloads at several times the DS throughput. */
+ *             measured workloads at ~2.5x the DS throughput.  Integration
+ *             guard: each evaluation also stores a per-particle estimate of
+ *             its FP32 far-field noise; a particle whose noise would reach
+ *             3 % of the crackle scale of its step (eta |j| dt / 12) is
+ *             evaluated entirely in DS next time, so the Aarseth timesteps
+ *             keep the DS schedule.  The default. */
 typedef enum nb_precision { NB_FP64 = 0, NB_MIXED = 1, NB_DS = 2, NB_HYBRID = 3 } nb_precision;
 
 typedef struct nb_config {
@@ -78,7 +83,7 @@ typedef struct nb_config {
                               * failure path without faulting the GPU. */
 } nb_config;
 
-/* Fill *cfg with the defaults: NB_DS, device 0, G = 1, eta_start = 0.01,
+/* Fill *cfg with the defaults: NB_HYBRID, device 0, G = 1, eta_start = 0.01,
  * dt_max = 1/16, dt_min = 2^-40, private stream, default launch shapes, no
  * autotuning. */
 void nb_config_init(nb_config* cfg);

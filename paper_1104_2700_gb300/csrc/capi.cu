@@ -478,6 +478,21 @@ nb_status refresh_bounds(nb_ctx* c)
     return NB_OK;
 }
 
+// Hybrid precision only, at a load with a fresh force evaluation: that
+// evaluation ran every pair in double-single (the state had a = j = 0), so
+// it left no far-field noise estimate, and the first block step would run
+// unguarded (a DS a0 against an FP32-noisy a1).  One more evaluation with
+// the new a, j and dt stores the estimate; its forces are discarded.
+nb_status hybrid_noise_pass(nb_ctx* c, bool ensemble)
+{
+    if (c->prec != Prec::HYBRID) return NB_OK;
+    NB_CK(c, nb::iota_launch(c->idx_user, c->n, c->n_act_user, c->stream));
+    if (ensemble)
+        return run_force_list(c, c->prec, c->jl, c->idx_user, c->n_act_user,
+                              static_cast<int32_t>(c->n));
+    return run_force(c, c->prec, c->jl, c->idx_user, c->n_act_user, static_cast<int32_t>(c->n));
+}
+
 // Set-up shared by nb_set_particles / nb_set_state.
 nb_status begin_load(nb_ctx* c, int64_t n, double eps, double eta)
 {
@@ -509,7 +524,7 @@ void nb_config_init(nb_config* cfg)
 {
     if (!cfg) return;
     std::memset(cfg, 0, sizeof(*cfg));
-    cfg->precision = NB_DS;
+    cfg->precision = NB_HYBRID;
     cfg->device = 0;
     cfg->G = 1.0;
     cfg->eta_start = 0.01;
@@ -615,6 +630,7 @@ nb_status nb_set_particles(nb_ctx* c, int64_t n, const double* m, const double* 
         return s;
     NB_CK(c, nb::init_dt_launch(c->st, c->acc1, c->jerk1, c->cfg.eta_start, c->cfg.dt_max,
                                 c->cfg.dt_min, 0.0, c->status_dev, c->stream));
+    if ((s = hybrid_noise_pass(c, false)) != NB_OK) return s;
     if ((s = check_status(c)) != NB_OK) return s;
     c->loaded = true;
     if (c->cfg.autotune) return nb_autotune(c, nullptr);
@@ -955,6 +971,7 @@ nb_status nb_set_ensemble(nb_ctx* c, int32_t k, const int64_t* offsets, const do
         return s;
     NB_CK(c, nb::init_dt_launch(c->st, c->acc1, c->jerk1, c->cfg.eta_start, c->cfg.dt_max,
                                 c->cfg.dt_min, 0.0, c->status_dev, c->stream));
+    if ((s = hybrid_noise_pass(c, true)) != NB_OK) return s;
     if ((s = check_status(c)) != NB_OK) return s;
     c->last_force_n_act = -1;
     c->loaded = true;

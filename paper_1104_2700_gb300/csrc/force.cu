@@ -441,11 +441,16 @@ constexpr int HY_RUN = 8;
 // (crackle), so an absolute force noise da sets a floor 12 da / dt^3 under
 // the crackle that Eq. timestep sees; once that floor rivals the true value
 // the timestep shrinks and keeps shrinking.  Each evaluation estimates its
-// far-field noise as 2 u sqrt(sum of squared far-pair |a| bounds) (FP32
-// rounding of independent terms); when the last estimate exceeds
+// far-field noise from the FP32 roundings it made: every far pair's term
+// (|a| bound b = G m / r^2) and every 8-term run sum (bounded by the sum of
+// its b), as 2 u sqrt(sum b^2 + sum run^2).  When the last estimate exceeds
 // HY_GUARD * eta |j| dt / 12 (the crackle scale of the particle's current
-// step), the particle is evaluated entirely in double-single.
-constexpr double HY_GUARD = 0.01;
+// step), the particle is evaluated entirely in double-single.  Switching
+// between the two precisions itself steps a0 - a1 by the full noise, so the
+// guard has hysteresis: once on, it stays on until the ratio falls below
+// HY_GUARD_OFF (the stored estimate carries the guard state in its sign).
+constexpr double HY_GUARD = 0.03;
+constexpr double HY_GUARD_OFF = 0.1;  // of the turn-on level
 constexpr double HY_U = 5.9604644775390625e-8;  // 2^-24
 
 struct HybridI : DSI {
@@ -454,7 +459,7 @@ struct HybridI : DSI {
     int particle;
 };
 struct HybridAcc : DSAccs {
-    float q;  // far-field noise estimate: sum of squared far-pair |a| bounds
+    float q;  // far-field noise estimate: squared pair bounds and run sums
     __device__ void zero()
     {
         DSAccs::zero();
@@ -496,8 +501,10 @@ struct PolicyHybrid {
         const float x = 4.f * V / (HY_THETA * J);
         const float cb = cbrtf(x);
         s.cj = cb * cb;
-        const double noise = 2.0 * HY_U * sqrt(f.st_hq[particle]);
-        s.all_near = 12.0 * noise > HY_GUARD * f.eta * sqrt(j2) * f.st_dt[particle];
+        const double hq = f.st_hq[particle];
+        const double noise = 2.0 * HY_U * sqrt(fabs(hq));
+        const double ratio = 12.0 * noise / (HY_GUARD * f.eta * sqrt(j2) * f.st_dt[particle]);
+        s.all_near = hq < 0.0 ? ratio > HY_GUARD_OFF : ratio > 1.0;
     }
 
     __device__ static void values(const Acc& a, double (&v)[NV])
@@ -511,7 +518,8 @@ struct PolicyHybrid {
 
     __device__ static void finish(const ForceParams& f, const I& s, const double (&v)[NV])
     {
-        if (s.particle >= 0) f.st_hq[s.particle] = v[7];
+        // a guarded evaluation stores its estimate negated (the guard state)
+        if (s.particle >= 0) f.st_hq[s.particle] = s.all_near ? -v[7] : v[7];
     }
 
     template <bool MASK>
@@ -532,11 +540,11 @@ struct PolicyHybrid {
         for (int q = 0; q < IT; ++q) nlo[q] = nhi[q] = 0u;
 #pragma unroll 1
         for (int k0 = 0; k0 < TJ; k0 += HY_RUN) {
-            float ax[IT], ay[IT], az[IT], jx[IT], jy[IT], jz[IT], ph[IT], qs[IT];
+            float ax[IT], ay[IT], az[IT], jx[IT], jy[IT], jz[IT], ph[IT], qs[IT], bs[IT];
             uint32_t run[IT];
 #pragma unroll
             for (int q = 0; q < IT; ++q) {
-                ax[q] = ay[q] = az[q] = jx[q] = jy[q] = jz[q] = ph[q] = qs[q] = 0.f;
+                ax[q] = ay[q] = az[q] = jx[q] = jy[q] = jz[q] = ph[q] = qs[q] = bs[q] = 0.f;
                 run[q] = 0u;
             }
 #pragma unroll 4
@@ -569,6 +577,7 @@ struct PolicyHybrid {
                     // noise estimate over the pairs the natural test calls far
                     const float am = (nat || self) ? 0.f : A.w * y * y;
                     qs[q] = fmaf(am, am, qs[q]);
+                    bs[q] += am;
                     if (self || near) y = 0.f;
                     const float mr = A.w * y;
                     const float ri2 = y * y;
@@ -590,7 +599,7 @@ struct PolicyHybrid {
                 ac[q].ax.fold(ax[q]), ac[q].ay.fold(ay[q]), ac[q].az.fold(az[q]);
                 ac[q].jx.fold(jx[q]), ac[q].jy.fold(jy[q]), ac[q].jz.fold(jz[q]);
                 ac[q].ph.fold(ph[q]);
-                ac[q].q += qs[q];
+                ac[q].q += fmaf(bs[q], bs[q], qs[q]);
                 if (k0 < 32) nlo[q] |= run[q] << k0;
                 else nhi[q] |= run[q] << (k0 - 32);
             }

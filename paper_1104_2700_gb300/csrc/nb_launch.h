@@ -34,7 +34,8 @@ struct StateDev {
     // double-single split (grid_split).
     uint32_t* bound = nullptr;
     // Hybrid precision: per particle, the far-field noise estimate of its
-    // last force evaluation (sum of squared far-pair |a| bounds); 0 = none.
+    // last force evaluation, negative when that evaluation was guarded
+    // (all double-single); 0 = none yet.
     double* hq = nullptr;
 };
 

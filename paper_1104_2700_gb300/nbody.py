@@ -269,7 +269,7 @@ def _ptr(x, dtype, shape=None):
 class Context:
     """One simulated system on one GPU (wraps an nb_ctx handle)."""
 
-    def __init__(self, precision="ds", device=0, G=1.0, eta_start=0.01,
+    def __init__(self, precision="hybrid", device=0, G=1.0, eta_start=0.01,
                  dt_max=1.0 / 16, dt_min=2.0 ** -40, stream=None, i_per_thread=0,
                  ctas_per_sm=0, autotune=False, wait_limit_cycles=0):
         cfg = nb_config_init()

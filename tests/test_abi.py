@@ -32,7 +32,7 @@ def test_library_exports_every_declared_symbol(nbody_lib):
 
 def test_config_defaults(nbody_lib):
     cfg = nbody_lib.nb_config_init()
-    assert cfg.precision == nbody_lib.NB_DS
+    assert cfg.precision == nbody_lib.NB_HYBRID
     assert cfg.G == 1.0 and cfg.eta_start == 0.01
     assert cfg.dt_max == 1.0 / 16 and cfg.dt_min == 2.0 ** -40
     assert cfg.autotune == 0
