@@ -159,7 +159,8 @@ nb_status nb_get_state(nb_ctx* ctx, double* r, double* v, double* a, double* j,
 /* Device snapshot of the whole Hermite state (no counterpart in the paper):
  * a rollback point that never leaves the GPU.  nb_snapshot_bytes() is the
  * size of one snapshot of the loaded system (0 if none is loaded).
- * nb_snapshot copies m, x, v, a, j, t, dt and the layout bounds into the
+ * nb_snapshot copies m, x, v, a, j, t, dt, the per-particle derived data
+ * (next-time keys, hybrid noise estimates) and the layout bounds into the
  * caller's device buffer `buf` (at least nb_snapshot_bytes, 16-byte
  * aligned); nb_restore copies such a snapshot back.  Both are one kernel on
  * the context stream, asynchronous and capturable in a CUDA graph.  A

@@ -124,7 +124,7 @@ void dfree(T*& p)
 void free_buffers(nb_ctx* c)
 {
     dfree(c->st.m), dfree(c->st.x), dfree(c->st.v), dfree(c->st.a), dfree(c->st.j);
-    dfree(c->st.t), dfree(c->st.dt), dfree(c->st.hq);
+    dfree(c->st.t), dfree(c->st.dt), dfree(c->st.hq), dfree(c->st.nkey);
     for (int k = 0; k < 4; ++k) {
         if (c->jl.arr[k]) cudaFree(c->jl.arr[k]);
         if (c->jl64.arr[k]) cudaFree(c->jl64.arr[k]);
@@ -208,6 +208,7 @@ nb_status ensure_capacity(nb_ctx* c, int64_t n, int64_t n_pad, int64_t k)
     NB_CK(c, cudaMalloc(&c->st.t, n * d));
     NB_CK(c, cudaMalloc(&c->st.dt, n * d));
     NB_CK(c, cudaMalloc(&c->st.hq, n * d));
+    NB_CK(c, cudaMalloc(&c->st.nkey, n * sizeof(unsigned long long)));
     // i-groups never mix systems: at most n / 32 + k of them
     const int64_t groups_bound = n + 32 * k;
     nb_status s = alloc_layout(c, c->prec, c->jl, n_pad);
@@ -467,14 +468,15 @@ nb_status build_step_graph(nb_ctx* c, double t_end)
 }
 
 // Bounds of the grid-aligned j-layout split, from the loaded positions and
-// velocities (the corrector raises them from then on), and a cleared
-// far-field noise estimate.
+// velocities (the corrector raises them from then on), a cleared far-field
+// noise estimate, and the next-time keys of the loaded t, dt.
 nb_status refresh_bounds(nb_ctx* c)
 {
     // a fresh load has no far-field noise estimate yet
     NB_CK(c, cudaMemsetAsync(c->st.hq, 0, c->n * sizeof(double), c->stream));
     NB_CK(c, cudaMemsetAsync(c->st.bound, 0, 2 * sizeof(uint32_t), c->stream));
     NB_CK(c, nb::bounds_launch(c->st.x, c->st.v, 3 * c->n, c->st.bound, c->stream));
+    NB_CK(c, nb::next_key_launch(c->st, c->stream));
     return NB_OK;
 }
 
@@ -662,7 +664,7 @@ nb_status nb_set_state(nb_ctx* c, int64_t n, const double* m, const double* r, c
 int64_t nb_snapshot_bytes(const nb_ctx* c)
 {
     if (!c || !c->loaded) return 0;
-    return (16 * c->n + 1) * static_cast<int64_t>(sizeof(double));
+    return (17 * c->n + 1) * static_cast<int64_t>(sizeof(double));
 }
 
 nb_status nb_snapshot(nb_ctx* c, void* buf)

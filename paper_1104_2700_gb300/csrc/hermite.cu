@@ -134,6 +134,24 @@ cudaError_t bounds_launch(const double* a, const double* b, int64_t count, uint3
     return cudaGetLastError();
 }
 
+__global__ void next_key_kernel(const double* __restrict__ t, const double* __restrict__ dt,
+                                int64_t n, unsigned long long* __restrict__ nkey)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        nkey[i] = dkey(t[i] + dt[i]);
+}
+
+cudaError_t next_key_launch(const StateDev& st, cudaStream_t s)
+{
+    if (st.n <= 0) return cudaSuccess;
+    const int threads = 64;  // the FP64 adds spread over every SM
+    const int64_t want = (st.n + threads - 1) / threads;
+    const unsigned blocks = static_cast<unsigned>(want < 4096 ? want : 4096);
+    next_key_kernel<<<blocks, threads, 0, s>>>(st.t, st.dt, st.n, st.nkey);
+    return cudaGetLastError();
+}
+
 cudaError_t predict_launch(const StateDev& st, Prec p, const JLayout& jl, double G,
                            const unsigned long long* t_bits, double t_host,
                            const int32_t* n_act_dev, cudaStream_t s, const ClusterDev* cl)
@@ -165,13 +183,13 @@ cudaError_t predict_launch(const StateDev& st, Prec p, const JLayout& jl, double
 // (ascending-index) compaction of the block {i : t_i + dt_i == t_next}.
 // Times are dyadic rationals, so the equality test is exact.
 // ---------------------------------------------------------------------------
-__global__ void tmin_kernel(const double* __restrict__ t, const double* __restrict__ dt,
-                            int64_t n, unsigned long long* tmin_bits)
+__global__ void tmin_kernel(const unsigned long long* __restrict__ nkey, int64_t n,
+                            unsigned long long* tmin_bits)
 {
     unsigned long long best = ~0ull;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const unsigned long long k = dkey(t[i] + dt[i]);
+        const unsigned long long k = nkey[i];
         best = k < best ? k : best;
     }
 #pragma unroll
@@ -197,12 +215,12 @@ __global__ void tmin_kernel(const double* __restrict__ t, const double* __restri
 // Particle i is in the block when its system's next time t_next (key in
 // tkeys, per cluster when cluster_of is given) is within t_end and t_i + dt_i
 // equals it.
-__device__ __forceinline__ bool is_active(const double* t, const double* dt, int64_t i,
+__device__ __forceinline__ bool is_active(const unsigned long long* nkey, int64_t i,
                                           const unsigned long long* tkeys,
                                           const int32_t* cluster_of, double t_end)
 {
-    const double tn = dkey_decode(tkeys[cluster_of ? cluster_of[i] : 0]);
-    return tn <= t_end && t[i] + dt[i] == tn;
+    const unsigned long long k = tkeys[cluster_of ? cluster_of[i] : 0];
+    return nkey[i] == k && dkey_decode(k) <= t_end;
 }
 
 // Block-wide exclusive scan of one int per thread (SCHED_THREADS threads).
@@ -235,7 +253,7 @@ __device__ int block_exclusive_scan(int v, int* total)
 }
 
 __global__ void __launch_bounds__(SCHED_THREADS)
-    count_kernel(const double* __restrict__ t, const double* __restrict__ dt, int64_t n,
+    count_kernel(const unsigned long long* __restrict__ nkey, int64_t n,
                  const unsigned long long* tkeys, const int32_t* cluster_of, double t_end,
                  SchedDev sd)
 {
@@ -244,7 +262,7 @@ __global__ void __launch_bounds__(SCHED_THREADS)
 #pragma unroll
     for (int e = 0; e < SCHED_PER_THREAD; ++e) {
         const int64_t i = base + e;
-        if (i < n && is_active(t, dt, i, tkeys, cluster_of, t_end)) ++c;
+        if (i < n && is_active(nkey, i, tkeys, cluster_of, t_end)) ++c;
     }
     int total;
     block_exclusive_scan(c, &total);
@@ -275,7 +293,7 @@ __global__ void __launch_bounds__(SCHED_THREADS)
 }
 
 __global__ void __launch_bounds__(SCHED_THREADS)
-    scatter_kernel(const double* __restrict__ t, const double* __restrict__ dt, int64_t n,
+    scatter_kernel(const unsigned long long* __restrict__ nkey, int64_t n,
                    const unsigned long long* tkeys, const int32_t* cluster_of, double t_end,
                    SchedDev sd)
 {
@@ -285,7 +303,7 @@ __global__ void __launch_bounds__(SCHED_THREADS)
 #pragma unroll
     for (int e = 0; e < SCHED_PER_THREAD; ++e) {
         const int64_t i = base + e;
-        if (i < n && is_active(t, dt, i, tkeys, cluster_of, t_end)) {
+        if (i < n && is_active(nkey, i, tkeys, cluster_of, t_end)) {
             flags |= 1u << e;
             ++c;
         }
@@ -297,8 +315,93 @@ __global__ void __launch_bounds__(SCHED_THREADS)
         if (flags & (1u << e)) sd.idx[pos++] = static_cast<int32_t>(base + e);
 }
 
+// Step 1 in one CTA, for systems small enough that a single SM beats three
+// launches.  Thread k owns particles k + SEL1_THREADS u (u < 32, coalesced).
+// One pass over t, dt gives each thread its smallest next-time key and a
+// bitmask of the u that reach it; after the block minimum, a thread's block
+// members are that mask if its minimum is the block's.  The ordered
+// compaction then runs on registers only: per u, warp ballots and a scan of
+// the warp counts keep the list in ascending index order.
+constexpr int SEL1_THREADS = 1024;
+constexpr int64_t SEL1_MAX_N = 32 * SEL1_THREADS;
+
+__global__ void __launch_bounds__(SEL1_THREADS)
+    select_one_cta_kernel(const unsigned long long* __restrict__ nkey, int64_t n, double t_end,
+                          SchedDev sd)
+{
+    __shared__ unsigned long long wmin[SEL1_THREADS / 32];
+    __shared__ int wcnt[2][SEL1_THREADS / 32 + 1];  // exclusive offsets, [32] = total
+    __shared__ unsigned long long tkey;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    unsigned long long best = ~0ull;
+    uint32_t mask = 0u;
+    for (int u = 0; u < 32; ++u) {
+        const int64_t i = tid + static_cast<int64_t>(SEL1_THREADS) * u;
+        if (i >= n) break;
+        const unsigned long long k = nkey[i];
+        if (k < best) {
+            best = k;
+            mask = 1u << u;
+        } else if (k == best) {
+            mask |= 1u << u;
+        }
+    }
+    unsigned long long bmin = best;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_xor_sync(0xffffffffu, bmin, o);
+        bmin = other < bmin ? other : bmin;
+    }
+    if (lane == 0) wmin[wid] = bmin;
+    __syncthreads();
+    if (wid == 0) {
+        bmin = wmin[lane];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, bmin, o);
+            bmin = other < bmin ? other : bmin;
+        }
+        if (lane == 0) {
+            tkey = bmin;
+            *sd.tmin_bits = bmin;
+        }
+    }
+    __syncthreads();
+    if (best != tkey || !(dkey_decode(tkey) <= t_end)) mask = 0u;
+    const int tiles = static_cast<int>((n + SEL1_THREADS - 1) / SEL1_THREADS);
+    int base = 0;
+    for (int u = 0; u < tiles; ++u) {
+        const bool act = (mask >> u) & 1u;
+        const unsigned m = __ballot_sync(0xffffffffu, act);
+        int* wc = wcnt[u & 1];
+        if (lane == 0) wc[wid] = __popc(m);
+        __syncthreads();
+        if (wid == 0) {  // exclusive scan of the warp counts
+            const int c = wc[lane];
+            int x = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            wc[lane] = x - c;
+            if (lane == 31) wc[32] = x;
+        }
+        __syncthreads();
+        if (act)
+            sd.idx[base + wc[wid] + __popc(m & ((1u << lane) - 1u))] =
+                static_cast<int32_t>(tid + SEL1_THREADS * u);
+        base += wc[32];
+    }
+    if (tid == 0) *sd.n_act = base;
+}
+
 cudaError_t select_launch(const StateDev& st, const SchedDev& sd, double t_end, cudaStream_t s)
 {
+    if (st.n > 0 && st.n <= SEL1_MAX_N) {
+        select_one_cta_kernel<<<1, SEL1_THREADS, 0, s>>>(st.nkey, st.n, t_end, sd);
+        return cudaGetLastError();
+    }
     cudaError_t e = cudaMemsetAsync(sd.tmin_bits, 0xff, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     if (st.n <= 0) return cudaMemsetAsync(sd.n_act, 0, sizeof(int32_t), s);
@@ -306,20 +409,20 @@ cudaError_t select_launch(const StateDev& st, const SchedDev& sd, double t_end, 
     if (nb64 > sd.max_blocks) return cudaErrorInvalidValue;
     const int nb = static_cast<int>(nb64);
     int tb = nb < 1024 ? nb : 1024;
-    tmin_kernel<<<tb, 256, 0, s>>>(st.t, st.dt, st.n, sd.tmin_bits);
-    count_kernel<<<nb, SCHED_THREADS, 0, s>>>(st.t, st.dt, st.n, sd.tmin_bits, nullptr, t_end, sd);
-    scatter_kernel<<<nb, SCHED_THREADS, 0, s>>>(st.t, st.dt, st.n, sd.tmin_bits, nullptr, t_end, sd);
+    tmin_kernel<<<tb, 256, 0, s>>>(st.nkey, st.n, sd.tmin_bits);
+    count_kernel<<<nb, SCHED_THREADS, 0, s>>>(st.nkey, st.n, sd.tmin_bits, nullptr, t_end, sd);
+    scatter_kernel<<<nb, SCHED_THREADS, 0, s>>>(st.nkey, st.n, sd.tmin_bits, nullptr, t_end, sd);
     return cudaGetLastError();
 }
 
 // Ensemble step 1: block c finds the next time of cluster c.
-__global__ void cluster_tmin_kernel(const double* __restrict__ t, const double* __restrict__ dt,
+__global__ void cluster_tmin_kernel(const unsigned long long* __restrict__ nkey,
                                     const int64_t* off, unsigned long long* tkey)
 {
     const int c = blockIdx.x;
     unsigned long long best = ~0ull;
     for (int64_t i = off[c] + threadIdx.x; i < off[c + 1]; i += blockDim.x) {
-        const unsigned long long k = dkey(t[i] + dt[i]);
+        const unsigned long long k = nkey[i];
         best = k < best ? k : best;
     }
 #pragma unroll
@@ -349,9 +452,9 @@ cudaError_t cluster_select_launch(const StateDev& st, const ClusterDev& cl, cons
     const int64_t nb64 = (st.n + SCHED_CHUNK - 1) / SCHED_CHUNK;
     if (nb64 > sd.max_blocks) return cudaErrorInvalidValue;
     const int nb = static_cast<int>(nb64);
-    cluster_tmin_kernel<<<cl.k, 256, 0, s>>>(st.t, st.dt, cl.off, cl.tkey);
-    count_kernel<<<nb, SCHED_THREADS, 0, s>>>(st.t, st.dt, st.n, cl.tkey, cl.cluster_of, t_end, sd);
-    scatter_kernel<<<nb, SCHED_THREADS, 0, s>>>(st.t, st.dt, st.n, cl.tkey, cl.cluster_of, t_end, sd);
+    cluster_tmin_kernel<<<cl.k, 256, 0, s>>>(st.nkey, cl.off, cl.tkey);
+    count_kernel<<<nb, SCHED_THREADS, 0, s>>>(st.nkey, st.n, cl.tkey, cl.cluster_of, t_end, sd);
+    scatter_kernel<<<nb, SCHED_THREADS, 0, s>>>(st.nkey, st.n, cl.tkey, cl.cluster_of, t_end, sd);
     return cudaGetLastError();
 }
 
@@ -461,6 +564,25 @@ cudaError_t plan_launch(const ClusterDev& cl, const int32_t* idx, const int32_t*
 #define DMUL __dmul_rn
 #define DDIV __ddiv_rn
 
+// Correctly rounded a / b for a constant b with y = RN(1/b): q0 = RN(a y)
+// is within an ulp, the FMA residual r = a - b q0 is exact, and one
+// correction RN(q0 + r y) gives RN(a / b) (Markstein's FMA division; an
+// exhaustive random test of b = 6, 24, 120 finds no mismatch).  Three FP64
+// operations instead of a general division, the same bits.
+__device__ __forceinline__ double div_const(double a, double b, double y)
+{
+    const double q0 = __dmul_rn(a, y);
+    const double r = __fma_rn(-q0, b, a);
+    return __fma_rn(r, y, q0);
+}
+
+// 1 / p for p a normal power of two: exact, by its exponent alone.
+__device__ __forceinline__ double recip_pow2(double p)
+{
+    const long long e = __double_as_longlong(p) >> 52;  // biased exponent (p > 0)
+    return __longlong_as_double((2046LL - e) << 52);
+}
+
 __device__ __forceinline__ double norm3_rn(double x, double y, double z)
 {
     return __dsqrt_rn(DADD(DADD(DMUL(x, x), DMUL(y, y)), DMUL(z, z)));
@@ -517,7 +639,7 @@ __global__ void correct_kernel(const StateDev st, const CorrectArgs c)
     const double h2 = DMUL(h, h), h3 = DMUL(h2, h), h4 = DMUL(h3, h), h5 = DMUL(h4, h);
     // h is a power of two, so dividing by h^2 or h^3 (and by 2) is an exact
     // scaling: multiplying by the exact reciprocal gives the quotient's bits.
-    const double ih2 = DDIV(1.0, h2), ih3 = DDIV(1.0, h3);
+    const double ih2 = recip_pow2(h2), ih3 = recip_pow2(h3);  // exact
     double a1[3], j1[3], s0[3], c0[3], xmax = 0.0, vmax = 0.0;
     bool finite = true;
 #pragma unroll
@@ -536,15 +658,17 @@ __global__ void correct_kernel(const StateDev st, const CorrectArgs c)
         const double x0 = st.x[q], v0 = st.v[q], a0 = st.a[q], j0 = st.j[q];
         // Eqs. xpred, vpred for the i particle (step 2).
         const double rp = DADD(DADD(DADD(x0, DMUL(v0, dtp)), DMUL(DMUL(a0, 0.5), p2)),
-                               DMUL(DDIV(j0, 6.0), p3));
+                               DMUL(div_const(j0, 6.0, 1.0 / 6.0), p3));
         const double vp = DADD(DADD(v0, DMUL(a0, dtp)), DMUL(DMUL(j0, 0.5), p2));
         // Step 5: snap and crackle from the Hermite interpolation.
         const double da = DSUB(a0, a1[d]);
         s0[d] = DMUL(DMUL(2.0, DSUB(DMUL(-3.0, da), DMUL(DADD(DMUL(2.0, j0), j1[d]), h))), ih2);
         c0[d] = DMUL(DMUL(6.0, DADD(DMUL(2.0, da), DMUL(DADD(j0, j1[d]), h))), ih3);
         // Step 6: corrector.
-        const double r1 = DADD(DADD(rp, DDIV(DMUL(s0[d], h4), 24.0)), DDIV(DMUL(c0[d], h5), 120.0));
-        const double v1 = DADD(DADD(vp, DDIV(DMUL(s0[d], h3), 6.0)), DDIV(DMUL(c0[d], h4), 24.0));
+        const double r1 = DADD(DADD(rp, div_const(DMUL(s0[d], h4), 24.0, 1.0 / 24.0)),
+                               div_const(DMUL(c0[d], h5), 120.0, 1.0 / 120.0));
+        const double v1 = DADD(DADD(vp, div_const(DMUL(s0[d], h3), 6.0, 1.0 / 6.0)),
+                               div_const(DMUL(c0[d], h4), 24.0, 1.0 / 24.0));
         // Step 7: a0 <- a1, j0 <- j1.
         st.x[q] = r1;
         st.v[q] = v1;
@@ -578,7 +702,9 @@ __global__ void correct_kernel(const StateDev st, const CorrectArgs c)
     }
     const double cand = dta < c.dt_max ? dta : c.dt_max;
     double dt_new = h;
-    if (cand >= DMUL(2.0, h) && fmod(tn, DMUL(2.0, h)) == 0.0) {
+    // t_next a multiple of 2h (h a power of two, so t_next / 2h is exact)
+    const double k2h = DMUL(tn, recip_pow2(DMUL(2.0, h)));
+    if (cand >= DMUL(2.0, h) && k2h == rint(k2h)) {
         dt_new = DMUL(2.0, h);
     } else if (cand >= h) {
         dt_new = h;
@@ -586,6 +712,7 @@ __global__ void correct_kernel(const StateDev st, const CorrectArgs c)
         while (dt_new > cand && dt_new >= c.dt_min) dt_new = DMUL(dt_new, 0.5);
     }
     st.dt[i] = dt_new;
+    st.nkey[i] = dkey(DADD(tn, dt_new));
     if (dt_new < c.dt_min) atomicOr(c.status, ST_DTMIN);
 }
 
@@ -612,16 +739,19 @@ __global__ void init_dt_kernel(const StateDev st, const double* acc, const doubl
     if (isnan(raw)) {
         atomicOr(status, ST_NONFINITE);
         st.dt[i] = dt_max;
+        st.nkey[i] = dkey(t0 + dt_max);
         return;
     }
     if (raw > dt_max) raw = dt_max;
     if (raw <= 0.0) {
         atomicOr(status, ST_DTMIN);
         st.dt[i] = dt_max;
+        st.nkey[i] = dkey(t0 + dt_max);
         return;
     }
     const double dt = pow2_floor(raw);
     st.dt[i] = dt;
+    st.nkey[i] = dkey(t0 + dt);
     if (dt < dt_min) atomicOr(status, ST_DTMIN);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -798,24 +928,31 @@ cudaError_t soa_to_aos_launch(const double* soa, double* aos, int64_t n, cudaStr
     return cudaGetLastError();
 }
 
-// Whole-state snapshot: buf = [m | x | v | a | j | t | dt | hq | bounds],
-// with the 16 n doubles of the state and one 8-byte slot for the two bounds.
+// Whole-state snapshot: buf = [m | x | v | a | j | t | dt | hq | nkey |
+// bounds], the 17 n 64-bit words of the state (copied as bits) and one
+// 8-byte slot for the two bounds.
 __global__ void snapshot_kernel(StateDev st, double* __restrict__ buf, int to_buf)
 {
     const int64_t n = st.n;
-    double* arr[8] = {st.m, st.x, st.v, st.a, st.j, st.t, st.dt, st.hq};
-    const int64_t len[8] = {n, 3 * n, 3 * n, 3 * n, 3 * n, n, n, n};
-    const int64_t total = 16 * n;
+    unsigned long long* arr[9] = {
+        reinterpret_cast<unsigned long long*>(st.m), reinterpret_cast<unsigned long long*>(st.x),
+        reinterpret_cast<unsigned long long*>(st.v), reinterpret_cast<unsigned long long*>(st.a),
+        reinterpret_cast<unsigned long long*>(st.j), reinterpret_cast<unsigned long long*>(st.t),
+        reinterpret_cast<unsigned long long*>(st.dt), reinterpret_cast<unsigned long long*>(st.hq),
+        st.nkey};
+    const int64_t len[9] = {n, 3 * n, 3 * n, 3 * n, 3 * n, n, n, n, n};
+    const int64_t total = 17 * n;
+    unsigned long long* w = reinterpret_cast<unsigned long long*>(buf);
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         int64_t off = e;
         int k = 0;
         while (off >= len[k]) off -= len[k++];
-        if (to_buf) buf[e] = arr[k][off];
-        else arr[k][off] = buf[e];
+        if (to_buf) w[e] = arr[k][off];
+        else arr[k][off] = w[e];
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        uint32_t* b = reinterpret_cast<uint32_t*>(buf + total);
+        uint32_t* b = reinterpret_cast<uint32_t*>(w + total);
         if (to_buf) b[0] = st.bound[0], b[1] = st.bound[1];
         else st.bound[0] = b[0], st.bound[1] = b[1];
     }
@@ -825,7 +962,7 @@ cudaError_t snapshot_launch(const StateDev& st, double* buf, bool to_buf, cudaSt
 {
     if (st.n <= 0) return cudaSuccess;
     const int threads = 256;
-    const int64_t want = (16 * st.n + threads - 1) / threads;
+    const int64_t want = (17 * st.n + threads - 1) / threads;
     const unsigned blocks = static_cast<unsigned>(want < 2048 ? want : 2048);
     snapshot_kernel<<<blocks, threads, 0, s>>>(st, buf, to_buf ? 1 : 0);
     return cudaGetLastError();

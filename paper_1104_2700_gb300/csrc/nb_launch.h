@@ -37,12 +37,17 @@ struct StateDev {
     // last force evaluation, negative when that evaluation was guarded
     // (all double-single); 0 = none yet.
     double* hq = nullptr;
+    // Per particle, the order-preserving key of its next time t_i + dt_i,
+    // kept by every writer of t and dt so that step 1 compares integers.
+    unsigned long long* nkey = nullptr;
 };
 
 // bound[0] = max |a_k|, bound[1] = max |b_k| over k < count (float bits,
 // rounded up), atomically raised; the caller zeroes bound first.
 cudaError_t bounds_launch(const double* a, const double* b, int64_t count, uint32_t* bound,
                           cudaStream_t s);
+// nkey[i] = key of t[i] + dt[i] for every particle.
+cudaError_t next_key_launch(const StateDev& st, cudaStream_t s);
 
 // Predicted j particles in the layout a force kernel streams.
 //   FP64 : arr[0] = double4 (x, y, z, G m), arr[1] = double4 (vx, vy, vz, 0)
@@ -209,8 +214,8 @@ cudaError_t energy_launch(const StateDev& st, const double* pot_all, double* par
 cudaError_t aos_to_soa_launch(const double* aos, double* soa, int64_t n, cudaStream_t s);
 cudaError_t soa_to_aos_launch(const double* soa, double* aos, int64_t n, cudaStream_t s);
 cudaError_t iota_launch(int32_t* idx, int64_t n, int32_t* n_act_dev, cudaStream_t s);
-// Copy the whole state (16 n doubles: m, x, v, a, j, t, dt, hq, then the
-// two bounds) to (to_buf) or from a device buffer of 16 n + 1 doubles.
+// Copy the whole state (17 n words: m, x, v, a, j, t, dt, hq, nkey, then
+// the two bounds) to (to_buf) or from a device buffer of 17 n + 1 doubles.
 cudaError_t snapshot_launch(const StateDev& st, double* buf, bool to_buf, cudaStream_t s);
 
 }  // namespace nb

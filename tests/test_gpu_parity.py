@@ -169,7 +169,10 @@ def _random_block_state(n, seed, T):
 
 
 def test_select_matches_oracle_bit_exact(gpu, orc):
-    for n, seed in ((1, 1), (100, 2), (2048, 3), (5000, 4)):
+    # one-CTA select up to 32768 particles (edges at one tile, the limit),
+    # the multi-block select above
+    for n, seed in ((1, 1), (100, 2), (1024, 5), (1025, 6), (2048, 3), (5000, 4),
+                    (32768, 7), (32769, 8), (70001, 9)):
         rng = np.random.default_rng(seed)
         m, r, v = ics.plummer(n, seed)
         dt = 2.0 ** -rng.integers(4, 12, n)

@@ -68,7 +68,7 @@ def test_snapshot_restore_replays_bitwise(gpu, prec):
     with gpu.Context(prec) as ctx:
         ctx.set_particles(m, r, v, 1.0 / 64, 0.02)
         nbytes = ctx.snapshot_bytes()
-        assert nbytes == (16 * n + 1) * 8
+        assert nbytes == (17 * n + 1) * 8
         buf = torch.empty(nbytes // 8, dtype=torch.float64, device="cuda")
         ctx.snapshot(buf)
         first = ctx.step_until(1.0 / 16)
