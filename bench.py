@@ -73,6 +73,10 @@ def parse_args():
                         "(default ds,fp64) to --t-end and report steps, rate, energy drift")
     p.add_argument("--t-end", type=float, default=None,
                    help="end time for --integrate (a multiple of dt_max = 1/16)")
+    p.add_argument("--energy-study", action="store_true",
+                   help="instead of the sweep: energy error against step count over "
+                        "eta (Sec. 4, Fig. err_itg): Plummer N = 1024, eps = 4/N, "
+                        "t = 0 -> 0.375")
     return p.parse_args()
 
 
@@ -808,9 +812,69 @@ def run_integration(args):
     print(json.dumps(out), flush=True)
 
 
+def run_energy_study(args):
+    """Sec. 4's integration test (Fig. err_itg): relative error of the total
+    energy, averaged over the outputs t = k/16 up to 1/8 of a crossing time
+    (t = 0.375, as Sec. 4 states it), against the number of steps per
+    particle per crossing time (2 sqrt 2), for a range of eta.  The potential is the FP64 one in every
+    mode, so the error is the integration's.  The FP64 oracle runs the same
+    integrations on the host cores."""
+    import torch
+    from paper_1104_2700_gb300 import build as nb_build
+    from paper_1104_2700_gb300 import nbody
+    from oracle import oracle
+    nb_build.build()
+    oracle.build()
+    n, seed = 1024, 1
+    eps, t_end, crossing = 4.0 / n, 0.375, 2.0 * math.sqrt(2.0)
+    m, r, v = ics.plummer(n, seed)
+    # eta enters Eq. timestep outside the square root (dt = eta (...)^(1/2));
+    # the start rule scales with it (eta_start = eta / 4), since a fixed
+    # eta_start lets the first steps set an eta-independent error floor
+    etas = [0.01, 0.02, 0.04, 0.08, 0.16, 0.32]
+    # MIXED is left out by default: its timestep collapse (precision_ablation)
+    # makes its step count say nothing about the integrator's order
+    modes = [x for x in args.modes.split(",") if x] if args.modes != "mixed,hybrid,ds,fp64" \
+        else ["fp64", "ds", "hybrid"]
+    outs = [k / 16 for k in range(1, int(round(t_end * 16)) + 1)]
+    rows = []
+    for eta in etas:
+        row = {"eta": eta}
+        for prec in modes:
+            with nbody.Context(prec, eta_start=eta / 4) as ctx:
+                ctx.set_particles(m, r, v, eps, eta)
+                k0, w0 = ctx.energy(fp64_potential=True)
+                errs, inter = [], 0
+                for t in outs:
+                    _, i = ctx.step_until(t)
+                    inter += i
+                    k1, w1 = ctx.energy(fp64_potential=True)
+                    errs.append(abs((k1 + w1) - (k0 + w0)) / abs(k0 + w0))
+            row[prec] = {"n_step": inter / n / n * crossing / t_end,
+                         "mean_rel_energy_error": float(np.mean(errs)),
+                         "final_rel_energy_error": errs[-1]}
+        s = oracle.State(m, r, v, eps, eta, eta_start=eta / 4, nthreads=os.cpu_count() or 1)
+        e0 = s.energy()
+        errs = []
+        for t in outs:
+            s.run(t)
+            errs.append(abs(s.energy() - e0) / abs(e0))
+        row["oracle"] = {"n_step": s.n_inter / n / n * crossing / t_end,
+                         "mean_rel_energy_error": float(np.mean(errs)),
+                         "final_rel_energy_error": errs[-1]}
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    print(json.dumps({"study": "energy error vs steps per crossing time (Sec. 4)",
+                      "eta_start": "eta / 4",
+                      "workload": f"plummer_n{n}_seed{seed}_eps4/n", "t_end": t_end,
+                      "outputs": outs, "data": "synthetic", "rows": rows}), flush=True)
+
+
 def main():
     args = parse_args()
-    if args.integrate:
+    if args.energy_study:
+        run_energy_study(args)
+    elif args.integrate:
         run_integration(args)
     elif args.profile:
         run_profile(args)
