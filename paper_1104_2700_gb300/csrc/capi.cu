@@ -1041,9 +1041,9 @@ nb_status nb_autotune(nb_ctx* c, nb_tuning* out)
                                static_cast<int32_t>(std::min<int64_t>(256, n)),
                                static_cast<int32_t>(std::min<int64_t>(2048, n)),
                                static_cast<int32_t>(std::min<int64_t>(16384, n))};
-    // candidates: i per thread (two only for MIXED single systems) x CTAs per SM
+    // candidates: i per thread (two only for MIXED and HYBRID single systems) x CTAs per SM
     std::vector<int> its = {1};
-    if (c->prec == Prec::MIXED && !c->ens) its.push_back(2);
+    if ((c->prec == Prec::MIXED || c->prec == Prec::HYBRID) && !c->ens) its.push_back(2);
     struct Cand {
         int it, cps;
         double us[4];

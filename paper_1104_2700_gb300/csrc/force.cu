@@ -436,14 +436,15 @@ struct PolicyDS {
 // evaluated in DS after it, each lane walking its own list, so the warp runs
 // the DS pair about max-over-lanes(near pairs in the tile) times per tile.
 constexpr float HY_THETA = 0.1f;
-constexpr int HY_RUN = 8;
+constexpr int HY_RUN = 16;
 // Integration guard.  The Hermite interpolation divides a0 - a1 by dt^3
 // (crackle), so an absolute force noise da sets a floor 12 da / dt^3 under
 // the crackle that Eq. timestep sees; once that floor rivals the true value
 // the timestep shrinks and keeps shrinking.  Each evaluation estimates its
-// far-field noise from the FP32 roundings it made: every far pair's term
-// (|a| bound b = G m / r^2) and every 8-term run sum (bounded by the sum of
-// its b), as 2 u sqrt(sum b^2 + sum run^2).  When the last estimate exceeds
+// far-field noise from the FP32 roundings it made, bounded through the run
+// sums: with b = G m / r^2 the |a| bound of a far pair, each HY_RUN-term run
+// contributes (sum of its b)^2 >= sum of its b^2, and the estimate is
+// 2 u sqrt(sum over runs of (sum b)^2).  When the last estimate exceeds
 // HY_GUARD * eta |j| dt / 12 (the crackle scale of the particle's current
 // step), the particle is evaluated entirely in double-single.  Switching
 // between the two precisions itself steps a0 - a1 by the full noise, so the
@@ -540,11 +541,11 @@ struct PolicyHybrid {
         for (int q = 0; q < IT; ++q) nlo[q] = nhi[q] = 0u;
 #pragma unroll 1
         for (int k0 = 0; k0 < TJ; k0 += HY_RUN) {
-            float ax[IT], ay[IT], az[IT], jx[IT], jy[IT], jz[IT], ph[IT], qs[IT], bs[IT];
+            float ax[IT], ay[IT], az[IT], jx[IT], jy[IT], jz[IT], ph[IT], bs[IT];
             uint32_t run[IT];
 #pragma unroll
             for (int q = 0; q < IT; ++q) {
-                ax[q] = ay[q] = az[q] = jx[q] = jy[q] = jz[q] = ph[q] = qs[q] = bs[q] = 0.f;
+                ax[q] = ay[q] = az[q] = jx[q] = jy[q] = jz[q] = ph[q] = bs[q] = 0.f;
                 run[q] = 0u;
             }
 #pragma unroll 4
@@ -574,12 +575,13 @@ struct PolicyHybrid {
                     float h = fmaf(-r2, yy, 1.f);
                     h = fmaf(-r2, fmaf(y, y, -yy), h);
                     y = fmaf(0.5f * y, h, y);
+                    if (self) y = 0.f;  // r = 0 when eps = 0: keep inf out of every term
+                    const float mr0 = A.w * y;
                     // noise estimate over the pairs the natural test calls far
-                    const float am = (nat || self) ? 0.f : A.w * y * y;
-                    qs[q] = fmaf(am, am, qs[q]);
-                    bs[q] += am;
-                    if (self || near) y = 0.f;
-                    const float mr = A.w * y;
+                    bs[q] += (nat || self) ? 0.f : mr0 * y;
+                    // near pairs (and the self pair) add nothing here: every
+                    // FP32 term below carries the factor m / r
+                    const float mr = (self || near) ? 0.f : mr0;
                     const float ri2 = y * y;
                     const float g = mr * ri2;
                     const float rv = fmaf(dx, dvx, fmaf(dy, dvy, dz * dvz));
@@ -599,7 +601,7 @@ struct PolicyHybrid {
                 ac[q].ax.fold(ax[q]), ac[q].ay.fold(ay[q]), ac[q].az.fold(az[q]);
                 ac[q].jx.fold(jx[q]), ac[q].jy.fold(jy[q]), ac[q].jz.fold(jz[q]);
                 ac[q].ph.fold(ph[q]);
-                ac[q].q += fmaf(bs[q], bs[q], qs[q]);
+                ac[q].q = fmaf(bs[q], bs[q], ac[q].q);
                 if (k0 < 32) nlo[q] |= run[q] << k0;
                 else nhi[q] |= run[q] << (k0 - 32);
             }
@@ -949,6 +951,7 @@ const void* kernel_ptr(Prec p, int it, bool ens = false)
         return nullptr;
     case Prec::HYBRID:
         if (it == 1) return kfn<PolicyHybrid<1>, 1>(ens);
+        if (it == 2) return kfn<PolicyHybrid<2>, 2>(ens);
         return nullptr;
     }
     return nullptr;

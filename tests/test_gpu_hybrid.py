@@ -123,3 +123,18 @@ def test_hybrid_integration_guard_prevents_step_collapse(gpu):
         if prec == "hybrid":
             assert dt.min() >= 2.0 ** -17
     assert steps["hybrid"] == pytest.approx(steps["ds"], rel=0.05)
+
+
+@pytest.mark.parametrize("it", [1, 2])
+def test_force_hybrid_launch_shapes_agree(gpu, orc, it):
+    """One and two i particles per lane: both within 1e-6 everywhere."""
+    n, eps = 5000, 4 / 5000
+    m, r, v = ics.plummer(n, 606)
+    a_all, j_all, p_all = orc.force(m, r, v, eps, nthreads=NTHREADS)
+    idx = np.arange(n, dtype=np.int32)
+    with gpu.Context("hybrid", i_per_thread=it) as ctx:
+        ctx.set_state(m, r, v, a_all, j_all, np.zeros(n), np.full(n, 1.0 / 16), eps=eps, eta=0.02)
+        ctx.predict(0.0)
+        acc, jerk, pot = ctx.force(idx)
+    assert max(_rel(acc, a_all).max(), _rel(jerk, j_all).max(),
+               (np.abs(pot - p_all) / np.abs(p_all)).max()) < 1e-6
