@@ -486,15 +486,18 @@ struct PolicyHybrid {
         s.all_near = false;
         s.particle = particle;
         if (p < 0) return;
+        // The near radius and the guard are thresholds, not results: FP32
+        // is ample, and it keeps this per-group set-up off the FP64 pipe.
         const int64_t n = f.n;
-        double a2 = 0.0, j2 = 0.0;
+        float a2 = 0.f, j2 = 0.f;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const double a = f.st_a[c * n + particle], jj = f.st_j[c * n + particle];
-            a2 = fma(a, a, a2);
-            j2 = fma(jj, jj, j2);
+            const float a = static_cast<float>(f.st_a[c * n + particle]);
+            const float jj = static_cast<float>(f.st_j[c * n + particle]);
+            a2 = fmaf(a, a, a2);
+            j2 = fmaf(jj, jj, j2);
         }
-        const float A = static_cast<float>(sqrt(a2)), J = static_cast<float>(sqrt(j2));
+        const float A = sqrtf(a2), J = sqrtf(j2);
         const float vi = sqrtf(s.vxh * s.vxh + s.vyh * s.vyh + s.vzh * s.vzh);
         const float V = vi + 1.7320509f * __uint_as_float(*f.bound_v) * 1.0001f;
         // 1/0 = inf: no estimate yet, every pair is near
@@ -502,10 +505,13 @@ struct PolicyHybrid {
         const float x = 4.f * V / (HY_THETA * J);
         const float cb = cbrtf(x);
         s.cj = cb * cb;
-        const double hq = f.st_hq[particle];
-        const double noise = 2.0 * HY_U * sqrt(fabs(hq));
-        const double ratio = 12.0 * noise / (HY_GUARD * f.eta * sqrt(j2) * f.st_dt[particle]);
-        s.all_near = hq < 0.0 ? ratio > HY_GUARD_OFF : ratio > 1.0;
+        const float hq = static_cast<float>(f.st_hq[particle]);
+        const float noise = 2.f * static_cast<float>(HY_U) * sqrtf(fabsf(hq));
+        const float scale = static_cast<float>(HY_GUARD * f.eta) * J *
+                            static_cast<float>(f.st_dt[particle]);
+        // ratio = 12 noise / scale, compared without a division
+        s.all_near = hq < 0.f ? 12.f * noise > static_cast<float>(HY_GUARD_OFF) * scale
+                              : 12.f * noise > scale;
     }
 
     __device__ static void values(const Acc& a, double (&v)[NV])
