@@ -895,17 +895,24 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
                 }
                 __threadfence();
                 if (lane == 0) *cnt = 0u;
+                // Entry by entry: each entry's NV values load together (and
+                // two entries are in flight), then add into NV running sums;
+                // every value still sums its entries in ascending order.
 #pragma unroll
-                for (int q = 0; q < IT; ++q)
+                for (int q = 0; q < IT; ++q) {
 #pragma unroll
-                    for (int c = 0; c < NV; ++c) {
-                        double sum = 0.0;
-#pragma unroll 4
-                        for (int64_t u = 0; u < cs; ++u)
-                            sum += __ldcg(f.scratch + (size_t)(key + (first + u) * stride) * NV * GI +
-                                          c * GI + q * 32 + lane);
-                        v[q][c] = sum;
+                    for (int c = 0; c < NV; ++c) v[q][c] = 0.0;
+#pragma unroll 2
+                    for (int64_t u = 0; u < cs; ++u) {
+                        const double* e = f.scratch + (size_t)(key + (first + u) * stride) * NV * GI +
+                                          q * 32 + lane;
+                        double x[NV];
+#pragma unroll
+                        for (int c = 0; c < NV; ++c) x[c] = __ldcg(e + c * GI);
+#pragma unroll
+                        for (int c = 0; c < NV; ++c) v[q][c] += x[c];
                     }
+                }
                 r = chunk;
                 kk = (kk + RB - 1) / RB;
                 stride *= RB;
