@@ -135,7 +135,8 @@ struct PolicyFP64 {
     }
 
     static constexpr int NV = 7;  // reduced values: acc (3), jerk (3), pot
-    __device__ static void values(const Acc& a, double (&v)[NV])
+    using TV = double;            // value type of the split-group tree
+    __device__ static void values(const Acc& a, TV (&v)[NV])
     {
         v[0] = a.ax, v[1] = a.ay, v[2] = a.az;
         v[3] = a.jx, v[4] = a.jy, v[5] = a.jz;
@@ -232,11 +233,13 @@ struct PolicyMixed {
     }
 
     static constexpr int NV = 7;  // reduced values: acc (3), jerk (3), pot
-    __device__ static void values(const Acc& a, double (&v)[NV])
+    using TV = DSPair;
+    __device__ static void values(const Acc& a, TV (&v)[NV])
     {
-        v[0] = a.ax.value(), v[1] = a.ay.value(), v[2] = a.az.value();
-        v[3] = a.jx.value(), v[4] = a.jy.value(), v[5] = a.jz.value();
-        v[6] = -a.ph.value();
+        v[0] = ds_pair_of(a.ax), v[1] = ds_pair_of(a.ay), v[2] = ds_pair_of(a.az);
+        v[3] = ds_pair_of(a.jx), v[4] = ds_pair_of(a.jy), v[5] = ds_pair_of(a.jz);
+        v[6] = ds_pair_of(a.ph);
+        v[6].h = -v[6].h, v[6].l = -v[6].l;
     }
 };
 
@@ -269,11 +272,12 @@ struct DSAccs {
     {
         ax.zero(), ay.zero(), az.zero(), jx.zero(), jy.zero(), jz.zero(), ph.zero();
     }
-    __device__ void values(double (&v)[7]) const
+    __device__ void values(DSPair (&v)[7]) const
     {
-        v[0] = ax.value(), v[1] = ay.value(), v[2] = az.value();
-        v[3] = jx.value(), v[4] = jy.value(), v[5] = jz.value();
-        v[6] = -ph.value();
+        v[0] = ds_pair_of(ax), v[1] = ds_pair_of(ay), v[2] = ds_pair_of(az);
+        v[3] = ds_pair_of(jx), v[4] = ds_pair_of(jy), v[5] = ds_pair_of(jz);
+        v[6] = ds_pair_of(ph);
+        v[6].h = -v[6].h, v[6].l = -v[6].l;
     }
 };
 
@@ -415,7 +419,8 @@ struct PolicyDS {
     }
 
     static constexpr int NV = 7;
-    __device__ static void values(const Acc& a, double (&v)[NV]) { a.values(v); }
+    using TV = DSPair;
+    __device__ static void values(const Acc& a, TV (&v)[NV]) { a.values(v); }
 };
 
 // Hybrid precision (no counterpart in the paper, which evaluates every pair
@@ -514,13 +519,14 @@ struct PolicyHybrid {
                               : 12.f * noise > scale;
     }
 
-    __device__ static void values(const Acc& a, double (&v)[NV])
+    using TV = DSPair;
+    __device__ static void values(const Acc& a, TV (&v)[NV])
     {
-        double w[7];
+        DSPair w[7];
         a.values(w);
 #pragma unroll
         for (int c = 0; c < 7; ++c) v[c] = w[c];
-        v[7] = static_cast<double>(a.q);
+        v[7].h = a.q, v[7].l = 0.f;
     }
 
     __device__ static void finish(const ForceParams& f, const I& s, const double (&v)[NV])
@@ -866,7 +872,8 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
             const int64_t wf = owner_warp(gi.tile0, T, Pu);
             const int64_t wl = owner_warp(gi.tile0 + gi.ntiles - 1, T, Pu);
             constexpr int NV = K::NV;
-            double v[IT][NV];
+            using TV = typename K::TV;
+            TV v[IT][NV];
 #pragma unroll
             for (int q = 0; q < IT; ++q) K::values(ac[q], v[q]);
             const int64_t key = wf + g;
@@ -875,11 +882,12 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
             int64_t stride = 1;
             bool final_here = true;
             for (int level = 0; kk > 1; ++level) {
-                double* mine = f.scratch + (size_t)(key + r * stride) * NV * GI;
+                const size_t mine = (size_t)(key + r * stride) * NV * GI;
 #pragma unroll
                 for (int q = 0; q < IT; ++q)
 #pragma unroll
-                    for (int c = 0; c < NV; ++c) mine[c * GI + q * 32 + lane] = v[q][c];
+                    for (int c = 0; c < NV; ++c)
+                        tree_store(f.scratch, mine + c * GI + q * 32 + lane, v[q][c]);
                 __threadfence();
                 __syncwarp();
                 const int64_t chunk = r / RB;
@@ -901,16 +909,15 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
 #pragma unroll
                 for (int q = 0; q < IT; ++q) {
 #pragma unroll
-                    for (int c = 0; c < NV; ++c) v[q][c] = 0.0;
-#pragma unroll 2
+                    for (int c = 0; c < NV; ++c) tree_zero(v[q][c]);
+#pragma unroll 4
                     for (int64_t u = 0; u < cs; ++u) {
-                        const double* e = f.scratch + (size_t)(key + (first + u) * stride) * NV * GI +
-                                          q * 32 + lane;
-                        double x[NV];
+                        const size_t e = (size_t)(key + (first + u) * stride) * NV * GI + q * 32 + lane;
+                        TV x[NV];
 #pragma unroll
-                        for (int c = 0; c < NV; ++c) x[c] = __ldcg(e + c * GI);
+                        for (int c = 0; c < NV; ++c) tree_load(f.scratch, e + c * GI, x[c]);
 #pragma unroll
-                        for (int c = 0; c < NV; ++c) v[q][c] += x[c];
+                        for (int c = 0; c < NV; ++c) tree_add(v[q][c], x[c]);
                     }
                 }
                 r = chunk;
@@ -922,14 +929,17 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
                 for (int q = 0; q < IT; ++q) {
                     const int64_t a = gi.act_begin + q * 32 + lane;
                     if (a < gi.act_begin + gi.act_count) {
-                        f.acc[3 * a + 0] = v[q][0];
-                        f.acc[3 * a + 1] = v[q][1];
-                        f.acc[3 * a + 2] = v[q][2];
-                        f.jerk[3 * a + 0] = v[q][3];
-                        f.jerk[3 * a + 1] = v[q][4];
-                        f.jerk[3 * a + 2] = v[q][5];
-                        f.pot[a] = v[q][6];
-                        if constexpr (K::NV > 7) K::finish(f, is[q], v[q]);
+                        double o[NV];
+#pragma unroll
+                        for (int c = 0; c < NV; ++c) o[c] = tree_value(v[q][c]);
+                        f.acc[3 * a + 0] = o[0];
+                        f.acc[3 * a + 1] = o[1];
+                        f.acc[3 * a + 2] = o[2];
+                        f.jerk[3 * a + 0] = o[3];
+                        f.jerk[3 * a + 1] = o[4];
+                        f.jerk[3 * a + 2] = o[5];
+                        f.pot[a] = o[6];
+                        if constexpr (K::NV > 7) K::finish(f, is[q], o);
                     }
                 }
             }

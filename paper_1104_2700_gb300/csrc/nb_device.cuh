@@ -179,4 +179,48 @@ struct DSAcc {
     }
 };
 
+// A value of the split-group reduction tree.  Policies that accumulate in
+// double-single hand their partial sums on as normalised float pairs, which
+// the tree adds with TwoSum on the FP32 pipe (GB300's FP64 rate is a small
+// fraction of FP32); a pair occupies the 8 bytes of a double in scratch.
+struct DSPair {
+    float h, l;
+};
+__device__ __forceinline__ DSPair ds_pair_of(const DSAcc& a)
+{
+    DSPair p;
+    two_sum(a.hi, a.lo, p.h, p.l);
+    return p;
+}
+__device__ __forceinline__ void tree_zero(double& a) { a = 0.0; }
+__device__ __forceinline__ void tree_zero(DSPair& a) { a.h = a.l = 0.f; }
+__device__ __forceinline__ void tree_add(double& a, double b) { a += b; }
+__device__ __forceinline__ void tree_add(DSPair& a, DSPair b)
+{
+    float s, e;
+    two_sum(a.h, b.h, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+    a.h = __fadd_rn(s, e);
+    a.l = __fsub_rn(e, __fsub_rn(a.h, s));
+}
+__device__ __forceinline__ void tree_store(double* base, size_t k, double x) { base[k] = x; }
+__device__ __forceinline__ void tree_store(double* base, size_t k, DSPair x)
+{
+    reinterpret_cast<float2*>(base)[k] = make_float2(x.h, x.l);
+}
+__device__ __forceinline__ void tree_load(const double* base, size_t k, double& x)
+{
+    x = __ldcg(base + k);
+}
+__device__ __forceinline__ void tree_load(const double* base, size_t k, DSPair& x)
+{
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(base) + k);
+    x.h = v.x, x.l = v.y;
+}
+__device__ __forceinline__ double tree_value(double x) { return x; }
+__device__ __forceinline__ double tree_value(DSPair x)
+{
+    return static_cast<double>(x.h) + static_cast<double>(x.l);
+}
+
 }  // namespace nb
