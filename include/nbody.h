@@ -51,7 +51,7 @@ typedef enum nb_status {
  *   NB_DS     the same pair formulas in double-single (float-float)
  *             arithmetic built from error-free FP32 transforms.
  *   NB_HYBRID no counterpart in the paper: FP32 pairs (refined rsqrt, FP32
- *             runs of 8 j folded into double-single sums) except near pairs,
+ *             runs of 16 j folded into double-single sums) except near pairs,
  *             whose acceleration or jerk term could exceed 10 % of the
  *             particle's own |a| or |j| (from its state a, j); those are
  *             evaluated in double-single.  A particle whose state has
