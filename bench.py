@@ -77,6 +77,10 @@ def parse_args():
                    help="instead of the sweep: energy error against step count over "
                         "eta (Sec. 4, Fig. err_itg): Plummer N = 1024, eps = 4/N, "
                         "t = 0 -> 0.375")
+    p.add_argument("--jerk-study", action="store_true",
+                   help="instead of the sweep: error distributions of acc, jerk, pot "
+                        "with the jerk summed in FP32 or compensated (Sec. 4, "
+                        "Fig. err_snp_djerk), Plummer N = 1K, 4K, 16K, 64K")
     return p.parse_args()
 
 
@@ -521,9 +525,11 @@ def run_ours(args):
     if not args.no_extra:
         extra = extra_measurements(nbody, torch, dev, stream, world, peak32)
 
-    cpu = None
+    cpu = cpu_paper = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(m, r, v, eps, args.cpu_seconds)
+        cpu_paper = paper_cpu_baseline(m, r, v, eps, args.cpu_seconds / 2,
+                                       (a_ref, j_ref, p_ref))
 
     if rank == 0:
         line = {
@@ -546,6 +552,7 @@ def run_ours(args):
             "fp64_speedup": (hm["value"] / modes["fp64"]["value"]) if "fp64" in modes else None,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "cpu_paper_kernel": cpu_paper,
             "gpu_launches": LAUNCHES_PER_BLOCK_STEP * len(NACTS) * hm["steps"],
             "clocks": clk,
             **extra,
@@ -553,11 +560,13 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
 
 
-# Kernels of one graph-replayed block step of the sweep: the state roll-back
-# (nb_restore), tmin + count + scatter (select), predict, the two force launch
-# variants (each returns at once outside its n_act window), correct.
-LAUNCHES_PER_BLOCK_STEP = 8
+# Kernels of one graph-replayed block step of the sweep (N = 16384): the
+# state roll-back (nb_restore), the one-CTA select (systems up to 32768
+# particles), predict, the two force launch variants (each returns at once
+# outside its n_act window), correct.
+LAUNCHES_PER_BLOCK_STEP = 6
 DTYPES = {"ds": "f32x2 (double-single on the FP32 pipes)", "mixed": "f32", "fp64": "f64",
+          "mixed_spj": "f32",
           "hybrid": "f32 (far pairs) + f32x2 double-single (near pairs)"}
 
 
@@ -628,7 +637,7 @@ def extra_measurements(nbody, torch, dev, stream, world, peak32):
                  (ms[off[q]:off[q + 1]], rs[off[q]:off[q + 1]], vs[off[q]:off[q + 1]], float(eps[q]))}
     for name, (m1, r1, v1, e1) in cases.items():
         row = {}
-        for prec in ("fp64", "ds", "hybrid", "mixed"):
+        for prec in ("fp64", "ds", "hybrid", "mixed", "mixed_spj"):
             # dt_max = t_end, so that every particle ends synchronised at t_end
             with nbody.Context(prec, device=dev.index, stream=stream, dt_max=1.0 / 64) as ctx:
                 ctx.set_particles(m1, r1, v1, e1, 0.02)
@@ -688,6 +697,58 @@ def cpu_baseline(m, r, v, eps, seconds):
                          "sample": f"{k1} of the {n} particles against all j, 1 thread, "
                                    f"{dt1:.1f} s"},
             "cpu_model": cpu_model()}
+
+
+# --- second CPU baseline: the paper's own mixed-precision loop ---------------------
+def paper_cpu_baseline(m, r, v, eps, seconds, ref):
+    """The paper's force loop (Sec. 3.2-3.3: DP relative positions, SP pair
+    arithmetic, DP acc/pot sums, SP jerk sums, 2 i x 4 j per vector) on the
+    host cores, on the same workload: all cores and one core, plus its
+    accuracy on the sample against the FP64 reference."""
+    from baseline import paper_cpu
+    n = len(m)
+    cores = os.cpu_count() or 1
+    lay = paper_cpu.Layout(m, r, v)
+    perm = ics.permutation(n, 5).astype(np.int32)
+    probe = perm[:max(2 * cores, 64)]
+    t0 = time.perf_counter()
+    lay.force(eps, probe, nthreads=cores)
+    dt = time.perf_counter() - t0
+    k = int(min(n, max(len(probe), seconds / 2 / max(dt, 1e-9) * len(probe))))
+    sample = perm[:k]
+    reps = 0
+    t0 = time.perf_counter()
+    while True:
+        acc, jerk, pot = lay.force(eps, sample, nthreads=cores)
+        reps += 1
+        dt = time.perf_counter() - t0
+        if dt >= 0.5 * seconds:
+            break
+    per_particle_1core = dt * cores / (reps * k)
+    k1 = int(max(16, min(n, 2.0 / max(per_particle_1core, 1e-12))))
+    t0 = time.perf_counter()
+    lay.force(eps, perm[:k1], nthreads=1)
+    dt1 = time.perf_counter() - t0
+    a_ref, j_ref, p_ref = (x[sample] for x in ref)
+    ea = np.linalg.norm(acc - a_ref, axis=1) / np.linalg.norm(a_ref, axis=1)
+    ej = np.linalg.norm(jerk - j_ref, axis=1) / np.linalg.norm(j_ref, axis=1)
+    ep = np.abs(pot - p_ref) / np.abs(p_ref)
+    value = reps * k * n / dt
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "paper_mixed_simd",
+            "openmp": paper_cpu.has_openmp(),
+            "sample": f"mixed-precision loop of Sec. 3.2-3.3 (GCC vector extensions, "
+                      f"no -march) on {k} of the {n} particles against all j, x{reps}, "
+                      f"OpenMP over i pairs, {dt:.1f} s",
+            "gflops_60flop": value * FLOPS_PER_INTERACTION / 1e9,
+            "one_core": {"value": k1 * n / dt1, "unit": UNIT,
+                         "gflops_60flop": k1 * n / dt1 * FLOPS_PER_INTERACTION / 1e9,
+                         "sample": f"{k1} of the {n} particles, 1 thread, {dt1:.1f} s"},
+            "accuracy_vs_fp64": {"particles": k,
+                                 "acc_rel_p50": float(np.median(ea)),
+                                 "acc_rel_max": float(ea.max()),
+                                 "jerk_rel_p50": float(np.median(ej)),
+                                 "jerk_rel_max": float(ej.max()),
+                                 "pot_rel_max": float(ep.max())}}
 
 
 def cpu_model():
@@ -870,9 +931,75 @@ def run_energy_study(args):
                       "outputs": outs, "data": "synthetic", "rows": rows}), flush=True)
 
 
+def run_jerk_study(args):
+    """Sec. 4's accumulation study (Figs. err_snp and err_snp_djerk): the
+    distribution over particles of the relative errors of acc, jerk and pot
+    against the FP64 path, for Plummer models of N = 1K, 4K, 16K and 64K
+    (eps = 4/N, all particles active), with the jerk summed in plain FP32
+    (mixed_spj, the paper's production kernel) and compensated (mixed), plus
+    hybrid and DS for scale.  Also the force-launch time of each mode (CUDA
+    events, n_act = N): the paper found DP jerk sums 20-25 % slower."""
+    import torch
+    from paper_1104_2700_gb300 import build as nb_build
+    from paper_1104_2700_gb300 import nbody
+    nb_build.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    modes = [x for x in args.modes.split(",") if x] if args.modes != "mixed,hybrid,ds,fp64" \
+        else ["mixed_spj", "mixed", "hybrid", "ds"]
+    qs = [0.5, 0.9, 0.99, 0.999, 1.0]
+    rows = []
+    for n in (1024, 4096, 16384, 65536):
+        m, r, v = ics.plummer(n, 11)
+        eps = 4.0 / n
+        idx = np.arange(n, dtype=np.int32)
+        idx_dev = torch.arange(n, dtype=torch.int32, device=dev)
+        z3, t0, dt0 = np.zeros((n, 3)), np.zeros(n), np.full(n, 1.0 / 16)
+
+        def forces(ctx, a, j):
+            ctx.set_state(m, r, v, a, j, t0, dt0, eps, 0.02)
+            ctx.predict(0.0)
+            return ctx.force(idx)
+
+        with nbody.Context("fp64", device=0, stream=stream) as ctx:
+            a_ref, j_ref, p_ref = forces(ctx, z3, z3)
+        row = {"n": n, "eps": eps}
+        for prec in modes:
+            with nbody.Context(prec, device=0, stream=stream) as ctx:
+                a, j, p = forces(ctx, a_ref, j_ref)
+                errs = {"acc": np.linalg.norm(a - a_ref, axis=1) / np.linalg.norm(a_ref, axis=1),
+                        "jerk": np.linalg.norm(j - j_ref, axis=1) / np.linalg.norm(j_ref, axis=1),
+                        "pot": np.abs(p - p_ref) / np.abs(p_ref)}
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                for _ in range(3):
+                    ctx.force(idx_dev)
+                e0.record(stream)
+                reps = max(3, int(2e9 // (n * n)))
+                for _ in range(reps):
+                    ctx.force(idx_dev)
+                e1.record(stream)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+            row[prec] = {k: {f"p{100 * q:g}": float(np.quantile(e, q)) for q in qs}
+                         for k, e in errs.items()}
+            row[prec]["force_ms"] = ms
+            row[prec]["interactions_per_s"] = n * n / (ms * 1e-3)
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    print(json.dumps({"study": "force error distributions, jerk summed in FP32 vs "
+                               "compensated (Sec. 4, Figs. err_snp, err_snp_djerk)",
+                      "workload": "plummer seed 11, eps = 4/N, all particles active, t = 0",
+                      "reference": "FP64 path (every operation in double)",
+                      "data": "synthetic", "rows": rows}), flush=True)
+
+
 def main():
     args = parse_args()
-    if args.energy_study:
+    if args.jerk_study:
+        run_jerk_study(args)
+    elif args.energy_study:
         run_energy_study(args)
     elif args.integrate:
         run_integration(args)

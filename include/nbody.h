@@ -62,8 +62,20 @@ typedef enum nb_status {
  *             its FP32 far-field noise; a particle whose noise would reach
  *             3 % of the crackle scale of its step (eta |j| dt / 12) is
  *             evaluated entirely in DS next time, so the Aarseth timesteps
- *             keep the DS schedule.  The default. */
-typedef enum nb_precision { NB_FP64 = 0, NB_MIXED = 1, NB_DS = 2, NB_HYBRID = 3 } nb_precision;
+ *             keep the DS schedule.  The default.
+ *   NB_MIXED_SPJ  NB_MIXED, except that the jerk is summed in plain FP32
+ *             across each warp's whole run of j (up to all N), as the
+ *             paper's production kernel does (Sec. 4, Fig. err_snp_djerk);
+ *             acceleration and potential are bit-identical to NB_MIXED under
+ *             the same launch shape.  For the accumulation study; its jerk
+ *             error grows with N. */
+typedef enum nb_precision {
+    NB_FP64 = 0,
+    NB_MIXED = 1,
+    NB_DS = 2,
+    NB_HYBRID = 3,
+    NB_MIXED_SPJ = 4
+} nb_precision;
 
 typedef struct nb_config {
     int32_t precision;    /* nb_precision                                       */

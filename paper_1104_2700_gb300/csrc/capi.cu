@@ -543,7 +543,7 @@ nb_status nb_create(const nb_config* cfg, nb_ctx** out)
 {
     if (!cfg || !out) return NB_EINVAL;
     *out = nullptr;
-    if (cfg->precision < NB_FP64 || cfg->precision > NB_HYBRID) return NB_EINVAL;
+    if (cfg->precision < NB_FP64 || cfg->precision > NB_MIXED_SPJ) return NB_EINVAL;
     if (!is_pow2(cfg->dt_max) || !(cfg->dt_min > 0.0) || cfg->dt_min > cfg->dt_max) return NB_EINVAL;
     if (!(cfg->eta_start > 0.0) || !std::isfinite(cfg->G)) return NB_EINVAL;
     nb_ctx* c = new (std::nothrow) nb_ctx;
@@ -570,7 +570,7 @@ nb_status nb_create(const nb_config* cfg, nb_ctx** out)
     // persistent CTAs per SM.  nb_autotune replaces them by measurement.
     for (int v = 0; v < 2; ++v) {
         int it = cfg->i_per_thread;
-        if (it == 0) it = (v == 1 && c->prec == Prec::MIXED) ? 2 : 1;
+        if (it == 0) it = (v == 1 && nb::is_mixed(c->prec)) ? 2 : 1;
         if (!nb::force_variant_exists(c->prec, it)) return bail(NB_EINVAL);
         if (nb::force_setup(c->prec, it) != cudaSuccess) return bail(NB_ECUDA);
         const int occ = nb::force_ctas_per_sm(c->prec, it);
@@ -1043,7 +1043,7 @@ nb_status nb_autotune(nb_ctx* c, nb_tuning* out)
                                static_cast<int32_t>(std::min<int64_t>(16384, n))};
     // candidates: i per thread (two only for MIXED and HYBRID single systems) x CTAs per SM
     std::vector<int> its = {1};
-    if ((c->prec == Prec::MIXED || c->prec == Prec::HYBRID) && !c->ens) its.push_back(2);
+    if ((nb::is_mixed(c->prec) || c->prec == Prec::HYBRID) && !c->ens) its.push_back(2);
     struct Cand {
         int it, cps;
         double us[4];

@@ -147,8 +147,11 @@ struct PolicyFP64 {
 // Mixed precision (Sec. 3.2): r_ij from double-single positions (the
 // double-single difference stands in for the paper's DP subtraction), the
 // remaining pair arithmetic in FP32 with a hardware rsqrt, FP32 partial
-// sums over each tile folded into double-single accumulators.
-template <int IT>
+// sums over each tile folded into double-single accumulators.  With SPJ the
+// jerk instead runs in one plain FP32 sum over the warp's whole range of j,
+// the accumulation of the paper's own kernel (Sec. 4, Fig. err_snp_djerk);
+// the acceleration and potential arithmetic is unchanged.
+template <int IT, bool SPJ = false>
 struct PolicyMixed {
     static constexpr int NARR = 3;
     __host__ __device__ static constexpr int elem(int a) { return a < 2 ? 16 : (a == 2 ? 8 : 0); }
@@ -192,8 +195,14 @@ struct PolicyMixed {
         const float eps2 = static_cast<float>(eps2d);
         float ax[IT], ay[IT], az[IT], jx[IT], jy[IT], jz[IT], ph[IT];
 #pragma unroll
-        for (int q = 0; q < IT; ++q)
-            ax[q] = ay[q] = az[q] = jx[q] = jy[q] = jz[q] = ph[q] = 0.f;
+        for (int q = 0; q < IT; ++q) {
+            ax[q] = ay[q] = az[q] = ph[q] = 0.f;
+            if (SPJ) {
+                jx[q] = ac[q].jx.hi, jy[q] = ac[q].jy.hi, jz[q] = ac[q].jz.hi;
+            } else {
+                jx[q] = jy[q] = jz[q] = 0.f;
+            }
+        }
 #pragma unroll 4
         for (int k = 0; k < TJ; ++k) {
             const float4 A = sA[k];
@@ -227,7 +236,11 @@ struct PolicyMixed {
 #pragma unroll
         for (int q = 0; q < IT; ++q) {
             ac[q].ax.fold(ax[q]), ac[q].ay.fold(ay[q]), ac[q].az.fold(az[q]);
-            ac[q].jx.fold(jx[q]), ac[q].jy.fold(jy[q]), ac[q].jz.fold(jz[q]);
+            if (SPJ) {
+                ac[q].jx.hi = jx[q], ac[q].jy.hi = jy[q], ac[q].jz.hi = jz[q];
+            } else {
+                ac[q].jx.fold(jx[q]), ac[q].jy.fold(jy[q]), ac[q].jz.fold(jz[q]);
+            }
             ac[q].ph.fold(ph[q]);
         }
     }
@@ -969,6 +982,10 @@ const void* kernel_ptr(Prec p, int it, bool ens = false)
         if (it == 1) return kfn<PolicyMixed<1>, 1>(ens);
         if (it == 2) return kfn<PolicyMixed<2>, 2>(ens);
         return nullptr;
+    case Prec::MIXED_SPJ:
+        if (it == 1) return kfn<PolicyMixed<1, true>, 1>(ens);
+        if (it == 2) return kfn<PolicyMixed<2, true>, 2>(ens);
+        return nullptr;
     case Prec::DS:
         if (it == 1) return kfn<PolicyDS<1>, 1>(ens);
         return nullptr;
@@ -986,7 +1003,8 @@ int jlayout_narr(Prec p)
 {
     switch (p) {
     case Prec::FP64: return 2;
-    case Prec::MIXED: return 3;
+    case Prec::MIXED:
+    case Prec::MIXED_SPJ: return 3;
     case Prec::DS: return 4;
     case Prec::HYBRID: return 4;
     }
@@ -997,7 +1015,8 @@ int jlayout_elem_bytes(Prec p, int k)
 {
     switch (p) {
     case Prec::FP64: return k < 2 ? 32 : 0;
-    case Prec::MIXED: return k < 2 ? 16 : (k == 2 ? 8 : 0);
+    case Prec::MIXED:
+    case Prec::MIXED_SPJ: return k < 2 ? 16 : (k == 2 ? 8 : 0);
     case Prec::DS: return k < 4 ? 16 : 0;
     case Prec::HYBRID: return k < 4 ? 16 : 0;
     }
@@ -1008,7 +1027,8 @@ size_t force_smem_bytes(Prec p)
 {
     switch (p) {
     case Prec::FP64: return (size_t)FORCE_WARPS * WarpSmem<PolicyFP64<1>>::BYTES;
-    case Prec::MIXED: return (size_t)FORCE_WARPS * WarpSmem<PolicyMixed<1>>::BYTES;
+    case Prec::MIXED:
+    case Prec::MIXED_SPJ: return (size_t)FORCE_WARPS * WarpSmem<PolicyMixed<1>>::BYTES;
     case Prec::DS: return (size_t)FORCE_WARPS * WarpSmem<PolicyDS<1>>::BYTES;
     case Prec::HYBRID: return (size_t)FORCE_WARPS * WarpSmem<PolicyHybrid<1>>::BYTES;
     }

@@ -168,6 +168,7 @@ cudaError_t predict_launch(const StateDev& st, Prec p, const JLayout& jl, double
         predict_kernel<0><<<blocks, threads, 0, s>>>(st, jl, G, t_bits, t_host, n_act_dev, jsrc, cof);
         break;
     case Prec::MIXED:
+    case Prec::MIXED_SPJ:  // same j layout
         predict_kernel<1><<<blocks, threads, 0, s>>>(st, jl, G, t_bits, t_host, n_act_dev, jsrc, cof);
         break;
     case Prec::DS:

@@ -14,7 +14,12 @@ namespace nb {
 //           into compensated (double-single) accumulators.
 //   DS    - the same pair formulas evaluated in double-single ("float-float")
 //           arithmetic on the FP32 pipes with error-free transforms.
-enum class Prec : int { FP64 = 0, MIXED = 1, DS = 2, HYBRID = 3 };
+//   HYBRID - FP32 far pairs, double-single near pairs.
+//   MIXED_SPJ - MIXED with the jerk summed in plain FP32, the accumulation
+//           the paper's own kernel uses (Sec. 4, Fig. err_snp_djerk).
+enum class Prec : int { FP64 = 0, MIXED = 1, DS = 2, HYBRID = 3, MIXED_SPJ = 4 };
+
+inline bool is_mixed(Prec p) { return p == Prec::MIXED || p == Prec::MIXED_SPJ; }
 
 // Device Hermite state of one context, structure of arrays.  x, v, a, j
 // hold 3*n doubles: component c of particle i at [c*n + i].

@@ -42,13 +42,24 @@ def test_config_defaults(nbody_lib):
 
 
 @pytest.mark.parametrize("field,value", [("dt_max", 0.1), ("dt_max", -1.0),
-                                         ("precision", 7), ("eta_start", 0.0)])
+                                         ("precision", 5), ("precision", -1),
+                                         ("eta_start", 0.0)])
 def test_create_rejects_bad_config_before_touching_the_gpu(nbody_lib, field, value):
     cfg = nbody_lib.nb_config_init()
     setattr(cfg, field, value)
     h = ctypes.c_void_p()
     st = nbody_lib.load().nb_create(ctypes.byref(cfg), ctypes.byref(h))
     assert st == nbody_lib.NB_EINVAL and h.value is None
+
+
+def test_precision_enum_matches_header(nbody_lib):
+    """The binding's precision names carry the values nbody.h declares."""
+    with open(os.path.join(ROOT, "include", "nbody.h")) as fh:
+        text = fh.read()
+    body = re.search(r"typedef enum nb_precision \{(.*?)\} nb_precision;", text, re.S).group(1)
+    declared = {k: int(v) for k, v in re.findall(r"(NB_\w+)\s*=\s*(\d+)", body)}
+    bound = {f"NB_{name.upper()}": val for name, val in nbody_lib.PRECISIONS.items()}
+    assert declared == bound
 
 
 def test_null_context_calls_fail_cleanly(nbody_lib):
