@@ -318,11 +318,11 @@ __global__ void __launch_bounds__(SCHED_THREADS)
 
 // Step 1 in one CTA, for systems small enough that a single SM beats three
 // launches.  Thread k owns particles k + SEL1_THREADS u (u < 32, coalesced).
-// One pass over t, dt gives each thread its smallest next-time key and a
+// One pass over the next-time keys gives each thread its smallest key and a
 // bitmask of the u that reach it; after the block minimum, a thread's block
 // members are that mask if its minimum is the block's.  The ordered
-// compaction then runs on registers only: per u, warp ballots and a scan of
-// the warp counts keep the list in ascending index order.
+// compaction then takes one warp ballot per u and a single block-wide scan
+// of the per-(u, warp) counts, which keeps the list in ascending index order.
 constexpr int SEL1_THREADS = 1024;
 constexpr int64_t SEL1_MAX_N = 32 * SEL1_THREADS;
 
@@ -331,20 +331,29 @@ __global__ void __launch_bounds__(SEL1_THREADS)
                           SchedDev sd)
 {
     __shared__ unsigned long long wmin[SEL1_THREADS / 32];
-    __shared__ int wcnt[2][SEL1_THREADS / 32 + 1];  // exclusive offsets, [32] = total
     __shared__ unsigned long long tkey;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     unsigned long long best = ~0ull;
     uint32_t mask = 0u;
-    for (int u = 0; u < 32; ++u) {
-        const int64_t i = tid + static_cast<int64_t>(SEL1_THREADS) * u;
-        if (i >= n) break;
-        const unsigned long long k = nkey[i];
-        if (k < best) {
-            best = k;
-            mask = 1u << u;
-        } else if (k == best) {
-            mask |= 1u << u;
+    const int tiles = static_cast<int>((n + SEL1_THREADS - 1) / SEL1_THREADS);  // <= 32
+    // keys in batches of 8 independent loads (one memory round trip each);
+    // slots past n read as the largest key and never join the mask
+    for (int u0 = 0; u0 < tiles; u0 += 8) {
+        unsigned long long kk[8];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+            const int64_t i = tid + static_cast<int64_t>(SEL1_THREADS) * (u0 + v);
+            kk[v] = (u0 + v < tiles && i < n) ? __ldcg(nkey + i) : ~0ull;
+        }
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+            const unsigned long long k = kk[v];
+            if (k < best) {
+                best = k;
+                mask = 1u << (u0 + v);
+            } else if (k == best && k != ~0ull) {
+                mask |= 1u << (u0 + v);
+            }
         }
     }
     unsigned long long bmin = best;
@@ -369,32 +378,48 @@ __global__ void __launch_bounds__(SEL1_THREADS)
     }
     __syncthreads();
     if (best != tkey || !(dkey_decode(tkey) <= t_end)) mask = 0u;
-    const int tiles = static_cast<int>((n + SEL1_THREADS - 1) / SEL1_THREADS);
-    int base = 0;
+    // Ordered compaction: slot of (tile u, warp w, lane) = members before
+    // tile u + members of tile u in warps before w + lanes before it.  One
+    // ballot per tile (lane u of each warp keeps its warp's ballot of tile
+    // u), the warp counts in [u][w] order, one block-wide exclusive scan.
+    __shared__ int cnt[32 * (SEL1_THREADS / 32)];
+    __shared__ int wtot[SEL1_THREADS / 32];
+    uint32_t bal = 0u;
     for (int u = 0; u < tiles; ++u) {
-        const bool act = (mask >> u) & 1u;
-        const unsigned m = __ballot_sync(0xffffffffu, act);
-        int* wc = wcnt[u & 1];
-        if (lane == 0) wc[wid] = __popc(m);
-        __syncthreads();
-        if (wid == 0) {  // exclusive scan of the warp counts
-            const int c = wc[lane];
-            int x = c;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
-            }
-            wc[lane] = x - c;
-            if (lane == 31) wc[32] = x;
-        }
-        __syncthreads();
-        if (act)
-            sd.idx[base + wc[wid] + __popc(m & ((1u << lane) - 1u))] =
-                static_cast<int32_t>(tid + SEL1_THREADS * u);
-        base += wc[32];
+        const uint32_t b = __ballot_sync(0xffffffffu, (mask >> u) & 1u);
+        if (lane == u) bal = b;
+        if (lane == 0) cnt[u * 32 + wid] = __popc(b);
     }
-    if (tid == 0) *sd.n_act = base;
+    __syncthreads();
+    const int mine = tid < tiles * 32 ? cnt[tid] : 0;  // entry tid = (u = wid, w = lane)
+    int x = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wtot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        const int c = wtot[lane];
+        int y = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int z = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += z;
+        }
+        wtot[lane] = y - c;  // exclusive
+        if (lane == 31) *sd.n_act = y;
+    }
+    __syncthreads();
+    if (tid < tiles * 32) cnt[tid] = wtot[wid] + x - mine;
+    __syncthreads();
+    for (int u = 0; u < tiles; ++u) {
+        const uint32_t b = __shfl_sync(0xffffffffu, bal, u);
+        if ((mask >> u) & 1u)
+            sd.idx[cnt[u * 32 + wid] + __popc(b & ((1u << lane) - 1u))] =
+                static_cast<int32_t>(tid + SEL1_THREADS * u);
+    }
 }
 
 cudaError_t select_launch(const StateDev& st, const SchedDev& sd, double t_end, cudaStream_t s)
@@ -589,6 +614,54 @@ __device__ __forceinline__ double norm3_rn(double x, double y, double z)
     return __dsqrt_rn(DADD(DADD(DMUL(x, x), DMUL(y, y)), DMUL(z, z)));
 }
 
+// Eq. timestep for the power-of-two rule only.  The rule compares the
+// candidate with powers of two alone, so all it needs is the k with
+// 2^k <= eta sqrt((|a||s| + |j|^2) / (|j||c| + |s|^2)) < 2^(k+1).  That is
+// taken in FP32: each norm after scaling its vector by a power of two
+// (|v| = nrm 2^E, the vector's largest component then in [0.5, 1)), the two
+// sums after aligning their terms' exponents.  About fifteen FP32 roundings
+// leave it within ~1e-6 of the FP64 value, so k is certain unless the value
+// lies within 1e-5 of a power of two; then, or when a vector is zero, tiny or
+// not finite, the function declines and the caller evaluates the formula in
+// FP64 as written.  Either way the timestep chosen is the oracle's.
+__device__ __forceinline__ bool norm3_scaled(const double (&v)[3], float& nrm, int& E)
+{
+    const float f0 = __double2float_rn(v[0]);
+    const float f1 = __double2float_rn(v[1]);
+    const float f2 = __double2float_rn(v[2]);
+    const float mx = fmaxf(fabsf(f0), fmaxf(fabsf(f1), fabsf(f2)));
+    if (!(mx >= 1e-30f && mx <= 1e30f)) return false;  // NaN fails too
+    frexpf(mx, &E);
+    const float x0 = ldexpf(f0, -E), x1 = ldexpf(f1, -E), x2 = ldexpf(f2, -E);
+    nrm = sqrtf(fmaf(x0, x0, fmaf(x1, x1, x2 * x2)));
+    return true;
+}
+
+__device__ __forceinline__ bool aarseth_interval(const double (&a)[3], const double (&j)[3],
+                                                 const double (&s)[3], const double (&c)[3],
+                                                 double eta, int& k)
+{
+    float nA, nJ, nS, nC;
+    int eA, eJ, eS, eC;
+    if (!norm3_scaled(a, nA, eA) || !norm3_scaled(j, nJ, eJ) || !norm3_scaled(s, nS, eS) ||
+        !norm3_scaled(c, nC, eC))
+        return false;
+    // numerator 2^en (..) and denominator 2^ed (..), each a sum of two
+    // positive terms
+    const int n1 = eA + eS, n2 = 2 * eJ, d1 = eJ + eC, d2 = 2 * eS;
+    const int en = n1 > n2 ? n1 : n2, ed = d1 > d2 ? d1 : d2;
+    const float num = ldexpf(nA * nS, n1 - en) + ldexpf(nJ * nJ, n2 - en);
+    const float den = ldexpf(nJ * nC, d1 - ed) + ldexpf(nS * nS, d2 - ed);
+    int ex = en - ed;
+    float r = num / den;
+    if (ex & 1) r *= 2.f, ex -= 1;  // an even exponent halves exactly
+    int e;
+    const float m = frexpf(static_cast<float>(eta) * sqrtf(r), &e);  // m in [0.5, 1)
+    if (!(m > 0.500005f && m < 0.99999f)) return false;
+    k = e - 1 + ex / 2;
+    return k > -1000 && k < 1000;
+}
+
 __device__ __forceinline__ double pow2_floor(double x)
 {
     int e;
@@ -689,19 +762,28 @@ __global__ void correct_kernel(const StateDev st, const CorrectArgs c)
     double sn[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) sn[d] = DADD(s0[d], DMUL(c0[d], h));
-    const double A = norm3_rn(a1[0], a1[1], a1[2]);
-    const double J = norm3_rn(j1[0], j1[1], j1[2]);
-    const double S = norm3_rn(sn[0], sn[1], sn[2]);
-    const double C = norm3_rn(c0[0], c0[1], c0[2]);
-    // a zero denominator (a particle that feels nothing) sets no constraint
-    const double den = DADD(DMUL(J, C), DMUL(S, S));
-    const double dta = den == 0.0 ? CUDART_INF
-                                  : DMUL(c.eta, __dsqrt_rn(DDIV(DADD(DMUL(A, S), DMUL(J, J)), den)));
-    if (isnan(dta)) {
-        atomicOr(c.status, ST_NONFINITE);
-        return;
+    // cand: min(dt_Aarseth, dt_max), or a power of two in the same
+    // power-of-two interval, which is all the rule below looks at
+    double cand;
+    int kq;
+    const int kmax = static_cast<int>((__double_as_longlong(c.dt_max) >> 52) & 0x7ff) - 1023;
+    if (aarseth_interval(a1, j1, sn, c0, c.eta, kq)) {
+        cand = kq >= kmax ? c.dt_max : __longlong_as_double(static_cast<long long>(kq + 1023) << 52);
+    } else {
+        const double A = norm3_rn(a1[0], a1[1], a1[2]);
+        const double J = norm3_rn(j1[0], j1[1], j1[2]);
+        const double S = norm3_rn(sn[0], sn[1], sn[2]);
+        const double C = norm3_rn(c0[0], c0[1], c0[2]);
+        // a zero denominator (a particle that feels nothing) sets no constraint
+        const double den = DADD(DMUL(J, C), DMUL(S, S));
+        const double dta =
+            den == 0.0 ? CUDART_INF : DMUL(c.eta, __dsqrt_rn(DDIV(DADD(DMUL(A, S), DMUL(J, J)), den)));
+        if (isnan(dta)) {
+            atomicOr(c.status, ST_NONFINITE);
+            return;
+        }
+        cand = dta < c.dt_max ? dta : c.dt_max;
     }
-    const double cand = dta < c.dt_max ? dta : c.dt_max;
     double dt_new = h;
     // t_next a multiple of 2h (h a power of two, so t_next / 2h is exact)
     const double k2h = DMUL(tn, recip_pow2(DMUL(2.0, h)));
@@ -934,26 +1016,30 @@ cudaError_t soa_to_aos_launch(const double* soa, double* aos, int64_t n, cudaStr
 // 8-byte slot for the two bounds.
 __global__ void snapshot_kernel(StateDev st, double* __restrict__ buf, int to_buf)
 {
+    // row blockIdx.y copies one array; the rows' offsets in buf follow the
+    // order m, x, v, a, j, t, dt, hq, nkey
     const int64_t n = st.n;
-    unsigned long long* arr[9] = {
-        reinterpret_cast<unsigned long long*>(st.m), reinterpret_cast<unsigned long long*>(st.x),
-        reinterpret_cast<unsigned long long*>(st.v), reinterpret_cast<unsigned long long*>(st.a),
-        reinterpret_cast<unsigned long long*>(st.j), reinterpret_cast<unsigned long long*>(st.t),
-        reinterpret_cast<unsigned long long*>(st.dt), reinterpret_cast<unsigned long long*>(st.hq),
-        st.nkey};
-    const int64_t len[9] = {n, 3 * n, 3 * n, 3 * n, 3 * n, n, n, n, n};
-    const int64_t total = 17 * n;
-    unsigned long long* w = reinterpret_cast<unsigned long long*>(buf);
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t off = e;
-        int k = 0;
-        while (off >= len[k]) off -= len[k++];
-        if (to_buf) w[e] = arr[k][off];
-        else arr[k][off] = w[e];
+    unsigned long long* arr;
+    int64_t len = n, off;
+    switch (blockIdx.y) {
+    case 0: arr = reinterpret_cast<unsigned long long*>(st.m), off = 0; break;
+    case 1: arr = reinterpret_cast<unsigned long long*>(st.x), len = 3 * n, off = n; break;
+    case 2: arr = reinterpret_cast<unsigned long long*>(st.v), len = 3 * n, off = 4 * n; break;
+    case 3: arr = reinterpret_cast<unsigned long long*>(st.a), len = 3 * n, off = 7 * n; break;
+    case 4: arr = reinterpret_cast<unsigned long long*>(st.j), len = 3 * n, off = 10 * n; break;
+    case 5: arr = reinterpret_cast<unsigned long long*>(st.t), off = 13 * n; break;
+    case 6: arr = reinterpret_cast<unsigned long long*>(st.dt), off = 14 * n; break;
+    case 7: arr = reinterpret_cast<unsigned long long*>(st.hq), off = 15 * n; break;
+    default: arr = st.nkey, off = 16 * n; break;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        uint32_t* b = reinterpret_cast<uint32_t*>(w + total);
+    unsigned long long* w = reinterpret_cast<unsigned long long*>(buf) + off;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        if (to_buf) w[e] = arr[e];
+        else arr[e] = w[e];
+    }
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+        uint32_t* b = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned long long*>(buf) + 17 * n);
         if (to_buf) b[0] = st.bound[0], b[1] = st.bound[1];
         else st.bound[0] = b[0], st.bound[1] = b[1];
     }
@@ -963,9 +1049,9 @@ cudaError_t snapshot_launch(const StateDev& st, double* buf, bool to_buf, cudaSt
 {
     if (st.n <= 0) return cudaSuccess;
     const int threads = 256;
-    const int64_t want = (17 * st.n + threads - 1) / threads;
-    const unsigned blocks = static_cast<unsigned>(want < 2048 ? want : 2048);
-    snapshot_kernel<<<blocks, threads, 0, s>>>(st, buf, to_buf ? 1 : 0);
+    const int64_t want = (3 * st.n + threads - 1) / threads;  // the longest row
+    const unsigned bx = static_cast<unsigned>(want < 512 ? want : 512);
+    snapshot_kernel<<<dim3(bx, 9), threads, 0, s>>>(st, buf, to_buf ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -213,6 +213,37 @@ def test_correct_bit_exact_against_oracle(gpu, orc):
     assert np.array_equal(out["r"][rest], r[rest]) and np.array_equal(out["t"][rest], t[rest])
 
 
+@pytest.mark.parametrize("rel", [0.0, 2.0 ** -45, -(2.0 ** -45), 1e-7, -1e-7, 4e-6, -4e-6,
+                                 3e-5, -3e-5, 0.3])
+def test_correct_timestep_at_power_of_two_boundaries(gpu, orc, rel):
+    """eta is set so that one particle's Eq. timestep value lands on, or a
+    hair to either side of, its current step h (a power of two): the
+    power-of-two rule must pick the oracle's step on both sides, whichever
+    precision the kernel evaluates the formula in."""
+    n, T = 400, 0.5
+    m, r, v, a, j, t, dt, due = _random_block_state(n, 21, T)
+    idx = np.nonzero(due)[0].astype(np.int32)
+    rng = np.random.default_rng(22)
+    a1 = a[idx] + rng.normal(0, 1e-3, (len(idx), 3))
+    j1 = j[idx] + rng.normal(0, 1e-2, (len(idx), 3))
+    rp, vp = orc.predict(r[idx], v[idx], a[idx], j[idx], t[idx], T)
+    sc = []
+    for k, i in enumerate(idx):
+        _, _, s0, c0 = orc.hermite_correct(rp[k], vp[k], a[i], j[i], a1[k], j1[k], dt[i])
+        sc.append((s0 + c0 * dt[i], c0))
+    i0 = idx[0]
+    unit = orc.aarseth_dt(1.0, a1[0], j1[0], *sc[0])
+    eta = dt[i0] / unit * (1.0 + rel)
+    with gpu.Context("fp64", dt_max=1.0 / 16) as ctx:
+        ctx.set_state(m, r, v, a, j, t, dt, eps=0.01, eta=eta)
+        ctx.correct(T, idx, a1, j1)
+        out = ctx.get_state()
+    for k, i in enumerate(idx):
+        dta = orc.aarseth_dt(eta, a1[k], j1[k], *sc[k])
+        _, dtn = orc.quantize_dt(dt[i], dta, T, 1.0 / 16)
+        assert out["dt"][i] == dtn, (k, dta / dt[i])
+
+
 def test_correct_rejects_particle_not_due(gpu):
     n, T = 100, 0.5
     m, r, v, a, j, t, dt, due = _random_block_state(n, 7, T)
