@@ -662,106 +662,15 @@ __device__ __forceinline__ bool aarseth_interval(const double (&a)[3], const dou
     return k > -1000 && k < 1000;
 }
 
-__device__ __forceinline__ double pow2_floor(double x)
+// Step 8 for one particle: Eq. timestep at the new time (a1, j1, the snap
+// carried to t_next, the crackle), then the power-of-two rule of the
+// hierarchical scheme.  Returns false (and flags the status) when the
+// formula is not a number.
+__device__ __forceinline__ bool next_timestep(const double (&a1)[3], const double (&j1)[3],
+                                              const double (&sn)[3], const double (&c0)[3],
+                                              double h, double tn, const CorrectArgs& c,
+                                              double& dt_new)
 {
-    int e;
-    frexp(x, &e);
-    return ldexp(1.0, e - 1);
-}
-
-__global__ void correct_kernel(const StateDev st, const CorrectArgs c)
-{
-    const int n_act = *c.n_act_dev;
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k == 0 && n_act > 0 && c.step_counter) atomicAdd(c.step_counter, 1ull);
-    if (c.inter_counter) {
-        // interactions: n_act * n for one system; each active particle adds
-        // its own system's size in an ensemble (summed per warp)
-        if (!c.cluster_of) {
-            if (k == 0 && n_act > 0)
-                atomicAdd(c.inter_counter, static_cast<unsigned long long>(n_act) *
-                                               static_cast<unsigned long long>(st.n));
-        } else {
-            unsigned long long mine = 0;
-            if (k < n_act) {
-                const int64_t i = c.idx[k];
-                if (i >= 0 && i < st.n) {
-                    const int cc = c.cluster_of[i];
-                    mine = static_cast<unsigned long long>(c.cl_off[cc + 1] - c.cl_off[cc]);
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
-            if ((threadIdx.x & 31) == 0 && mine) atomicAdd(c.inter_counter, mine);
-        }
-    }
-    if (k >= n_act) return;
-    const int64_t n = st.n;
-    const int64_t i = c.idx[k];
-    if (i < 0 || i >= n) {
-        atomicOr(c.status, ST_BADINDEX);
-        return;
-    }
-    const double tn = dkey_decode(c.t_bits[c.cluster_of ? c.cluster_of[i] : 0]);
-    const double h = st.dt[i];
-    if (DADD(st.t[i], h) != tn) {
-        atomicOr(c.status, ST_NOTDUE);
-        return;
-    }
-    const double dtp = DSUB(tn, st.t[i]);
-    const double p2 = DMUL(dtp, dtp), p3 = DMUL(p2, dtp);
-    const double h2 = DMUL(h, h), h3 = DMUL(h2, h), h4 = DMUL(h3, h), h5 = DMUL(h4, h);
-    // h is a power of two, so dividing by h^2 or h^3 (and by 2) is an exact
-    // scaling: multiplying by the exact reciprocal gives the quotient's bits.
-    const double ih2 = recip_pow2(h2), ih3 = recip_pow2(h3);  // exact
-    double a1[3], j1[3], s0[3], c0[3], xmax = 0.0, vmax = 0.0;
-    bool finite = true;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        a1[d] = c.acc1[3 * k + d];
-        j1[d] = c.jerk1[3 * k + d];
-        finite = finite && isfinite(a1[d]) && isfinite(j1[d]);
-    }
-    if (!finite) {
-        atomicOr(c.status, ST_NONFINITE);
-        return;
-    }
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const int64_t q = d * n + i;
-        const double x0 = st.x[q], v0 = st.v[q], a0 = st.a[q], j0 = st.j[q];
-        // Eqs. xpred, vpred for the i particle (step 2).
-        const double rp = DADD(DADD(DADD(x0, DMUL(v0, dtp)), DMUL(DMUL(a0, 0.5), p2)),
-                               DMUL(div_const(j0, 6.0, 1.0 / 6.0), p3));
-        const double vp = DADD(DADD(v0, DMUL(a0, dtp)), DMUL(DMUL(j0, 0.5), p2));
-        // Step 5: snap and crackle from the Hermite interpolation.
-        const double da = DSUB(a0, a1[d]);
-        s0[d] = DMUL(DMUL(2.0, DSUB(DMUL(-3.0, da), DMUL(DADD(DMUL(2.0, j0), j1[d]), h))), ih2);
-        c0[d] = DMUL(DMUL(6.0, DADD(DMUL(2.0, da), DMUL(DADD(j0, j1[d]), h))), ih3);
-        // Step 6: corrector.
-        const double r1 = DADD(DADD(rp, div_const(DMUL(s0[d], h4), 24.0, 1.0 / 24.0)),
-                               div_const(DMUL(c0[d], h5), 120.0, 1.0 / 120.0));
-        const double v1 = DADD(DADD(vp, div_const(DMUL(s0[d], h3), 6.0, 1.0 / 6.0)),
-                               div_const(DMUL(c0[d], h4), 24.0, 1.0 / 24.0));
-        // Step 7: a0 <- a1, j0 <- j1.
-        st.x[q] = r1;
-        st.v[q] = v1;
-        st.a[q] = a1[d];
-        st.j[q] = j1[d];
-        xmax = fmax(xmax, fabs(r1));
-        vmax = fmax(vmax, fabs(v1));
-    }
-    st.t[i] = tn;
-    // raise the layout bounds if this particle moved past them (rare)
-    const uint32_t xb = __float_as_uint(__double2float_ru(xmax));
-    const uint32_t vb = __float_as_uint(__double2float_ru(vmax));
-    if (xb > st.bound[0]) atomicMax(&st.bound[0], xb);
-    if (vb > st.bound[1]) atomicMax(&st.bound[1], vb);
-    // Step 8: Eq. timestep at the new time (a1, j1, snap carried to t_next,
-    // crackle), then the power-of-two rule of the hierarchical scheme.
-    double sn[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) sn[d] = DADD(s0[d], DMUL(c0[d], h));
     // cand: min(dt_Aarseth, dt_max), or a power of two in the same
     // power-of-two interval, which is all the rule below looks at
     double cand;
@@ -780,11 +689,11 @@ __global__ void correct_kernel(const StateDev st, const CorrectArgs c)
             den == 0.0 ? CUDART_INF : DMUL(c.eta, __dsqrt_rn(DDIV(DADD(DMUL(A, S), DMUL(J, J)), den)));
         if (isnan(dta)) {
             atomicOr(c.status, ST_NONFINITE);
-            return;
+            return false;
         }
         cand = dta < c.dt_max ? dta : c.dt_max;
     }
-    double dt_new = h;
+    dt_new = h;
     // t_next a multiple of 2h (h a power of two, so t_next / 2h is exact)
     const double k2h = DMUL(tn, recip_pow2(DMUL(2.0, h)));
     if (cand >= DMUL(2.0, h) && k2h == rint(k2h)) {
@@ -794,17 +703,140 @@ __global__ void correct_kernel(const StateDev st, const CorrectArgs c)
     } else {
         while (dt_new > cand && dt_new >= c.dt_min) dt_new = DMUL(dt_new, 0.5);
     }
-    st.dt[i] = dt_new;
-    st.nkey[i] = dkey(DADD(tn, dt_new));
-    if (dt_new < c.dt_min) atomicOr(c.status, ST_DTMIN);
+    return true;
+}
+
+__device__ __forceinline__ double pow2_floor(double x)
+{
+    int e;
+    frexp(x, &e);
+    return ldexp(1.0, e - 1);
+}
+
+// GB300's FP64 unit spends ~68 cycles on each warp instruction whatever
+// its number of active lanes, and a warp has one in flight, so a block's
+// latency is the FP64 instruction count of its busiest warp.  A block of
+// three warps therefore takes 32 active particles: warp d does component d
+// of the prediction, snap, crackle and corrector (the bulk of the FP64
+// work), and warp 0 then takes each particle's timestep from the three
+// components left in shared memory.
+constexpr int CORR_P = 32;  // particles per block, one per lane
+
+__global__ void __launch_bounds__(3 * CORR_P) correct_kernel(const StateDev st, const CorrectArgs c)
+{
+    __shared__ double sv[4][3][CORR_P];  // a1, j1, snap at t_next, crackle
+    __shared__ int fin[3][CORR_P];
+    const int d = threadIdx.x / CORR_P, lane = threadIdx.x % CORR_P;
+    const int n_act = *c.n_act_dev;
+    const int64_t n = st.n;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && n_act > 0) {
+        if (c.step_counter) atomicAdd(c.step_counter, 1ull);
+        // interactions: n_act * n for one system (an ensemble adds, per
+        // active particle, its own system's size below)
+        if (c.inter_counter && !c.cluster_of)
+            atomicAdd(c.inter_counter, static_cast<unsigned long long>(n_act) *
+                                           static_cast<unsigned long long>(n));
+    }
+    for (int64_t g = (int64_t)blockIdx.x * CORR_P; g < n_act; g += (int64_t)gridDim.x * CORR_P) {
+        const int64_t k = g + lane;
+        const bool act = k < n_act;
+        const int64_t i = act ? c.idx[k] : -1;
+        const bool inr = act && i >= 0 && i < n;
+        if (d == 0) {
+            if (act && !inr) atomicOr(c.status, ST_BADINDEX);
+            if (c.inter_counter && c.cluster_of) {
+                unsigned long long mine = 0;
+                if (inr) {
+                    const int cc = c.cluster_of[i];
+                    mine = static_cast<unsigned long long>(c.cl_off[cc + 1] - c.cl_off[cc]);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+                if (lane == 0 && mine) atomicAdd(c.inter_counter, mine);
+            }
+        }
+        double tn = 0.0, h = 0.0, t0 = 0.0, a1 = 0.0, j1 = 0.0;
+        if (inr) {
+            tn = dkey_decode(c.t_bits[c.cluster_of ? c.cluster_of[i] : 0]);
+            h = st.dt[i];
+            t0 = st.t[i];
+            a1 = c.acc1[3 * k + d];
+            j1 = c.jerk1[3 * k + d];
+        }
+        fin[d][lane] = isfinite(a1) && isfinite(j1);
+        __syncthreads();
+        const bool finite = fin[0][lane] && fin[1][lane] && fin[2][lane];
+        const bool due = inr && DADD(t0, h) == tn;
+        if (d == 0 && inr) {
+            if (!due) atomicOr(c.status, ST_NOTDUE);
+            else if (!finite) atomicOr(c.status, ST_NONFINITE);
+        }
+        const bool work = due && finite;
+        if (work) {
+            const double dtp = DSUB(tn, t0);
+            const double p2 = DMUL(dtp, dtp), p3 = DMUL(p2, dtp);
+            const double h2 = DMUL(h, h), h3 = DMUL(h2, h), h4 = DMUL(h3, h), h5 = DMUL(h4, h);
+            // h is a power of two, so dividing by h^2 or h^3 (and by 2) is an
+            // exact scaling: multiplying by the exact reciprocal gives the
+            // quotient's bits.
+            const double ih2 = recip_pow2(h2), ih3 = recip_pow2(h3);  // exact
+            const int64_t q = d * n + i;
+            const double x0 = st.x[q], v0 = st.v[q], a0 = st.a[q], j0 = st.j[q];
+            // Eqs. xpred, vpred for the i particle (step 2).
+            const double rp = DADD(DADD(DADD(x0, DMUL(v0, dtp)), DMUL(DMUL(a0, 0.5), p2)),
+                                   DMUL(div_const(j0, 6.0, 1.0 / 6.0), p3));
+            const double vp = DADD(DADD(v0, DMUL(a0, dtp)), DMUL(DMUL(j0, 0.5), p2));
+            // Step 5: snap and crackle from the Hermite interpolation.
+            const double da = DSUB(a0, a1);
+            const double s0 = DMUL(DMUL(2.0, DSUB(DMUL(-3.0, da), DMUL(DADD(DMUL(2.0, j0), j1), h))), ih2);
+            const double c0 = DMUL(DMUL(6.0, DADD(DMUL(2.0, da), DMUL(DADD(j0, j1), h))), ih3);
+            // Step 6: corrector.
+            const double r1 = DADD(DADD(rp, div_const(DMUL(s0, h4), 24.0, 1.0 / 24.0)),
+                                   div_const(DMUL(c0, h5), 120.0, 1.0 / 120.0));
+            const double v1 = DADD(DADD(vp, div_const(DMUL(s0, h3), 6.0, 1.0 / 6.0)),
+                                   div_const(DMUL(c0, h4), 24.0, 1.0 / 24.0));
+            // Step 7: a0 <- a1, j0 <- j1.
+            st.x[q] = r1;
+            st.v[q] = v1;
+            st.a[q] = a1;
+            st.j[q] = j1;
+            // raise the layout bounds if this particle moved past them (rare)
+            const uint32_t xb = __float_as_uint(__double2float_ru(fabs(r1)));
+            const uint32_t vb = __float_as_uint(__double2float_ru(fabs(v1)));
+            if (xb > st.bound[0]) atomicMax(&st.bound[0], xb);
+            if (vb > st.bound[1]) atomicMax(&st.bound[1], vb);
+            sv[0][d][lane] = a1;
+            sv[1][d][lane] = j1;
+            sv[2][d][lane] = DADD(s0, DMUL(c0, h));  // snap carried to t_next
+            sv[3][d][lane] = c0;
+        }
+        __syncthreads();
+        if (d == 0 && work) {
+            st.t[i] = tn;
+            double a3[3], j3[3], s3[3], c3[3];
+#pragma unroll
+            for (int e = 0; e < 3; ++e)
+                a3[e] = sv[0][e][lane], j3[e] = sv[1][e][lane], s3[e] = sv[2][e][lane],
+                c3[e] = sv[3][e][lane];
+            double dt_new;
+            if (next_timestep(a3, j3, s3, c3, h, tn, c, dt_new)) {
+                st.dt[i] = dt_new;
+                st.nkey[i] = dkey(DADD(tn, dt_new));
+                if (dt_new < c.dt_min) atomicOr(c.status, ST_DTMIN);
+            }
+        }
+        // fin and sv are written again only after the next iteration's
+        // first barrier has seen warp 0 through its reads
+    }
 }
 
 cudaError_t correct_launch(const StateDev& st, const CorrectArgs& c, cudaStream_t s)
 {
     if (st.n <= 0) return cudaSuccess;
-    const int threads = 128;
-    const unsigned blocks = static_cast<unsigned>((st.n + threads - 1) / threads);
-    correct_kernel<<<blocks, threads, 0, s>>>(st, c);
+    // enough blocks for every particle to be active; each loops over groups
+    const int64_t want = (st.n + CORR_P - 1) / CORR_P;
+    const unsigned blocks = static_cast<unsigned>(want < 2432 ? want : 2432);
+    correct_kernel<<<blocks, 3 * CORR_P, 0, s>>>(st, c);
     return cudaGetLastError();
 }
 
