@@ -71,6 +71,7 @@ struct ForceParams {
 // Plain FP64: the baseline path.
 template <int IT>
 struct PolicyFP64 {
+    static constexpr bool GUARDED = false;
     static constexpr int NARR = 2;
     __host__ __device__ static constexpr int elem(int a) { return a < 2 ? 32 : 0; }
     static constexpr int TILE_BYTES = TJ * 64;
@@ -153,6 +154,7 @@ struct PolicyFP64 {
 // the acceleration and potential arithmetic is unchanged.
 template <int IT, bool SPJ = false>
 struct PolicyMixed {
+    static constexpr bool GUARDED = false;
     static constexpr int NARR = 3;
     __host__ __device__ static constexpr int elem(int a) { return a < 2 ? 16 : (a == 2 ? 8 : 0); }
     static constexpr int TILE_BYTES = TJ * 40;
@@ -400,6 +402,7 @@ __device__ __forceinline__ void ds_pair(const float4& A, const float4& B, const 
 
 template <int IT>
 struct PolicyDS {
+    static constexpr bool GUARDED = false;
     static constexpr int NARR = 4;
     __host__ __device__ static constexpr int elem(int a) { return a < 4 ? 16 : 0; }
     static constexpr int TILE_BYTES = TJ * 64;
@@ -488,6 +491,7 @@ struct HybridAcc : DSAccs {
 
 template <int IT>
 struct PolicyHybrid {
+    static constexpr bool GUARDED = true;
     static constexpr int NARR = 4;
     __host__ __device__ static constexpr int elem(int a) { return a < 4 ? 16 : 0; }
     static constexpr int TILE_BYTES = TJ * 64;
@@ -548,7 +552,12 @@ struct PolicyHybrid {
         if (s.particle >= 0) f.st_hq[s.particle] = s.all_near ? -v[7] : v[7];
     }
 
-    template <bool MASK>
+    __device__ static bool guarded(const I& s) { return s.all_near; }
+
+    // GUARD: some lane of the warp has the integration guard on (rare); the
+    // other instantiation assumes none has, so near is the natural test and
+    // the noise estimate reuses the far-pair factor m / r.
+    template <bool MASK, bool GUARD>
     __device__ static void tile(const unsigned char* buf, int64_t j0, const double eps2d,
                                 I (&is)[IT], Acc (&ac)[IT])
     {
@@ -593,20 +602,27 @@ struct PolicyHybrid {
                     const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, e2h)));
                     const bool self = MASK && (j0 + k == s.p);
                     const bool nat = r2 < fmaxf(A.w * is[q].ca, C.w * is[q].cj);
-                    const bool near = (nat || is[q].all_near) && !self;
-                    // rsqrt refined once: y (1 + h/2), h = 1 - r^2 y^2
+                    const bool near = (nat || (GUARD && is[q].all_near)) && !self;
+                    // rsqrt refined once: y (1 + h/2) with the residual
+                    // h = 1 - r^2 y^2 taken from the rounded y^2 (an error of
+                    // at most an ulp of h, unbiased)
                     float y = rsqrtf(r2);
-                    const float yy = y * y;
-                    float h = fmaf(-r2, yy, 1.f);
-                    h = fmaf(-r2, fmaf(y, y, -yy), h);
+                    const float h = fmaf(-r2, y * y, 1.f);
                     y = fmaf(0.5f * y, h, y);
                     if (self) y = 0.f;  // r = 0 when eps = 0: keep inf out of every term
                     const float mr0 = A.w * y;
-                    // noise estimate over the pairs the natural test calls far
-                    bs[q] += (nat || self) ? 0.f : mr0 * y;
-                    // near pairs (and the self pair) add nothing here: every
-                    // FP32 term below carries the factor m / r
-                    const float mr = (self || near) ? 0.f : mr0;
+                    // near pairs (and the self pair, whose y is 0) add nothing
+                    // here: every FP32 term below carries the factor m / r.
+                    // The noise estimate sums m / r^2 over the pairs the
+                    // natural test calls far.
+                    float mr;
+                    if (GUARD) {
+                        bs[q] += (nat || self) ? 0.f : mr0 * y;
+                        mr = (self || near) ? 0.f : mr0;
+                    } else {
+                        mr = nat ? 0.f : mr0;
+                        bs[q] = fmaf(mr, y, bs[q]);
+                    }
                     const float ri2 = y * y;
                     const float g = mr * ri2;
                     const float rv = fmaf(dx, dvx, fmaf(dy, dvy, dz * dvz));
@@ -817,6 +833,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
     typename K::I is[IT];
     typename K::Acc ac[IT];
     bool fresh = true;
+    bool guard_any = false;  // some lane of this group has the hybrid guard on
 
     for (int64_t t = t0; t < t1; ++t) {
         const int64_t k = t - t0;
@@ -844,6 +861,12 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
                 K::load_i(f, p, particle, is[q]);
                 ac[q].zero();
             }
+            if constexpr (K::GUARDED) {
+                bool gq = false;
+#pragma unroll
+                for (int q = 0; q < IT; ++q) gq |= K::guarded(is[q]);
+                guard_any = __any_sync(0xffffffffu, gq);
+            }
         }
         const bool ok = mbar_wait_bounded(&bars[s], parity, f.wait_limit);
         if (!__all_sync(0xffffffffu, ok)) {
@@ -865,10 +888,19 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
         for (int q = 0; q < IT; ++q)
             self_here |= (is[q].p >= j0 && is[q].p < j0 + TJ);
         const unsigned char* buf = ring + s * K::TILE_BYTES;
-        if (__any_sync(0xffffffffu, self_here))
-            K::template tile<true>(buf, j0, gi.eps2, is, ac);
-        else
-            K::template tile<false>(buf, j0, gi.eps2, is, ac);
+        const bool mask_self = __any_sync(0xffffffffu, self_here);
+        if constexpr (K::GUARDED) {
+            if (guard_any) {
+                if (mask_self) K::template tile<true, true>(buf, j0, gi.eps2, is, ac);
+                else K::template tile<false, true>(buf, j0, gi.eps2, is, ac);
+            } else {
+                if (mask_self) K::template tile<true, false>(buf, j0, gi.eps2, is, ac);
+                else K::template tile<false, false>(buf, j0, gi.eps2, is, ac);
+            }
+        } else {
+            if (mask_self) K::template tile<true>(buf, j0, gi.eps2, is, ac);
+            else K::template tile<false>(buf, j0, gi.eps2, is, ac);
+        }
         __syncwarp();
         if (t + K::STAGES < t1) {
             if (lane == 0) fence_proxy_async_smem();
