@@ -26,13 +26,12 @@ __device__ __forceinline__ double dkey_decode(unsigned long long k)
 
 // ---------------------------------------------------------------------------
 // Steps 2-3: Taylor predictor (Eqs. xpred, vpred) for every j particle, in
-// Horner form with FMA, written straight into the force kernel's j layout.
+// Horner form with FMA, written straight into the FP64 force kernel's j layout.
 // ---------------------------------------------------------------------------
-template <int PREC>
-__global__ void predict_kernel(const StateDev st, const JLayout jl, const double G,
-                               const unsigned long long* t_bits, const double t_host,
-                               const int32_t* n_act_dev, const int32_t* jsrc,
-                               const int32_t* cluster_of)
+__global__ void predict_fp64_kernel(const StateDev st, const JLayout jl, const double G,
+                                    const unsigned long long* t_bits, const double t_host,
+                                    const int32_t* n_act_dev, const int32_t* jsrc,
+                                    const int32_t* cluster_of)
 {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // j-layout slot
     if (q >= st.n_pad) return;
@@ -58,47 +57,158 @@ __global__ void predict_kernel(const StateDev st, const JLayout jl, const double
         vp[0] = vp[1] = vp[2] = 0.0;
         gm = 0.0;
     }
-    if (PREC == static_cast<int>(Prec::FP64)) {
-        double2* P = static_cast<double2*>(jl.arr[0]) + 2 * q;
-        double2* V = static_cast<double2*>(jl.arr[1]) + 2 * q;
-        P[0] = make_double2(xp[0], xp[1]);
-        P[1] = make_double2(xp[2], gm);
-        V[0] = make_double2(vp[0], vp[1]);
-        V[1] = make_double2(vp[2], 0.0);
-    } else {
-        // grid-aligned splits; ghosts keep their far-away marker (zero mass)
-        const GridQuantum gx = grid_quantum(st.bound[0]);
-        float hi[3], lo[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            if (i >= 0) {
-                grid_split(xp[c], gx, hi[c], lo[c]);
-            } else {
-                hi[c] = static_cast<float>(GHOST_POS);
-                lo[c] = 0.f;
-            }
-        }
+    double2* P = static_cast<double2*>(jl.arr[0]) + 2 * q;
+    double2* V = static_cast<double2*>(jl.arr[1]) + 2 * q;
+    P[0] = make_double2(xp[0], xp[1]);
+    P[1] = make_double2(xp[2], gm);
+    V[0] = make_double2(vp[0], vp[1]);
+    V[1] = make_double2(vp[2], 0.0);
+}
+
+// ---------------------------------------------------------------------------
+// Steps 2-3 for the precisions whose j layout holds double-single values
+// (MIXED, DS, HYBRID): the prediction in double-single arithmetic on the
+// FP32 pipes.  GB300 spends ~68 cycles on each FP64 warp instruction, and the
+// FP64 Horner form plus the FP64 split into the layout took ~80 of them per
+// particle, so over a large system (an ensemble predicts every particle at
+// each block step) the predictor was FP64-bound.  Here each FP64 state value
+// is cut into hi + lo floats with integer operations on its bits (hi: the
+// leading 24 significand bits; lo: the remaining 29 rounded to a float, so
+// hi + lo keeps ~48 bits), Eqs. xpred and vpred run as double-single Horner
+// steps (FMA-based TwoProd and TwoSum), and the grid-aligned split is taken
+// from the double-single result.  The layout agrees with an FP64 prediction
+// to its own resolution (~2^-47 of the bound); values far outside the
+// layout's range (|x| < 2^-60 or > 2^60, or not finite) take FP64
+// conversions instead.
+// ---------------------------------------------------------------------------
+struct Dsf {
+    float hi, lo;
+};
+
+__device__ __forceinline__ Dsf dsf_of(double x)
+{
+    // work on the two 32-bit words (tests on the whole 64-bit pattern would
+    // become FP64 compares, which cost as much as the conversion they avoid)
+    const unsigned hw = static_cast<unsigned>(__double2hiint(x));
+    const unsigned lw = static_cast<unsigned>(__double2loint(x));
+    const unsigned e = (hw >> 20) & 0x7ffu;
+    if (e - (1023u - 60u) > 120u) {  // zero, |x| < 2^-60 or > 2^60, not finite
+        if (((hw & 0x7fffffffu) | lw) == 0u) return {0.f, 0.f};
+        const float hi = __double2float_rn(x);
+        return {hi, __double2float_rn(x - static_cast<double>(hi))};
+    }
+    const unsigned sign = hw & 0x80000000u;
+    // 52 significand bits: 20 in hw, 32 in lw; hi keeps the leading 23
+    const float hi =
+        __uint_as_float(sign | ((e - 1023u + 127u) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
+    // the remaining 29 significand bits are worth rest * 2^(e - 1075)
+    const unsigned rest = lw & 0x1fffffffu;
+    const float lo = __uint2float_rn(rest) * __uint_as_float((e - 1075u + 127u) << 23);
+    return {hi, sign ? -lo : lo};
+}
+
+__device__ __forceinline__ Dsf dsf_add(Dsf a, Dsf b)
+{
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    const float h = __fadd_rn(s, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+
+__device__ __forceinline__ Dsf dsf_fma(Dsf a, Dsf b, Dsf c)  // a b + c
+{
+    float p, e;
+    two_prod(a.hi, b.hi, p, e);
+    e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+    const float h = __fadd_rn(p, e);
+    return dsf_add({h, __fsub_rn(e, __fsub_rn(h, p))}, c);
+}
+
+__device__ __forceinline__ Dsf dsf_scale(Dsf a, float pow2) { return {a.hi * pow2, a.lo * pow2}; }
+
+// The grid quantum of grid_quantum() as floats, from the bound's bits.
+__device__ __forceinline__ void grid_quantum_f(uint32_t bound_bits, float& q, float& inv_q)
+{
+    const int eb = static_cast<int>((bound_bits >> 23) & 0xff);
+    int e;
+    if (eb == 0 || eb == 255)
+        frexp(2.0 * static_cast<double>(__uint_as_float(bound_bits)), &e);
+    else
+        e = eb - 125;  // 2B = (1.f / 2) 2^(eb - 125), 1.f / 2 in [0.5, 1)
+    q = ldexpf(1.f, e - 23);
+    inv_q = ldexpf(1.f, 23 - e);
+}
+
+// x rounded to a multiple of q (hi) and the rest (lo); x.hi - hi is exact.
+__device__ __forceinline__ void grid_split_ds(Dsf x, float q, float inv_q, float& hi, float& lo)
+{
+    hi = rintf(x.hi * inv_q) * q;
+    lo = __fadd_rn(__fsub_rn(x.hi, hi), x.lo);
+}
+
+template <int PREC>
+__global__ void predict_ds_kernel(const StateDev st, const JLayout jl, const double G,
+                                  const unsigned long long* t_bits, const double t_host,
+                                  const int32_t* n_act_dev, const int32_t* jsrc,
+                                  const int32_t* cluster_of)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // j-layout slot
+    if (q >= st.n_pad) return;
+    if (n_act_dev && *n_act_dev == 0) return;
+    const int64_t n = st.n;
+    const int64_t i = jsrc ? jsrc[q] : (q < n ? q : -1);
+    if (i < 0) {  // a ghost: far away, zero mass
+        const float g = static_cast<float>(GHOST_POS);
         if (PREC == static_cast<int>(Prec::MIXED)) {
-            static_cast<float4*>(jl.arr[0])[q] =
-                make_float4(hi[0], hi[1], hi[2], __double2float_rn(gm));
-            static_cast<float4*>(jl.arr[1])[q] =
-                make_float4(lo[0], lo[1], lo[2], __double2float_rn(vp[0]));
-            static_cast<float2*>(jl.arr[2])[q] =
-                make_float2(__double2float_rn(vp[1]), __double2float_rn(vp[2]));
+            static_cast<float4*>(jl.arr[0])[q] = make_float4(g, g, g, 0.f);
+            static_cast<float4*>(jl.arr[1])[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            static_cast<float2*>(jl.arr[2])[q] = make_float2(0.f, 0.f);
         } else {
-            const float gh = __double2float_rn(gm);
-            const float gl = __double2float_rn(gm - static_cast<double>(gh));
-            const GridQuantum gv = grid_quantum(st.bound[1]);
-            float vh[3], vl[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) grid_split(vp[c], gv, vh[c], vl[c]);
-            static_cast<float4*>(jl.arr[0])[q] = make_float4(hi[0], hi[1], hi[2], gh);
-            static_cast<float4*>(jl.arr[1])[q] = make_float4(lo[0], lo[1], lo[2], gl);
-            // (G m)^(2/3): the hybrid precision's near-pair test
-            const float g23 = cbrtf(gh);
-            static_cast<float4*>(jl.arr[2])[q] = make_float4(vh[0], vh[1], vh[2], g23 * g23);
-            static_cast<float4*>(jl.arr[3])[q] = make_float4(vl[0], vl[1], vl[2], 0.f);
+            static_cast<float4*>(jl.arr[0])[q] = make_float4(g, g, g, 0.f);
+            static_cast<float4*>(jl.arr[1])[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            static_cast<float4*>(jl.arr[2])[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            static_cast<float4*>(jl.arr[3])[q] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
+        return;
+    }
+    const double t = t_bits ? dkey_decode(t_bits[cluster_of ? cluster_of[i] : 0]) : t_host;
+    const Dsf h = dsf_of(t - st.t[i]);  // exact: both times are dyadic
+    const Dsf gm = dsf_fma(dsf_of(G), dsf_of(st.m[i]), Dsf{0.f, 0.f});
+    const Dsf sixth = {0x1.555556p-3f, -0x1.555556p-28f};  // 1/6 to ~2^-50
+    float qx, iqx;
+    grid_quantum_f(st.bound[0], qx, iqx);
+    float hi[3], lo[3];
+    Dsf vp[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const Dsf x = dsf_of(st.x[c * n + i]), v = dsf_of(st.v[c * n + i]);
+        const Dsf a = dsf_of(st.a[c * n + i]), j = dsf_of(st.j[c * n + i]);
+        // Eq. xpred: x + h (v + h (a / 2 + h j / 6)); Eq. vpred: v + h (a + h j / 2)
+        Dsf u = dsf_fma(j, sixth, Dsf{0.f, 0.f});
+        u = dsf_fma(h, u, dsf_scale(a, 0.5f));
+        u = dsf_fma(h, u, v);
+        grid_split_ds(dsf_fma(h, u, x), qx, iqx, hi[c], lo[c]);
+        vp[c] = dsf_fma(h, dsf_fma(h, dsf_scale(j, 0.5f), a), v);
+    }
+    if (PREC == static_cast<int>(Prec::MIXED)) {
+        static_cast<float4*>(jl.arr[0])[q] = make_float4(hi[0], hi[1], hi[2], __fadd_rn(gm.hi, gm.lo));
+        static_cast<float4*>(jl.arr[1])[q] =
+            make_float4(lo[0], lo[1], lo[2], __fadd_rn(vp[0].hi, vp[0].lo));
+        static_cast<float2*>(jl.arr[2])[q] =
+            make_float2(__fadd_rn(vp[1].hi, vp[1].lo), __fadd_rn(vp[2].hi, vp[2].lo));
+    } else {
+        float qv, iqv;
+        grid_quantum_f(st.bound[1], qv, iqv);
+        float vh[3], vl[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) grid_split_ds(vp[c], qv, iqv, vh[c], vl[c]);
+        static_cast<float4*>(jl.arr[0])[q] = make_float4(hi[0], hi[1], hi[2], gm.hi);
+        static_cast<float4*>(jl.arr[1])[q] = make_float4(lo[0], lo[1], lo[2], gm.lo);
+        // (G m)^(2/3): the hybrid precision's near-pair test
+        const float g23 = cbrtf(gm.hi);
+        static_cast<float4*>(jl.arr[2])[q] = make_float4(vh[0], vh[1], vh[2], g23 * g23);
+        static_cast<float4*>(jl.arr[3])[q] = make_float4(vl[0], vl[1], vl[2], 0.f);
     }
 }
 
@@ -165,15 +275,15 @@ cudaError_t predict_launch(const StateDev& st, Prec p, const JLayout& jl, double
     const int32_t* cof = cl ? cl->cluster_of : nullptr;
     switch (p) {
     case Prec::FP64:
-        predict_kernel<0><<<blocks, threads, 0, s>>>(st, jl, G, t_bits, t_host, n_act_dev, jsrc, cof);
+        predict_fp64_kernel<<<blocks, threads, 0, s>>>(st, jl, G, t_bits, t_host, n_act_dev, jsrc, cof);
         break;
     case Prec::MIXED:
     case Prec::MIXED_SPJ:  // same j layout
-        predict_kernel<1><<<blocks, threads, 0, s>>>(st, jl, G, t_bits, t_host, n_act_dev, jsrc, cof);
+        predict_ds_kernel<1><<<blocks, threads, 0, s>>>(st, jl, G, t_bits, t_host, n_act_dev, jsrc, cof);
         break;
     case Prec::DS:
     case Prec::HYBRID:  // same j layout
-        predict_kernel<2><<<blocks, threads, 0, s>>>(st, jl, G, t_bits, t_host, n_act_dev, jsrc, cof);
+        predict_ds_kernel<2><<<blocks, threads, 0, s>>>(st, jl, G, t_bits, t_host, n_act_dev, jsrc, cof);
         break;
     }
     return cudaGetLastError();

@@ -154,6 +154,45 @@ def test_force_after_prediction(gpu, orc):
     assert np.max(_rel(jerk, j0)) < 1e-10
 
 
+@pytest.mark.parametrize("prec", ["ds", "hybrid", "mixed"])
+def test_force_after_prediction_double_single_layout(gpu, orc, prec):
+    """The predictor of the FP32-pipe precisions works in double-single from the
+    FP64 state; the forces at the predicted positions must still meet each
+    precision's bound against oracle predict + force (FP64 throughout)."""
+    n = 1500
+    m, r, v = ics.plummer(n, 19)
+    rng = np.random.default_rng(3)
+    eps = 4.0 / n
+    # the particles' own a, j (HYBRID's near test reads them from the state);
+    # zero and tiny components take the exact paths of the split
+    a, j, _ = orc.force(m, r, v, eps, nthreads=NTHREADS)
+    a[::97] = 0.0
+    j[::11, 1] = 1e-30
+    dt = 2.0 ** -rng.integers(5, 9, n)
+    t = np.where(rng.uniform(size=n) < 0.5, 0.0, 1.0 / 64 - dt / 4)
+    tp = 1.0 / 64
+    idx = np.arange(n, dtype=np.int32)
+    rp, vp = orc.predict(r, v, a, j, t, tp)
+    a0, j0, p0 = orc.force(m, rp, vp, eps, nthreads=NTHREADS)
+    sa, sj, sp = _magnitude_sums(m, rp, vp, eps, idx)
+    with gpu.Context(prec) as ctx:
+        ctx.set_state(m, r, v, a, j, t, dt, eps=eps, eta=0.02)
+        ctx.predict(tp)
+        acc, jerk, pot = ctx.force(idx)
+    ea = np.linalg.norm(acc - a0, axis=1)
+    ej = np.linalg.norm(jerk - j0, axis=1)
+    ep = np.abs(pot - p0)
+    if prec == "ds":
+        assert np.all(ea <= 1e-10 * sa) and np.all(ej <= 1e-10 * sj)
+        assert np.all(ep <= 1e-10 * sp)
+    elif prec == "hybrid":
+        assert _rel(acc, a0).max() < 1e-6 and _rel(jerk, j0).max() < 1e-6
+        assert (ep / np.abs(p0)).max() < 1e-6
+    else:
+        assert np.all(ea <= 8 * U32 * sa) and np.all(ej <= 16 * U32 * sj)
+        assert np.all(ep <= 8 * U32 * sp)
+
+
 def _random_block_state(n, seed, T):
     """State with dyadic t, dt where a known subset is due at time T."""
     rng = np.random.default_rng(seed)
