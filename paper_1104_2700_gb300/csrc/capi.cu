@@ -136,7 +136,8 @@ void free_buffers(nb_ctx* c)
     dfree(c->scratch), dfree(c->counters), dfree(c->staging);
     dfree(c->energy_partials), dfree(c->energy_out), dfree(c->energy_ticket);
     dfree(c->cl.off), dfree(c->cl.joff), dfree(c->cl.eps2), dfree(c->cl.cluster_of);
-    dfree(c->cl.jsrc), dfree(c->cl.tkey), dfree(c->cl.grp_cluster), dfree(c->cl.grp_act_begin);
+    dfree(c->cl.jsrc), dfree(c->cl.tkey), dfree(c->cl.cnt), dfree(c->cl.grp_cluster);
+    dfree(c->cl.grp_act_begin);
     dfree(c->cl.grp_act_count), dfree(c->cl.grp_tile0), dfree(c->cl.plan_scalars);
     dfree(c->cl_energy);
     c->cap = c->cap_pad = c->cap_k = 0;
@@ -249,6 +250,7 @@ nb_status ensure_capacity(nb_ctx* c, int64_t n, int64_t n_pad, int64_t k)
         NB_CK(c, cudaMalloc(&cl.cluster_of, n * sizeof(int32_t)));
         NB_CK(c, cudaMalloc(&cl.jsrc, n_pad * sizeof(int32_t)));
         NB_CK(c, cudaMalloc(&cl.tkey, k * sizeof(unsigned long long)));
+        NB_CK(c, cudaMalloc(&cl.cnt, k * sizeof(int32_t)));
         NB_CK(c, cudaMalloc(&cl.grp_cluster, cl.max_groups * sizeof(int32_t)));
         NB_CK(c, cudaMalloc(&cl.grp_act_begin, cl.max_groups * sizeof(int32_t)));
         NB_CK(c, cudaMalloc(&cl.grp_act_count, cl.max_groups * sizeof(int32_t)));
@@ -370,13 +372,16 @@ nb::ForceArgs force_args(nb_ctx* c, Prec p, const nb::JLayout& jl, const int32_t
 }
 
 // Force on a sorted active list: in ensemble mode the plan comes first.
+// plan_from_counts: idx is the select's list of this block step, so the plan
+// may take each cluster's share from the select's per-cluster counts.
 nb_status run_force_list(nb_ctx* c, Prec p, const nb::JLayout& jl, const int32_t* idx,
-                         const int32_t* n_act_dev, int32_t n_act_host = -1)
+                         const int32_t* n_act_dev, int32_t n_act_host = -1,
+                         bool plan_from_counts = false)
 {
     if (c->ens) {
         // both variants of an ensemble context share one i per thread
         const int gi = 32 * (p == c->prec ? c->var[0].it : 1);
-        NB_CK(c, nb::plan_launch(c->cl, idx, n_act_dev, gi, c->stream));
+        NB_CK(c, nb::plan_launch(c->cl, idx, n_act_dev, gi, c->stream, plan_from_counts));
     }
     return run_force(c, p, jl, idx, n_act_dev, n_act_host);
 }
@@ -418,7 +423,7 @@ nb_status block_step(nb_ctx* c, double t_end)
         NB_CK(c, nb::select_launch(c->st, c->sd, t_end, c->stream));
     NB_CK(c, nb::predict_launch(c->st, c->prec, c->jl, c->cfg.G, tkeys, 0.0, c->sd.n_act,
                                 c->stream, cl));
-    nb_status s = run_force_list(c, c->prec, c->jl, c->sd.idx, c->sd.n_act);
+    nb_status s = run_force_list(c, c->prec, c->jl, c->sd.idx, c->sd.n_act, -1, true);
     if (s != NB_OK) return s;
     nb::CorrectArgs ca;
     ca.idx = c->sd.idx;

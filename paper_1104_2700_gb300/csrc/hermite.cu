@@ -551,33 +551,54 @@ cudaError_t select_launch(const StateDev& st, const SchedDev& sd, double t_end, 
     return cudaGetLastError();
 }
 
-// Ensemble step 1: block c finds the next time of cluster c.
+// Ensemble step 1: block c finds the next time of cluster c and how many of
+// its particles reach it (0 when that time lies past t_end): a reduction of
+// (smallest key, count of that key) pairs.
+__device__ __forceinline__ void min_count_merge(unsigned long long& best, int& n,
+                                                unsigned long long ob, int on)
+{
+    if (ob < best) {
+        best = ob;
+        n = on;
+    } else if (ob == best) {
+        n += on;
+    }
+}
+
 __global__ void cluster_tmin_kernel(const unsigned long long* __restrict__ nkey,
-                                    const int64_t* off, unsigned long long* tkey)
+                                    const int64_t* off, unsigned long long* tkey, int32_t* cnt,
+                                    double t_end)
 {
     const int c = blockIdx.x;
     unsigned long long best = ~0ull;
-    for (int64_t i = off[c] + threadIdx.x; i < off[c + 1]; i += blockDim.x) {
-        const unsigned long long k = nkey[i];
-        best = k < best ? k : best;
-    }
+    int n = 0;
+    for (int64_t i = off[c] + threadIdx.x; i < off[c + 1]; i += blockDim.x)
+        min_count_merge(best, n, nkey[i], 1);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
-        best = other < best ? other : best;
+        const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int on = __shfl_xor_sync(0xffffffffu, n, o);
+        min_count_merge(best, n, ob, on);
     }
     __shared__ unsigned long long wbest[32];
+    __shared__ int wn[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) wbest[wid] = best;
+    if (lane == 0) wbest[wid] = best, wn[wid] = n;
     __syncthreads();
     if (wid == 0) {
-        best = lane < (int)(blockDim.x >> 5) ? wbest[lane] : ~0ull;
+        const bool have = lane < (int)(blockDim.x >> 5);
+        best = have ? wbest[lane] : ~0ull;
+        n = have ? wn[lane] : 0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
-            best = other < best ? other : best;
+            const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int on = __shfl_xor_sync(0xffffffffu, n, o);
+            min_count_merge(best, n, ob, on);
         }
-        if (lane == 0) tkey[c] = best;
+        if (lane == 0) {
+            tkey[c] = best;
+            cnt[c] = (best != ~0ull && dkey_decode(best) <= t_end) ? n : 0;
+        }
     }
 }
 
@@ -588,7 +609,7 @@ cudaError_t cluster_select_launch(const StateDev& st, const ClusterDev& cl, cons
     const int64_t nb64 = (st.n + SCHED_CHUNK - 1) / SCHED_CHUNK;
     if (nb64 > sd.max_blocks) return cudaErrorInvalidValue;
     const int nb = static_cast<int>(nb64);
-    cluster_tmin_kernel<<<cl.k, 256, 0, s>>>(st.nkey, cl.off, cl.tkey);
+    cluster_tmin_kernel<<<cl.k, 256, 0, s>>>(st.nkey, cl.off, cl.tkey, cl.cnt, t_end);
     count_kernel<<<nb, SCHED_THREADS, 0, s>>>(st.nkey, st.n, cl.tkey, cl.cluster_of, t_end, sd);
     scatter_kernel<<<nb, SCHED_THREADS, 0, s>>>(st.nkey, st.n, cl.tkey, cl.cluster_of, t_end, sd);
     return cudaGetLastError();
@@ -641,17 +662,35 @@ __device__ int64_t plan_scan(int64_t v, int64_t* total)
 }
 
 __global__ void __launch_bounds__(PLAN_THREADS)
-    plan_kernel(const ClusterDev cl, const int32_t* idx, const int32_t* n_act_dev, int gi)
+    plan_kernel(const ClusterDev cl, const int32_t* idx, const int32_t* n_act_dev, int gi,
+                const int32_t* cnt)
 {
     const int64_t n_act = *n_act_dev;
     const int K = cl.k;
     const int per = (K + PLAN_THREADS - 1) / PLAN_THREADS;
     const int c0 = threadIdx.x * per;
     const int c1 = c0 + per < K ? c0 + per : K;
-    int64_t gsum = 0, tsum = 0;
+    // cluster c's share [b, e) of the ascending active list: from the
+    // select's counts (a scan), or by binary search in idx
+    int64_t csum = 0;
+    if (cnt)
+        for (int c = c0; c < c1; ++c) csum += cnt[c];
+    int64_t ctot;
+    const int64_t cbase = plan_scan(csum, &ctot);
+    auto share = [&](int c, int64_t& run, int64_t& b, int64_t& e) {
+        if (cnt) {
+            b = run;
+            e = run + cnt[c];
+            run = e;
+        } else {
+            b = lower_bound_i32(idx, n_act, cl.off[c]);
+            e = lower_bound_i32(idx, n_act, cl.off[c + 1]);
+        }
+    };
+    int64_t gsum = 0, tsum = 0, run = cbase;
     for (int c = c0; c < c1; ++c) {
-        const int64_t b = lower_bound_i32(idx, n_act, cl.off[c]);
-        const int64_t e = lower_bound_i32(idx, n_act, cl.off[c + 1]);
+        int64_t b, e;
+        share(c, run, b, e);
         const int64_t gc = (e - b + gi - 1) / gi;
         gsum += gc;
         tsum += gc * ((cl.joff[c + 1] - cl.joff[c]) / TJ);
@@ -663,9 +702,10 @@ __global__ void __launch_bounds__(PLAN_THREADS)
         if (threadIdx.x == 0) cl.plan_scalars[0] = cl.plan_scalars[1] = 0;
         return;
     }
+    run = cbase;
     for (int c = c0; c < c1; ++c) {
-        const int64_t b = lower_bound_i32(idx, n_act, cl.off[c]);
-        const int64_t e = lower_bound_i32(idx, n_act, cl.off[c + 1]);
+        int64_t b, e;
+        share(c, run, b, e);
         const int64_t nt = (cl.joff[c + 1] - cl.joff[c]) / TJ;
         for (int64_t a = b; a < e; a += gi) {
             cl.grp_cluster[gbase] = c;
@@ -684,9 +724,9 @@ __global__ void __launch_bounds__(PLAN_THREADS)
 }
 
 cudaError_t plan_launch(const ClusterDev& cl, const int32_t* idx, const int32_t* n_act_dev,
-                        int gi, cudaStream_t s)
+                        int gi, cudaStream_t s, bool from_counts)
 {
-    plan_kernel<<<1, PLAN_THREADS, 0, s>>>(cl, idx, n_act_dev, gi);
+    plan_kernel<<<1, PLAN_THREADS, 0, s>>>(cl, idx, n_act_dev, gi, from_counts ? cl.cnt : nullptr);
     return cudaGetLastError();
 }
 

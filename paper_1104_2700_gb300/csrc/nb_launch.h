@@ -94,6 +94,8 @@ struct ClusterDev {
     int32_t* cluster_of = nullptr;   // n: cluster of each particle
     int32_t* jsrc = nullptr;         // n_pad: particle of each j slot, -1 = ghost
     unsigned long long* tkey = nullptr;  // k: next block time of each cluster (key)
+    int32_t* cnt = nullptr;              // k: members of each cluster's next block
+                                         // (0 past t_end), from cluster_select_launch
     // force plan written by plan_launch
     int32_t* grp_cluster = nullptr;
     int32_t* grp_act_begin = nullptr;
@@ -172,8 +174,11 @@ cudaError_t predict_launch(const StateDev& st, Prec p, const JLayout& jl, double
 // the force plan of the active list (idx ascending, clusters contiguous).
 cudaError_t cluster_select_launch(const StateDev& st, const ClusterDev& cl, const SchedDev& sd,
                                   double t_end, cudaStream_t s);
+// With from_counts the plan takes each cluster's share of the (sorted) active
+// list from cl.cnt, written by the select of the same block step; otherwise
+// it finds the shares in idx by binary search (any sorted list).
 cudaError_t plan_launch(const ClusterDev& cl, const int32_t* idx, const int32_t* n_act_dev,
-                        int gi, cudaStream_t s);
+                        int gi, cudaStream_t s, bool from_counts = false);
 // Per-cluster energies: out[2c] = sum 1/2 m v^2, out[2c+1] = sum 1/2 m phi.
 cudaError_t cluster_energy_launch(const StateDev& st, const ClusterDev& cl, const double* pot_all,
                                   double* out, cudaStream_t s);
