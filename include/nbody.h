@@ -88,6 +88,11 @@ typedef struct nb_config {
     int32_t i_per_thread; /* force kernel register blocking; 0 = default        */
     int32_t ctas_per_sm;  /* persistent force CTAs per SM; 0 = default          */
     int32_t autotune;     /* 1: run nb_autotune after every load                */
+    int32_t j_split;      /* lanes per i particle: the j range of each tile is
+                           * split over 1, 2, 4 or 8 lanes of a warp and the
+                           * partial sums are added with warp shuffles (a
+                           * group then holds 32 / j_split i); 0 = default 1.
+                           * Only with i_per_thread 1 above 1.            */
     int64_t wait_limit_cycles; /* GPU clock cycles a force kernel waits for
                               * one staged j tile before it gives up and the
                               * call fails with NB_ETIMEOUT; 0 = about one
@@ -100,18 +105,24 @@ typedef struct nb_config {
  * autotuning. */
 void nb_config_init(nb_config* cfg);
 
-/* Launch shapes of the force kernel (i-tile per lane, j-split over warps): blocks of
- * fewer than nact_split active particles use the "small" shape, others the
- * "large" one.  i_per_thread is the i-tile per lane (an i-group is 32 times
- * that); ctas_per_sm sets the persistent grid, which fixes how far each
- * i-group's j range is split across warps.  The *_us fields give the force
- * time the autotuner measured for the chosen shapes on its probe blocks. */
+/* Launch shapes of the force kernel (i-tile per lane, j-split inside a warp
+ * and over warps): blocks of fewer than nact_split active particles use the
+ * "small" shape, others the "large" one.  i_per_thread is the i-tile per
+ * lane; j_split the lanes that share one i, each taking every j_split-th j
+ * of a tile (an i-group is 32 * i_per_thread / j_split particles); ctas_per_sm
+ * sets the persistent grid, which fixes how far each i-group's j range is
+ * split across warps.  An ensemble context uses one i-tile and one j split
+ * for both shapes (its force plan is cut once per block).  The *_us fields
+ * give the force time the autotuner measured for the chosen shapes on its
+ * probe blocks. */
 typedef struct nb_tuning {
     int32_t small_i_per_thread;
     int32_t small_ctas_per_sm;
     int32_t large_i_per_thread;
     int32_t large_ctas_per_sm;
     int32_t nact_split;
+    int32_t small_j_split;
+    int32_t large_j_split;
     double small_us;
     double large_us;
 } nb_tuning;

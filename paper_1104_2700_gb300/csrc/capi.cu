@@ -29,6 +29,7 @@ struct nb_ctx {
     struct Variant {
         int it = 1;
         int grid = 0;
+        int split = 1;  // lanes per i (j split inside a warp)
     } var[2];
     int32_t nact_split = 1024;
     int grid64 = 0;      // persistent CTAs of the FP64 energy pass (1 i per thread)
@@ -243,7 +244,7 @@ nb_status ensure_capacity(nb_ctx* c, int64_t n, int64_t n_pad, int64_t k)
     NB_CK(c, cudaMemset(c->energy_ticket, 0, sizeof(uint32_t)));
     if (k > 0) {
         nb::ClusterDev& cl = c->cl;
-        cl.max_groups = n / 32 + k + 1;
+        cl.max_groups = n / 4 + k + 1;  // groups are at least 32 / 8 wide
         NB_CK(c, cudaMalloc(&cl.off, (k + 1) * sizeof(int64_t)));
         NB_CK(c, cudaMalloc(&cl.joff, (k + 1) * sizeof(int64_t)));
         NB_CK(c, cudaMalloc(&cl.eps2, k * sizeof(double)));
@@ -316,12 +317,14 @@ nb_status run_force(nb_ctx* c, Prec p, const nb::JLayout& jl, const int32_t* idx
     nb::ForceArgs f = force_args(c, p, jl, idx, n_act_dev);
     if (p != c->prec) {  // the FP64 energy pass of a lower-precision context
         f.it = 1;
+        f.split = 1;
         f.grid = c->grid64;
         NB_CK(c, nb::force_launch(f, c->stream));
         return NB_OK;
     }
     for (int v = 0; v < 2; ++v) {
         f.it = c->var[v].it;
+        f.split = c->var[v].split;
         f.grid = c->var[v].grid;
         f.nact_lo = v == 0 ? 0 : c->nact_split;
         f.nact_hi = v == 0 ? c->nact_split : 0x7fffffff;
@@ -379,8 +382,8 @@ nb_status run_force_list(nb_ctx* c, Prec p, const nb::JLayout& jl, const int32_t
                          bool plan_from_counts = false)
 {
     if (c->ens) {
-        // both variants of an ensemble context share one i per thread
-        const int gi = 32 * (p == c->prec ? c->var[0].it : 1);
+        // both variants of an ensemble context share one i-group width
+        const int gi = p == c->prec ? 32 * c->var[0].it / c->var[0].split : 32;
         NB_CK(c, nb::plan_launch(c->cl, idx, n_act_dev, gi, c->stream, plan_from_counts));
     }
     return run_force(c, p, jl, idx, n_act_dev, n_act_host);
@@ -541,6 +544,7 @@ void nb_config_init(nb_config* cfg)
     cfg->i_per_thread = 0;
     cfg->ctas_per_sm = 0;
     cfg->autotune = 0;
+    cfg->j_split = 0;
     cfg->wait_limit_cycles = 0;
 }
 
@@ -549,6 +553,9 @@ nb_status nb_create(const nb_config* cfg, nb_ctx** out)
     if (!cfg || !out) return NB_EINVAL;
     *out = nullptr;
     if (cfg->precision < NB_FP64 || cfg->precision > NB_MIXED_SPJ) return NB_EINVAL;
+    if (cfg->j_split != 0 && cfg->j_split != 1 && cfg->j_split != 2 && cfg->j_split != 4 &&
+        cfg->j_split != 8)
+        return NB_EINVAL;
     if (!is_pow2(cfg->dt_max) || !(cfg->dt_min > 0.0) || cfg->dt_min > cfg->dt_max) return NB_EINVAL;
     if (!(cfg->eta_start > 0.0) || !std::isfinite(cfg->G)) return NB_EINVAL;
     nb_ctx* c = new (std::nothrow) nb_ctx;
@@ -574,18 +581,20 @@ nb_status nb_create(const nb_config* cfg, nb_ctx** out)
     // thread for small blocks, two for large MIXED blocks; at most 4
     // persistent CTAs per SM.  nb_autotune replaces them by measurement.
     for (int v = 0; v < 2; ++v) {
+        const int split = cfg->j_split > 0 ? cfg->j_split : 1;
         int it = cfg->i_per_thread;
-        if (it == 0) it = (v == 1 && nb::is_mixed(c->prec)) ? 2 : 1;
-        if (!nb::force_variant_exists(c->prec, it)) return bail(NB_EINVAL);
-        if (nb::force_setup(c->prec, it) != cudaSuccess) return bail(NB_ECUDA);
-        const int occ = nb::force_ctas_per_sm(c->prec, it);
+        if (it == 0) it = (v == 1 && nb::is_mixed(c->prec) && split == 1) ? 2 : 1;
+        if (!nb::force_variant_exists(c->prec, it, split)) return bail(NB_EINVAL);
+        if (nb::force_setup(c->prec, it, split) != cudaSuccess) return bail(NB_ECUDA);
+        const int occ = nb::force_ctas_per_sm(c->prec, it, split);
         if (occ < 1) return bail(NB_ECUDA);
         const int per_sm = cfg->ctas_per_sm > 0 ? cfg->ctas_per_sm : std::min(occ, 4);
         c->var[v].it = it;
+        c->var[v].split = split;
         c->var[v].grid = per_sm * c->num_sms;
     }
-    if (nb::force_setup(Prec::FP64, 1) != cudaSuccess) return bail(NB_ECUDA);
-    const int per_sm64 = nb::force_ctas_per_sm(Prec::FP64, 1);
+    if (nb::force_setup(Prec::FP64, 1, 1) != cudaSuccess) return bail(NB_ECUDA);
+    const int per_sm64 = nb::force_ctas_per_sm(Prec::FP64, 1, 1);
     if (per_sm64 < 1) return bail(NB_ECUDA);
     c->grid64 = per_sm64 * c->num_sms;
     if (cudaMalloc(&c->status_dev, sizeof(uint32_t)) != cudaSuccess) return bail(NB_ENOMEM);
@@ -946,9 +955,10 @@ nb_status nb_set_ensemble(nb_ctx* c, int32_t k, const int64_t* offsets, const do
     c->ens = true;
     nb_status s = ensure_capacity(c, n, n_pad, k);
     if (s != NB_OK) return s;
-    // the ensemble plan cuts i-groups for one i-per-thread value
-    if (c->var[1].it != c->var[0].it) {
+    // the ensemble plan cuts i-groups of one width for both variants
+    if (c->var[1].it != c->var[0].it || c->var[1].split != c->var[0].split) {
         c->var[1].it = c->var[0].it;
+        c->var[1].split = c->var[0].split;
         if ((s = ensure_force_scratch(c, c->var[0].grid, c->var[1].grid)) != NB_OK) return s;
     }
     c->eps = 0.0;  // per system: cl.eps2
@@ -1018,10 +1028,12 @@ nb_status nb_selftest_timeout(nb_ctx* c)
     uint32_t* h = reinterpret_cast<uint32_t*>(c->pinned);
     NB_CK(c, cudaMemsetAsync(c->status_dev, 0, sizeof(uint32_t), c->stream));
     NB_CK(c, nb::iota_launch(c->idx_user, c->n, c->n_act_user, c->stream));
-    if (c->ens) NB_CK(c, nb::plan_launch(c->cl, c->idx_user, c->n_act_user, 32 * c->var[0].it,
-                                         c->stream));
+    if (c->ens)
+        NB_CK(c, nb::plan_launch(c->cl, c->idx_user, c->n_act_user,
+                                 32 * c->var[0].it / c->var[0].split, c->stream));
     nb::ForceArgs f = force_args(c, c->prec, c->jl, c->idx_user, c->n_act_user);
     f.it = c->var[0].it;
+    f.split = c->var[0].split;
     f.grid = c->var[0].grid;
     f.wait_limit = 200000;  // ~0.1 ms per warp
     f.unfed_first_tile = 1;
@@ -1046,20 +1058,23 @@ nb_status nb_autotune(nb_ctx* c, nb_tuning* out)
                                static_cast<int32_t>(std::min<int64_t>(256, n)),
                                static_cast<int32_t>(std::min<int64_t>(2048, n)),
                                static_cast<int32_t>(std::min<int64_t>(16384, n))};
-    // candidates: i per thread (two only for MIXED and HYBRID single systems) x CTAs per SM
-    std::vector<int> its = {1};
-    if ((nb::is_mixed(c->prec) || c->prec == Prec::HYBRID) && !c->ens) its.push_back(2);
+    // candidates: (i per thread, j split) x CTAs per SM; two i per thread
+    // only for MIXED and HYBRID single systems, and only without a j split
+    std::vector<std::pair<int, int>> shapes = {{1, 1}, {1, 2}, {1, 4}, {1, 8}};
+    if ((nb::is_mixed(c->prec) || c->prec == Prec::HYBRID) && !c->ens) shapes.push_back({2, 1});
     struct Cand {
-        int it, cps;
+        int it, split, cps;
         double us[4];
     };
     std::vector<Cand> cands;
     int max_grid = 0;
-    for (int it : its) {
-        const int occ = nb::force_ctas_per_sm(c->prec, it);
+    for (const auto& sh : shapes) {
+        if (nb::force_setup(c->prec, sh.first, sh.second) != cudaSuccess)
+            return fail(c, NB_ECUDA, "autotune: kernel attributes");
+        const int occ = nb::force_ctas_per_sm(c->prec, sh.first, sh.second);
         for (int cps : {1, 2, 3, 4, 5, 6, 8})
             if (cps <= occ) {
-                cands.push_back({it, cps, {0, 0, 0, 0}});
+                cands.push_back({sh.first, sh.second, cps, {0, 0, 0, 0}});
                 max_grid = std::max(max_grid, cps * c->num_sms);
             }
     }
@@ -1067,7 +1082,7 @@ nb_status nb_autotune(nb_ctx* c, nb_tuning* out)
     // scratch for the largest candidate grid with either i per thread
     const nb_ctx::Variant keep0 = c->var[0], keep1 = c->var[1];
     c->var[0] = {1, max_grid};
-    c->var[1] = {its.back(), max_grid};
+    c->var[1] = {shapes.back().first, max_grid};
     s = ensure_force_scratch(c, max_grid, max_grid);
     c->var[0] = keep0;
     c->var[1] = keep1;
@@ -1087,11 +1102,12 @@ nb_status nb_autotune(nb_ctx* c, nb_tuning* out)
             st = fail(c, NB_ECUDA, "autotune: set n_act");
         for (auto& cd : cands) {
             if (st != NB_OK) break;
-            if (c->ens && cudaSuccess != nb::plan_launch(c->cl, c->idx_user, c->n_act_user, 32 * cd.it,
-                                                         c->stream))
+            if (c->ens && cudaSuccess != nb::plan_launch(c->cl, c->idx_user, c->n_act_user,
+                                                         32 * cd.it / cd.split, c->stream))
                 st = fail(c, NB_ECUDA, "autotune: plan");
             nb::ForceArgs f = force_args(c, c->prec, c->jl, c->idx_user, c->n_act_user);
             f.it = cd.it;
+            f.split = cd.split;
             f.grid = cd.cps * c->num_sms;
             const int reps = 3;
             cudaError_t e = nb::force_launch(f, c->stream);  // warm-up
@@ -1109,14 +1125,30 @@ nb_status nb_autotune(nb_ctx* c, nb_tuning* out)
     cudaEventDestroy(e1);
     if (st != NB_OK) return st;
     if ((s = check_status(c)) != NB_OK) return s;
-    // best shape per bucket; ties go to the smaller grid (listed first)
-    const Cand* best[2] = {&cands[0], &cands[0]};
-    for (const auto& cd : cands) {
-        if (cd.us[0] + cd.us[1] < best[0]->us[0] + best[0]->us[1]) best[0] = &cd;
-        if (cd.us[2] + cd.us[3] < best[1]->us[2] + best[1]->us[3]) best[1] = &cd;
+    // best shape per bucket; ties go to the smaller grid (listed first).  An
+    // ensemble's plan is cut once per block for both variants, so there the
+    // two share the (i per thread, j split) with the least total time.
+    auto best_of = [&](int b, int it, int split) {
+        const Cand* bc = nullptr;
+        for (const auto& cd : cands) {
+            if (it > 0 && (cd.it != it || cd.split != split)) continue;
+            if (!bc || cd.us[2 * b] + cd.us[2 * b + 1] < bc->us[2 * b] + bc->us[2 * b + 1]) bc = &cd;
+        }
+        return bc;
+    };
+    const Cand* best[2] = {best_of(0, 0, 0), best_of(1, 0, 0)};
+    if (c->ens) {
+        double tbest = -1.0;
+        for (const auto& sh : shapes) {
+            const Cand* b0 = best_of(0, sh.first, sh.second);
+            const Cand* b1 = best_of(1, sh.first, sh.second);
+            if (!b0 || !b1) continue;
+            const double tot = b0->us[0] + b0->us[1] + b1->us[2] + b1->us[3];
+            if (tbest < 0.0 || tot < tbest) best[0] = b0, best[1] = b1, tbest = tot;
+        }
     }
-    c->var[0] = {best[0]->it, best[0]->cps * c->num_sms};
-    c->var[1] = {best[1]->it, best[1]->cps * c->num_sms};
+    c->var[0] = {best[0]->it, best[0]->cps * c->num_sms, best[0]->split};
+    c->var[1] = {best[1]->it, best[1]->cps * c->num_sms, best[1]->split};
     c->nact_split = 1024;
     drop_graph(c);
     c->last_force_n_act = -1;
@@ -1126,6 +1158,8 @@ nb_status nb_autotune(nb_ctx* c, nb_tuning* out)
         out->large_i_per_thread = best[1]->it;
         out->large_ctas_per_sm = best[1]->cps;
         out->nact_split = c->nact_split;
+        out->small_j_split = best[0]->split;
+        out->large_j_split = best[1]->split;
         out->small_us = best[0]->us[0] + best[0]->us[1];
         out->large_us = best[1]->us[2] + best[1]->us[3];
     }

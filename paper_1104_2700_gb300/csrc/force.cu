@@ -16,6 +16,8 @@
 //     warps is summed by the last warp to finish, in warp order, from
 //     partials in global scratch: deterministic, and no warp ever waits on
 //     another.
+#include <type_traits>
+
 #include "nb_device.cuh"
 #include "nb_launch.h"
 
@@ -101,14 +103,16 @@ struct PolicyFP64 {
         s.vx = v0.x, s.vy = v0.y, s.vz = v1.x;
     }
 
-    template <bool MASK>
+    // S lanes share each i; lane slice sl takes records sl, sl + S, ...
+    template <bool MASK, int S>
     __device__ static void tile(const unsigned char* buf, int64_t j0, const double eps2,
-                                I (&is)[IT], Acc (&ac)[IT])
+                                I (&is)[IT], Acc (&ac)[IT], int sl)
     {
         const double2* sP = reinterpret_cast<const double2*>(buf);
         const double2* sV = reinterpret_cast<const double2*>(buf + TJ * 32);
 #pragma unroll 2
-        for (int k = 0; k < TJ; ++k) {
+        for (int u = 0; u < TJ / S; ++u) {
+            const int k = sl + S * u;
             const double2 p0 = sP[2 * k], p1 = sP[2 * k + 1];
             const double2 v0 = sV[2 * k], v1 = sV[2 * k + 1];
 #pragma unroll
@@ -187,9 +191,9 @@ struct PolicyMixed {
         s.vx = B.w, s.vy = C.x, s.vz = C.y;
     }
 
-    template <bool MASK>
+    template <bool MASK, int S>
     __device__ static void tile(const unsigned char* buf, int64_t j0, const double eps2d,
-                                I (&is)[IT], Acc (&ac)[IT])
+                                I (&is)[IT], Acc (&ac)[IT], int sl)
     {
         const float4* sA = reinterpret_cast<const float4*>(buf);
         const float4* sB = reinterpret_cast<const float4*>(buf + TJ * 16);
@@ -206,7 +210,8 @@ struct PolicyMixed {
             }
         }
 #pragma unroll 4
-        for (int k = 0; k < TJ; ++k) {
+        for (int u = 0; u < TJ / S; ++u) {
+            const int k = sl + S * u;
             const float4 A = sA[k];
             const float4 B = sB[k];
             const float2 C = sC[k];
@@ -413,9 +418,9 @@ struct PolicyDS {
 
     __device__ static void load_i(const ForceParams& f, int p, int, I& s) { ds_load_i(f, p, s); }
 
-    template <bool MASK>
+    template <bool MASK, int S>
     __device__ static void tile(const unsigned char* buf, int64_t j0, const double eps2d,
-                                I (&is)[IT], Acc (&ac)[IT])
+                                I (&is)[IT], Acc (&ac)[IT], int sl)
     {
         const float4* sA = reinterpret_cast<const float4*>(buf);
         const float4* sB = reinterpret_cast<const float4*>(buf + TJ * 16);
@@ -424,7 +429,8 @@ struct PolicyDS {
         const float e2h = static_cast<float>(eps2d);
         const float e2l = static_cast<float>(eps2d - static_cast<double>(e2h));
 #pragma unroll 1
-        for (int k = 0; k < TJ; ++k) {
+        for (int u = 0; u < TJ / S; ++u) {
+            const int k = sl + S * u;
             const float4 A = sA[k];
             const float4 B = sB[k];
             const float4 C = sC[k];
@@ -557,11 +563,14 @@ struct PolicyHybrid {
     // GUARD: some lane of the warp has the integration guard on (rare); the
     // other instantiation assumes none has, so near is the natural test and
     // the noise estimate reuses the far-pair factor m / r.
-    template <bool MASK, bool GUARD>
+    template <bool MASK, bool GUARD, int S>
     __device__ static void tile(const unsigned char* buf, int64_t j0, const double eps2d,
-                                I (&is)[IT], Acc (&ac)[IT])
+                                I (&is)[IT], Acc (&ac)[IT], int sl)
     {
         static_assert(TJ == 64, "one 64-bit near mask per lane and tile");
+        // this lane's records: tile slots sl + S u, u < R, in runs of RUN
+        constexpr int R = TJ / S;
+        constexpr int RUN = R < HY_RUN ? R : HY_RUN;
         const float4* sA = reinterpret_cast<const float4*>(buf);
         const float4* sB = reinterpret_cast<const float4*>(buf + TJ * 16);
         const float4* sC = reinterpret_cast<const float4*>(buf + TJ * 32);
@@ -569,12 +578,12 @@ struct PolicyHybrid {
         const float e2h = static_cast<float>(eps2d);
         const float e2l = static_cast<float>(eps2d - static_cast<double>(e2h));
         // Pass 1: every pair in FP32; near pairs add nothing here and are
-        // marked in a per-lane 64-bit mask (bit k = slot j0 + k).
+        // marked in a per-lane 64-bit mask (bit u = slot sl + S u).
         uint32_t nlo[IT], nhi[IT];
 #pragma unroll
         for (int q = 0; q < IT; ++q) nlo[q] = nhi[q] = 0u;
 #pragma unroll 1
-        for (int k0 = 0; k0 < TJ; k0 += HY_RUN) {
+        for (int u0 = 0; u0 < R; u0 += RUN) {
             float ax[IT], ay[IT], az[IT], jx[IT], jy[IT], jz[IT], ph[IT], bs[IT];
             uint32_t run[IT];
 #pragma unroll
@@ -583,8 +592,8 @@ struct PolicyHybrid {
                 run[q] = 0u;
             }
 #pragma unroll 4
-            for (int u = 0; u < HY_RUN; ++u) {
-                const int k = k0 + u;
+            for (int du = 0; du < RUN; ++du) {
+                const int k = sl + S * (u0 + du);
                 const float4 A = sA[k];
                 const float4 B = sB[k];
                 const float4 C = sC[k];
@@ -634,7 +643,7 @@ struct PolicyHybrid {
                     jy[q] = fmaf(g, fmaf(t, dy, dvy), jy[q]);
                     jz[q] = fmaf(g, fmaf(t, dz, dvz), jz[q]);
                     ph[q] += mr;
-                    run[q] |= static_cast<uint32_t>(near) << u;
+                    run[q] |= static_cast<uint32_t>(near) << du;
                 }
             }
 #pragma unroll
@@ -643,8 +652,8 @@ struct PolicyHybrid {
                 ac[q].jx.fold(jx[q]), ac[q].jy.fold(jy[q]), ac[q].jz.fold(jz[q]);
                 ac[q].ph.fold(ph[q]);
                 ac[q].q = fmaf(bs[q], bs[q], ac[q].q);
-                if (k0 < 32) nlo[q] |= run[q] << k0;
-                else nhi[q] |= run[q] << (k0 - 32);
+                if (u0 < 32) nlo[q] |= run[q] << u0;
+                else nhi[q] |= run[q] << (u0 - 32);
             }
         }
         // Pass 2: the near pairs in double-single, each lane walking its own
@@ -654,14 +663,15 @@ struct PolicyHybrid {
             uint32_t lo = nlo[q], hi = nhi[q];
             while (__any_sync(0xffffffffu, (lo | hi) != 0u)) {
                 if ((lo | hi) != 0u) {
-                    int k;
+                    int u;
                     if (lo) {
-                        k = __ffs(lo) - 1;
+                        u = __ffs(lo) - 1;
                         lo &= lo - 1u;
                     } else {
-                        k = 32 + __ffs(hi) - 1;
+                        u = 32 + __ffs(hi) - 1;
                         hi &= hi - 1u;
                     }
+                    const int k = sl + S * u;
                     ds_pair<false>(sA[k], sB[k], sC[k], sD[k], is[q], e2h, e2l, j0 + k, ac[q]);
                 }
             }
@@ -776,7 +786,10 @@ struct ClusterPlan {
     }
 };
 
-template <class K, int IT, class Plan>
+// S: lanes per i (the j split inside a warp).  Lane = ir + IW sl: i slot ir
+// of the warp's IW = 32 / S, j slice sl; the S slices of an i are summed with
+// shuffles before the split-group tree.
+template <class K, int IT, int S, class Plan>
 __global__ void __launch_bounds__(FORCE_WARPS * 32)
     force_kernel(const ForceParams f)
 {
@@ -786,7 +799,10 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
     const int64_t w = (int64_t)blockIdx.x * FORCE_WARPS + wib;
     const int64_t P = (int64_t)gridDim.x * FORCE_WARPS;
 
-    constexpr int GI = 32 * IT;
+    static_assert(S == 1 || S == 2 || S == 4 || S == 8, "j split of 1, 2, 4 or 8 lanes");
+    constexpr int IW = 32 / S;
+    constexpr int GI = IW * IT;
+    const int ir = lane % IW, sl = lane / IW;
     {
         // Launch variants tuned for different block sizes share one stream:
         // each works only inside its n_act window (read on the device, so
@@ -847,7 +863,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
             fresh = false;
 #pragma unroll
             for (int q = 0; q < IT; ++q) {
-                const int64_t a = gi.act_begin + q * 32 + lane;
+                const int64_t a = gi.act_begin + q * IW + ir;
                 int p = -1, particle = -1;
                 if (a < gi.act_begin + gi.act_count) {
                     particle = f.idx[a];
@@ -891,15 +907,15 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
         const bool mask_self = __any_sync(0xffffffffu, self_here);
         if constexpr (K::GUARDED) {
             if (guard_any) {
-                if (mask_self) K::template tile<true, true>(buf, j0, gi.eps2, is, ac);
-                else K::template tile<false, true>(buf, j0, gi.eps2, is, ac);
+                if (mask_self) K::template tile<true, true, S>(buf, j0, gi.eps2, is, ac, sl);
+                else K::template tile<false, true, S>(buf, j0, gi.eps2, is, ac, sl);
             } else {
-                if (mask_self) K::template tile<true, false>(buf, j0, gi.eps2, is, ac);
-                else K::template tile<false, false>(buf, j0, gi.eps2, is, ac);
+                if (mask_self) K::template tile<true, false, S>(buf, j0, gi.eps2, is, ac, sl);
+                else K::template tile<false, false, S>(buf, j0, gi.eps2, is, ac, sl);
             }
         } else {
-            if (mask_self) K::template tile<true>(buf, j0, gi.eps2, is, ac);
-            else K::template tile<false>(buf, j0, gi.eps2, is, ac);
+            if (mask_self) K::template tile<true, S>(buf, j0, gi.eps2, is, ac, sl);
+            else K::template tile<false, S>(buf, j0, gi.eps2, is, ac, sl);
         }
         __syncwarp();
         if (t + K::STAGES < t1) {
@@ -921,6 +937,13 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
             TV v[IT][NV];
 #pragma unroll
             for (int q = 0; q < IT; ++q) K::values(ac[q], v[q]);
+            // the S slices of each i, summed in a fixed butterfly order
+#pragma unroll
+            for (int o = IW; o < 32; o <<= 1)
+#pragma unroll
+                for (int q = 0; q < IT; ++q)
+#pragma unroll
+                    for (int c = 0; c < NV; ++c) tree_xor(v[q][c], o);
             const int64_t key = wf + g;
             int64_t kk = wl - wf + 1;  // entries at this level
             int64_t r = w - wf;        // my entry at this level
@@ -928,11 +951,13 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
             bool final_here = true;
             for (int level = 0; kk > 1; ++level) {
                 const size_t mine = (size_t)(key + r * stride) * NV * GI;
+                if (sl == 0) {
 #pragma unroll
-                for (int q = 0; q < IT; ++q)
+                    for (int q = 0; q < IT; ++q)
 #pragma unroll
-                    for (int c = 0; c < NV; ++c)
-                        tree_store(f.scratch, mine + c * GI + q * 32 + lane, v[q][c]);
+                        for (int c = 0; c < NV; ++c)
+                            tree_store(f.scratch, mine + c * GI + q * IW + ir, v[q][c]);
+                }
                 __threadfence();
                 __syncwarp();
                 const int64_t chunk = r / RB;
@@ -953,11 +978,12 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
                 // every value still sums its entries in ascending order.
 #pragma unroll
                 for (int q = 0; q < IT; ++q) {
+                    if (sl != 0) break;  // only slice 0 carries the sums on
 #pragma unroll
                     for (int c = 0; c < NV; ++c) tree_zero(v[q][c]);
 #pragma unroll 4
                     for (int64_t u = 0; u < cs; ++u) {
-                        const size_t e = (size_t)(key + (first + u) * stride) * NV * GI + q * 32 + lane;
+                        const size_t e = (size_t)(key + (first + u) * stride) * NV * GI + q * IW + ir;
                         TV x[NV];
 #pragma unroll
                         for (int c = 0; c < NV; ++c) tree_load(f.scratch, e + c * GI, x[c]);
@@ -969,10 +995,10 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
                 kk = (kk + RB - 1) / RB;
                 stride *= RB;
             }
-            if (final_here) {
+            if (final_here && sl == 0) {
 #pragma unroll
                 for (int q = 0; q < IT; ++q) {
-                    const int64_t a = gi.act_begin + q * 32 + lane;
+                    const int64_t a = gi.act_begin + q * IW + ir;
                     if (a < gi.act_begin + gi.act_count) {
                         double o[NV];
 #pragma unroll
@@ -997,34 +1023,40 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
 // ---------------------------------------------------------------------------
 namespace {
 
-template <class K, int IT>
+template <class K, int IT, int S>
 const void* kfn(bool ens)
 {
-    return ens ? reinterpret_cast<const void*>(&force_kernel<K, IT, ClusterPlan>)
-               : reinterpret_cast<const void*>(&force_kernel<K, IT, UniformPlan>);
+    return ens ? reinterpret_cast<const void*>(&force_kernel<K, IT, S, ClusterPlan>)
+               : reinterpret_cast<const void*>(&force_kernel<K, IT, S, UniformPlan>);
 }
 
-const void* kernel_ptr(Prec p, int it, bool ens = false)
+// One i per lane with any j split; two i per lane without one.
+template <class K1, class K2>
+const void* kfn_split(int it, int split, bool ens)
+{
+    if (it == 1) {
+        switch (split) {
+        case 1: return kfn<K1, 1, 1>(ens);
+        case 2: return kfn<K1, 1, 2>(ens);
+        case 4: return kfn<K1, 1, 4>(ens);
+        case 8: return kfn<K1, 1, 8>(ens);
+        }
+        return nullptr;
+    }
+    if constexpr (!std::is_same<K2, void>::value)
+        if (it == 2 && split == 1) return kfn<K2, 2, 1>(ens);
+    return nullptr;
+}
+
+const void* kernel_ptr(Prec p, int it, int split, bool ens = false)
 {
     switch (p) {
-    case Prec::FP64:
-        if (it == 1) return kfn<PolicyFP64<1>, 1>(ens);
-        return nullptr;
-    case Prec::MIXED:
-        if (it == 1) return kfn<PolicyMixed<1>, 1>(ens);
-        if (it == 2) return kfn<PolicyMixed<2>, 2>(ens);
-        return nullptr;
+    case Prec::FP64: return kfn_split<PolicyFP64<1>, void>(it, split, ens);
+    case Prec::MIXED: return kfn_split<PolicyMixed<1>, PolicyMixed<2>>(it, split, ens);
     case Prec::MIXED_SPJ:
-        if (it == 1) return kfn<PolicyMixed<1, true>, 1>(ens);
-        if (it == 2) return kfn<PolicyMixed<2, true>, 2>(ens);
-        return nullptr;
-    case Prec::DS:
-        if (it == 1) return kfn<PolicyDS<1>, 1>(ens);
-        return nullptr;
-    case Prec::HYBRID:
-        if (it == 1) return kfn<PolicyHybrid<1>, 1>(ens);
-        if (it == 2) return kfn<PolicyHybrid<2>, 2>(ens);
-        return nullptr;
+        return kfn_split<PolicyMixed<1, true>, PolicyMixed<2, true>>(it, split, ens);
+    case Prec::DS: return kfn_split<PolicyDS<1>, void>(it, split, ens);
+    case Prec::HYBRID: return kfn_split<PolicyHybrid<1>, PolicyHybrid<2>>(it, split, ens);
     }
     return nullptr;
 }
@@ -1067,12 +1099,12 @@ size_t force_smem_bytes(Prec p)
     return 0;
 }
 
-bool force_variant_exists(Prec p, int it) { return kernel_ptr(p, it) != nullptr; }
+bool force_variant_exists(Prec p, int it, int split) { return kernel_ptr(p, it, split) != nullptr; }
 
-cudaError_t force_setup(Prec p, int it)
+cudaError_t force_setup(Prec p, int it, int split)
 {
     for (int e = 0; e < 2; ++e) {
-        const void* fn = kernel_ptr(p, it, e == 1);
+        const void* fn = kernel_ptr(p, it, split, e == 1);
         if (!fn) return cudaErrorInvalidValue;
         const cudaError_t r = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    static_cast<int>(force_smem_bytes(p)));
@@ -1081,9 +1113,9 @@ cudaError_t force_setup(Prec p, int it)
     return cudaSuccess;
 }
 
-int force_ctas_per_sm(Prec p, int it)
+int force_ctas_per_sm(Prec p, int it, int split)
 {
-    const void* fn = kernel_ptr(p, it);
+    const void* fn = kernel_ptr(p, it, split);
     if (!fn) return 0;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, FORCE_WARPS * 32,
@@ -1101,7 +1133,7 @@ size_t force_scratch_doubles(int it, int64_t n_act_max, int warps)
 
 int64_t force_counter_stride(int64_t n_act_max, int warps)
 {
-    return warps + (n_act_max + 31) / 32;  // groups are at least 32 wide
+    return warps + (n_act_max + 3) / 4;  // groups are at least 32 / 8 wide
 }
 
 int64_t force_counter_entries(int64_t n_act_max, int warps)
@@ -1111,7 +1143,7 @@ int64_t force_counter_entries(int64_t n_act_max, int warps)
 
 cudaError_t force_launch(const ForceArgs& a, cudaStream_t s)
 {
-    const void* fn = kernel_ptr(a.prec, a.it, a.plan.grp_tile0 != nullptr);
+    const void* fn = kernel_ptr(a.prec, a.it, a.split, a.plan.grp_tile0 != nullptr);
     if (!fn || a.grid <= 0) return cudaErrorInvalidValue;
     ForceParams f;
     f.jl0 = a.jl.arr[0];

@@ -217,6 +217,19 @@ __device__ __forceinline__ void tree_load(const double* base, size_t k, DSPair& 
     const float2 v = __ldcg(reinterpret_cast<const float2*>(base) + k);
     x.h = v.x, x.l = v.y;
 }
+// a += the same value of the lane lane ^ o (butterfly step; the sum is the
+// same in both lanes, since the addition of two values is symmetric)
+__device__ __forceinline__ void tree_xor(double& a, int o)
+{
+    tree_add(a, __shfl_xor_sync(0xffffffffu, a, o));
+}
+__device__ __forceinline__ void tree_xor(DSPair& a, int o)
+{
+    DSPair b;
+    b.h = __shfl_xor_sync(0xffffffffu, a.h, o);
+    b.l = __shfl_xor_sync(0xffffffffu, a.l, o);
+    tree_add(a, b);
+}
 __device__ __forceinline__ double tree_value(double x) { return x; }
 __device__ __forceinline__ double tree_value(DSPair x)
 {

@@ -121,6 +121,7 @@ struct ForcePlan {
 struct ForceArgs {
     Prec prec = Prec::MIXED;
     int it = 1;          // i particles per thread (register blocking)
+    int split = 1;       // lanes per i: the j split inside a warp (1, 2, 4, 8)
     JLayout jl;
     int64_t n = 0;       // real particles (index validation)
     int64_t n_pad = 0;   // j count incl. ghosts, multiple of TJ
@@ -149,10 +150,10 @@ struct ForceArgs {
     double eta = 0.0;
 };
 
-cudaError_t force_setup(Prec p, int it);  // one-time attribute setup
-int force_ctas_per_sm(Prec p, int it);
+cudaError_t force_setup(Prec p, int it, int split);  // one-time attribute setup
+int force_ctas_per_sm(Prec p, int it, int split);
 size_t force_smem_bytes(Prec p);
-bool force_variant_exists(Prec p, int it);
+bool force_variant_exists(Prec p, int it, int split);
 // Scratch needed for n_act_max active particles with `warps` persistent warps.
 size_t force_scratch_doubles(int it, int64_t n_act_max, int warps);
 // Arrival counters of the split-group reduction tree: stride per level and

@@ -111,11 +111,11 @@ nb_status setup_device(int dev, DeviceSetup*& out)
     if (!s.ready) {
         void* addr = nullptr;
         if (cudaGetSymbolAddress(&addr, nb_static_scratch) != cudaSuccess) return NB_ECUDA;
-        if (nb::force_setup(nb::Prec::DS, 1) != cudaSuccess) return NB_ECUDA;
+        if (nb::force_setup(nb::Prec::DS, 1, 1) != cudaSuccess) return NB_ECUDA;
         int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return NB_ECUDA;
-        int per_sm = nb::force_ctas_per_sm(nb::Prec::DS, 1);
+        int per_sm = nb::force_ctas_per_sm(nb::Prec::DS, 1, 1);
         if (per_sm < 1) return NB_ECUDA;
         if (per_sm > STATIC_CTAS_PER_SM) per_sm = STATIC_CTAS_PER_SM;
         s.base = static_cast<unsigned char*>(addr);

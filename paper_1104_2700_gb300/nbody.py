@@ -35,6 +35,7 @@ class NbConfig(ctypes.Structure):
         ("i_per_thread", c_int32),
         ("ctas_per_sm", c_int32),
         ("autotune", c_int32),
+        ("j_split", c_int32),
         ("wait_limit_cycles", c_int64),
     ]
 
@@ -46,6 +47,8 @@ class NbTuning(ctypes.Structure):
         ("large_i_per_thread", c_int32),
         ("large_ctas_per_sm", c_int32),
         ("nact_split", c_int32),
+        ("small_j_split", c_int32),
+        ("large_j_split", c_int32),
         ("small_us", c_double),
         ("large_us", c_double),
     ]
@@ -272,7 +275,7 @@ class Context:
 
     def __init__(self, precision="hybrid", device=0, G=1.0, eta_start=0.01,
                  dt_max=1.0 / 16, dt_min=2.0 ** -40, stream=None, i_per_thread=0,
-                 ctas_per_sm=0, autotune=False, wait_limit_cycles=0):
+                 ctas_per_sm=0, autotune=False, wait_limit_cycles=0, j_split=0):
         cfg = nb_config_init()
         cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         cfg.device = int(device)
@@ -285,6 +288,7 @@ class Context:
         cfg.i_per_thread = int(i_per_thread)
         cfg.ctas_per_sm = int(ctas_per_sm)
         cfg.autotune = int(bool(autotune))
+        cfg.j_split = int(j_split)
         cfg.wait_limit_cycles = int(wait_limit_cycles)
         self.cfg = cfg
         self.handle = nb_create(cfg)

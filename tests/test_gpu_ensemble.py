@@ -32,12 +32,15 @@ def _rel(x, ref):
     return np.linalg.norm(x - ref, axis=1) / np.linalg.norm(ref, axis=1)
 
 
+@pytest.mark.parametrize("split", [1, 4, 8])
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("ds", 1e-9), ("hybrid", 1e-6)])
-def test_ensemble_force_equals_each_system_alone(gpu, orc, prec, tol):
+def test_ensemble_force_equals_each_system_alone(gpu, orc, prec, tol, split):
+    """split: lanes per i (the j split inside a warp), so groups of 32 / split
+    active particles and their partial sums added by warp shuffles."""
     sizes = [100, 333, 1000, 64, 2049, 1]
     off, m, r, v, eps = _systems(sizes, 300)
     n = off[-1]
-    with gpu.Context(prec) as ctx:
+    with gpu.Context(prec, j_split=split) as ctx:
         ctx.set_ensemble(off, m, r, v, eps, 0.02)
         assert gpu.nb_num_systems(ctx.handle) == len(sizes)
         ctx.predict(0.0)

@@ -118,6 +118,51 @@ def test_force_ds_within_1e6_per_particle(gpu, orc, n, n_act, eps):
     assert np.all(np.linalg.norm(jerk - j0, axis=1) <= 1e-10 * sj)
 
 
+@pytest.mark.parametrize("split", [2, 4, 8])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "ds", "hybrid"])
+@pytest.mark.parametrize("n,n_act,eps", [(1000, 37, 4 / 1000), (3001, 3001, 4 / 3001),
+                                         (3001, 129, 0.0), (64, 5, 1 / 64)])
+def test_force_j_split_within_warp(gpu, orc, prec, split, n, n_act, eps):
+    """The j split inside a warp: `split` lanes share each i, lane slice s
+    taking tile slots s, s + split, ...; the slices' partial sums are added by
+    warp shuffles before the split-group tree.  Same bounds as the unsplit
+    kernel (every group size, ragged blocks, the self pair at eps = 0)."""
+    m, r, v = ics.plummer(n, 500 + n)
+    idx = ics.permutation(n, 9)[:n_act].astype(np.int32)
+    z = np.zeros((n, 3))
+    a0, j0, p0 = orc.force(m, r, v, eps, idx=idx, nthreads=NTHREADS)
+    if prec == "hybrid":  # its near test reads the particles' own a, j
+        aa, jj, _ = orc.force(m, r, v, eps, nthreads=NTHREADS)
+    else:
+        aa, jj = z, z
+    with gpu.Context(prec, j_split=split) as ctx:
+        ctx.set_state(m, r, v, aa, jj, np.zeros(n), np.full(n, 1.0 / 16), eps=eps, eta=0.02)
+        ctx.predict(0.0)
+        acc, jerk, pot = ctx.force(idx)
+    sa, sj, sp = _magnitude_sums(m, r, v, eps, idx)
+    ea = np.linalg.norm(acc - a0, axis=1)
+    ej = np.linalg.norm(jerk - j0, axis=1)
+    ep = np.abs(pot - p0)
+    if prec == "fp64":
+        assert _rel(acc, a0).max() < 1e-10 and _rel(jerk, j0).max() < 1e-10
+    elif prec == "ds":
+        assert np.all(ea <= 1e-10 * sa) and np.all(ej <= 1e-10 * sj)
+    elif prec == "hybrid":
+        assert _rel(acc, a0).max() < 1e-6 and _rel(jerk, j0).max() < 1e-6
+        assert (ep / np.abs(p0)).max() < 1e-6
+    else:
+        assert np.all(ea <= 8 * U32 * sa) and np.all(ej <= 16 * U32 * sj)
+        assert np.all(ep <= 8 * U32 * sp)
+
+
+def test_force_j_split_rejects_bad_values(gpu):
+    for bad in (3, 16, -1):
+        with pytest.raises(gpu.NbError):
+            gpu.Context("hybrid", j_split=bad)
+    with pytest.raises(gpu.NbError):  # two i per lane has no j split
+        gpu.Context("mixed", j_split=4, i_per_thread=2)
+
+
 def test_force_self_exclusion_coincident_particles(gpu, orc):
     """Two particles at one point (eps > 0) still attract; the self pair does not."""
     m = np.array([0.3, 0.5, 0.2])
