@@ -67,6 +67,9 @@ def parse_args():
     p.add_argument("--profile", choices=["mixed", "hybrid", "ds", "fp64"], default=None,
                    help="only run --launches force launches (for ncu), no timing")
     p.add_argument("--profile-nact", type=int, default=16384)
+    p.add_argument("--profile-shape", default="0,0,0",
+                   help="i per thread, j split, CTAs per SM of the profiled launch "
+                        "(0 = the default)")
     p.add_argument("--launches", type=int, default=3)
     p.add_argument("--integrate", choices=sorted(INTEGRATIONS), default=None,
                    help="instead of the sweep: integrate one workload in --modes "
@@ -93,10 +96,12 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_metric(prec, key="traffic_bytes_per_launch"):
+def profiled_metric(prec, key="traffic_bytes_per_launch", shape=None):
     """A figure of the force launch at n_act = N from the committed ncu summary
     (DRAM bytes per launch, thread instructions per interaction), or None when
-    the kernel sources changed since it was captured."""
+    the kernel sources changed since it was captured or it was captured with
+    another kernel shape (i per thread, j split) than `shape`; the CTAs per SM
+    only change how far the j range splits over warps."""
     import re
     path = os.path.join(ROOT, "profiles", f"force_{prec}_n16384.md")
     if not os.path.exists(path):
@@ -106,6 +111,10 @@ def profiled_metric(prec, key="traffic_bytes_per_launch"):
     t = re.search(key + r":\s*([0-9.]+)", text)
     if not h or not t or h.group(1) != kernel_source_hash():
         return None
+    if shape is not None:
+        sh = re.search(r"launch_shape:\s*([0-9]+),([0-9]+),([0-9]+)", text)
+        if not sh or tuple(int(x) for x in sh.groups())[:2] != tuple(shape)[:2]:
+            return None
     return float(t.group(1))
 
 
@@ -118,7 +127,8 @@ def run_profile(args):
     n, eps = WL.n, WL.eps
     m, r, v = WL.particles()
     idx = torch.from_numpy(ics.permutation(n, WL.seed)[:args.profile_nact].astype(np.int32)).cuda()
-    with nbody.Context(args.profile) as ctx:
+    it, split, cps = (int(x) for x in args.profile_shape.split(","))
+    with nbody.Context(args.profile, i_per_thread=it, j_split=split, ctas_per_sm=cps) as ctx:
         # loading evaluates every force once (the launch ncu skips with -s 1)
         # and leaves a, j in the state for the hybrid near-pair test
         ctx.set_particles(m, r, v, eps, WL.eta)
@@ -127,7 +137,7 @@ def run_profile(args):
             ctx.force(idx)
         ctx.synchronize()
     print(json.dumps({"profile": args.profile, "n": n, "n_act": args.profile_nact,
-                      "launches": args.launches}))
+                      "launches": args.launches, "shape": [it, split, cps]}))
 
 
 # --- distributed plumbing -------------------------------------------------------
@@ -443,9 +453,20 @@ def run_ours(args):
     except nbody.NbError as exc:
         meas["error"] = str(exc)
 
+    def large_shape(p):
+        t = modes[p].get("autotuned_launch") or {}
+        return (t.get("large_i_per_thread", 1), t.get("large_j_split", 1),
+                t.get("large_ctas_per_sm", 0))
+
+    def kernel_name(p):
+        it, split, cps = large_shape(p)
+        pol = {"mixed": "Mixed", "ds": "DS", "hybrid": "Hybrid", "fp64": "FP64"}[p]
+        return (f"force_kernel<Policy{pol}<{it}>, IT={it}, j_split={split}, UniformPlan> "
+                f"({cps} CTAs/SM)")
+
     def roofline_of(p, kernel):
         ach = FLOPS_PER_INTERACTION * modes[p]["force_interactions_per_s"] / 1e12
-        ipi = profiled_metric(p, "thread_instructions_per_interaction")
+        ipi = profiled_metric(p, "thread_instructions_per_interaction", large_shape(p))
         issue = None
         if ipi:
             # one warp instruction per clock per SM sub-partition (4 per SM)
@@ -461,12 +482,15 @@ def run_ours(args):
                     "frac": (ach / pk) if pk else None, "kernel": kernel, "peak_basis": basis,
                     "launch_ms": modes[p]["force_launch_ms_nact_N"], "issue": issue}
         return {"bound": "alu", "achieved": ach, "peak": peak32, "unit": "TFLOP/s",
-                "frac": ach / peak32, "traffic": profiled_metric(p), "kernel": kernel,
+                "frac": ach / peak32, "traffic": profiled_metric(p, shape=large_shape(p)),
+                "kernel": kernel,
                 "peak_measured": meas.get("fp32"),
                 "frac_of_measured": (ach / meas["fp32"]) if meas.get("fp32") else None,
                 "issue": issue,
                 "traffic_source": f"profiles/force_{p}_n16384.md (ncu, kernel source "
-                                  f"hash {kernel_source_hash()}; null if the kernel changed)",
+                                  f"hash {kernel_source_hash()}, launch shape "
+                                  f"{','.join(str(x) for x in large_shape(p))}; null if the "
+                                  f"kernel source or its i-tile / j split differs)",
                 "algorithmic_bytes_per_launch": n * {"mixed": 40, "ds": 64, "hybrid": 64,
                                                      "fp64": 64}[p],
                 "launch_ms": modes[p]["force_launch_ms_nact_N"],
@@ -475,13 +499,10 @@ def run_ours(args):
                               f"run's FFMA-chain throughput); "
                               f"60 flop per interaction (paper convention)"}
 
-    kname = {"mixed": "force_kernel<PolicyMixed<2>,2>", "ds": "force_kernel<PolicyDS<1>,1>",
-             "hybrid": "force_kernel<PolicyHybrid<1>,1>",
-             "fp64": "force_kernel<PolicyFP64<1>,1>"}
-    roofline = roofline_of(head, kname[head])
-    roofline_mixed = roofline_of("mixed", kname["mixed"]) if "mixed" in modes else None
+    roofline = roofline_of(head, kernel_name(head))
+    roofline_mixed = roofline_of("mixed", kernel_name("mixed")) if "mixed" in modes else None
     if "fp64" in modes:
-        modes["fp64"]["roofline"] = roofline_of("fp64", kname["fp64"])
+        modes["fp64"]["roofline"] = roofline_of("fp64", kernel_name("fp64"))
 
     # End to end through the public API with host buffers: every step copies
     # the state in from pinned host memory and the corrected state back out.
@@ -612,7 +633,7 @@ def extra_measurements(nbody, torch, dev, stream, world, peak32):
     for prec in ("hybrid", "ds"):
         with nbody.Context(prec, device=dev.index, stream=stream) as ctx:
             ctx.set_ensemble(off, ms, rs, vs, eps, ics.ENSEMBLE_K256["eta"])
-            ctx.autotune()
+            tun = ctx.autotune()
             ctx.set_ensemble(off, ms, rs, vs, eps, ics.ENSEMBLE_K256["eta"])
             torch.cuda.synchronize(dev)
             w0 = time.perf_counter()
@@ -621,7 +642,8 @@ def extra_measurements(nbody, torch, dev, stream, world, peak32):
             w = time.perf_counter() - w0
             ens[prec] = {"value": world * inter / w, "unit": UNIT, "block_steps": int(steps),
                          "interactions": int(inter), "wall_s": w,
-                         "us_per_block_step": 1e6 * w / max(steps, 1)}
+                         "us_per_block_step": 1e6 * w / max(steps, 1),
+                         "autotuned_launch": tun}
     out["ensemble_k256"] = ens
     # Precision ablation of the integration (Sec. 4 measures energy error
     # against step count in mixed and DP): block steps, smallest timestep and

@@ -128,9 +128,10 @@ typedef struct nb_tuning {
 } nb_tuning;
 
 /* Autotuner: time every candidate launch shape of the force kernel on the
- * loaded system (probe blocks of 32 and 256 particles for "small", 2048 and
- * min(n, 16384) for "large"; the first particles by index) and keep the
- * fastest for each bucket.  Predicts all particles to the time of particle
+ * loaded system (probe blocks of 32, 256, 2048 and min(n, 16384) particles,
+ * the first by index) and keep the fastest for each bucket, with the bucket
+ * boundary nact_split at 1024 (probes 32 and 256 small) or 4096 (2048 small
+ * too), whichever gives the least total.  Predicts all particles to the time of particle
  * 0 first, so call nb_predict again before nb_force.  *out (may be NULL)
  * receives the choice.  Blocks.  Errors: NB_ESTATE (nothing loaded),
  * NB_ECUDA. */

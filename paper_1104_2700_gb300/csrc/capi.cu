@@ -1125,31 +1125,46 @@ nb_status nb_autotune(nb_ctx* c, nb_tuning* out)
     cudaEventDestroy(e1);
     if (st != NB_OK) return st;
     if ((s = check_status(c)) != NB_OK) return s;
-    // best shape per bucket; ties go to the smaller grid (listed first).  An
-    // ensemble's plan is cut once per block for both variants, so there the
-    // two share the (i per thread, j split) with the least total time.
-    auto best_of = [&](int b, int it, int split) {
+    // Best shape per bucket; ties go to the smaller grid (listed first).  The
+    // small bucket holds the probes below the split (two or three of them:
+    // nact_split 1024 or 4096), the large one the rest.  An ensemble's plan
+    // is cut once per block for both variants, so there the two share the
+    // (i per thread, j split) with the least total time.
+    auto bucket_us = [](const Cand& cd, int lo, int hi) {
+        double t = 0.0;
+        for (int q = lo; q < hi; ++q) t += cd.us[q];
+        return t;
+    };
+    auto best_of = [&](int lo, int hi, int it, int split) {
         const Cand* bc = nullptr;
         for (const auto& cd : cands) {
             if (it > 0 && (cd.it != it || cd.split != split)) continue;
-            if (!bc || cd.us[2 * b] + cd.us[2 * b + 1] < bc->us[2 * b] + bc->us[2 * b + 1]) bc = &cd;
+            if (!bc || bucket_us(cd, lo, hi) < bucket_us(*bc, lo, hi)) bc = &cd;
         }
         return bc;
     };
-    const Cand* best[2] = {best_of(0, 0, 0), best_of(1, 0, 0)};
-    if (c->ens) {
-        double tbest = -1.0;
-        for (const auto& sh : shapes) {
-            const Cand* b0 = best_of(0, sh.first, sh.second);
-            const Cand* b1 = best_of(1, sh.first, sh.second);
-            if (!b0 || !b1) continue;
-            const double tot = b0->us[0] + b0->us[1] + b1->us[2] + b1->us[3];
-            if (tbest < 0.0 || tot < tbest) best[0] = b0, best[1] = b1, tbest = tot;
+    const Cand* best[2] = {nullptr, nullptr};
+    int split_probe = 2;
+    double tbest = -1.0;
+    for (int sp : {2, 3}) {  // probes [0, sp) are "small"
+        const Cand* b[2] = {best_of(0, sp, 0, 0), best_of(sp, 4, 0, 0)};
+        if (c->ens) {
+            b[0] = b[1] = nullptr;
+            double tsh = -1.0;
+            for (const auto& sh : shapes) {
+                const Cand* b0 = best_of(0, sp, sh.first, sh.second);
+                const Cand* b1 = best_of(sp, 4, sh.first, sh.second);
+                if (!b0 || !b1) continue;
+                const double tot = bucket_us(*b0, 0, sp) + bucket_us(*b1, sp, 4);
+                if (tsh < 0.0 || tot < tsh) b[0] = b0, b[1] = b1, tsh = tot;
+            }
         }
+        const double tot = bucket_us(*b[0], 0, sp) + bucket_us(*b[1], sp, 4);
+        if (tbest < 0.0 || tot < tbest) best[0] = b[0], best[1] = b[1], split_probe = sp, tbest = tot;
     }
     c->var[0] = {best[0]->it, best[0]->cps * c->num_sms, best[0]->split};
     c->var[1] = {best[1]->it, best[1]->cps * c->num_sms, best[1]->split};
-    c->nact_split = 1024;
+    c->nact_split = split_probe == 2 ? 1024 : 4096;
     drop_graph(c);
     c->last_force_n_act = -1;
     if (out) {
@@ -1160,8 +1175,8 @@ nb_status nb_autotune(nb_ctx* c, nb_tuning* out)
         out->nact_split = c->nact_split;
         out->small_j_split = best[0]->split;
         out->large_j_split = best[1]->split;
-        out->small_us = best[0]->us[0] + best[0]->us[1];
-        out->large_us = best[1]->us[2] + best[1]->us[3];
+        out->small_us = bucket_us(*best[0], 0, split_probe);
+        out->large_us = bucket_us(*best[1], split_probe, 4);
     }
     return NB_OK;
 }
