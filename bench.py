@@ -877,6 +877,27 @@ def run_integration(args):
                 "value": inter / wall, "log2_min_dt": float(np.log2(st["dt"].min())),
                 "mean_steps_per_particle": inter / wl.n / wl.n,
                 "rel_energy_drift": abs((k1 + w1) - (k0 + w0)) / abs(k0 + w0)}
+            if prec != "fp64":
+                # every particle's force at the evolved (synchronised) state, in
+                # this mode as the integration would evaluate it next, against
+                # the FP64 path on the same state
+                idx = np.arange(wl.n, dtype=np.int32)
+                ctx.predict(t_end)
+                acc, jerk, pot = ctx.force(idx)
+                with nbody.Context("fp64") as ref:
+                    ref.set_state(m, st["r"], st["v"], st["a"], st["j"], st["t"], st["dt"],
+                                  wl.eps, wl.eta)
+                    ref.predict(t_end)
+                    a64, j64, p64 = ref.force(idx)
+                ea = np.linalg.norm(acc - a64, axis=1) / np.linalg.norm(a64, axis=1)
+                ej = np.linalg.norm(jerk - j64, axis=1) / np.linalg.norm(j64, axis=1)
+                ep = np.abs(pot - p64) / np.abs(p64)
+                out["modes"][prec]["force_error_at_t_end"] = {
+                    "particles": int(wl.n), "acc_rel_max": float(ea.max()),
+                    "acc_rel_p50": float(np.median(ea)), "jerk_rel_max": float(ej.max()),
+                    "jerk_rel_p50": float(np.median(ej)), "pot_rel_max": float(ep.max()),
+                    "n_above_1e-6": int(np.sum((ea > 1e-6) | (ej > 1e-6) | (ep > 1e-6))),
+                    "reference": "FP64 GPU path on the same state"}
         print(json.dumps({"partial": prec, **out["modes"][prec]}), file=sys.stderr, flush=True)
     if wl.n <= 4096:
         from oracle import oracle

@@ -115,3 +115,26 @@ def test_force_large_n_sampled_hybrid(gpu, orc, wl):
     err = max(_rel(acc, a0).max(), _rel(jerk, j0).max(),
               (np.abs(pot - p0) / np.abs(p0)).max())
     assert err < 1e-6, err
+
+
+def test_hybrid_force_after_integration_n65536(gpu, orc):
+    """The N = 65536 Plummer workload (eps = 4/N) integrated in HYBRID to
+    t = 1/16: every particle's force at that evolved state, evaluated as the
+    integration's next step would (its own a, j and guard states), against the
+    oracle on the same state.  Checks the 1e-6 bound away from the initial
+    conditions the other full-size tests use."""
+    wl = ics.MIXED_N64K
+    m, r, v = wl.particles()
+    t_end = 1.0 / 16
+    idx = np.arange(wl.n, dtype=np.int32)
+    with gpu.Context("hybrid") as ctx:
+        ctx.set_particles(m, r, v, wl.eps, wl.eta)
+        ctx.step_until(t_end)
+        st = ctx.get_state()
+        assert np.all(st["t"] == t_end)
+        ctx.predict(t_end)
+        acc, jerk, pot = ctx.force(idx)
+    a0, j0, p0 = orc.force(m, st["r"], st["v"], wl.eps, idx=idx, nthreads=NTHREADS)
+    assert _rel(acc, a0).max() < 1e-6
+    assert _rel(jerk, j0).max() < 1e-6
+    assert (np.abs(pot - p0) / np.abs(p0)).max() < 1e-6
