@@ -23,6 +23,11 @@ struct nb_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // A second stream for the launch variant that sits idle: both variants of
+    // a device-sized block go out as parallel branches (fork on ev_fork, join
+    // on ev_join), so the idle one's launch and exit cost no time in series.
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int num_sms = 0;
     // Force launch variants of the context precision: [0] for blocks with
     // n_act < nact_split, [1] for larger ones (i per thread, persistent CTAs).
@@ -322,6 +327,14 @@ nb_status run_force(nb_ctx* c, Prec p, const nb::JLayout& jl, const int32_t* idx
         NB_CK(c, nb::force_launch(f, c->stream));
         return NB_OK;
     }
+    // With the block size on the device both variants are launched, the
+    // small-block one on the aux stream; exactly one of them does any work,
+    // and neither touches memory the other uses before it has read n_act.
+    const bool fork = n_act_host < 0;
+    if (fork) {
+        NB_CK(c, cudaEventRecord(c->ev_fork, c->stream));
+        NB_CK(c, cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
+    }
     for (int v = 0; v < 2; ++v) {
         f.it = c->var[v].it;
         f.split = c->var[v].split;
@@ -329,7 +342,11 @@ nb_status run_force(nb_ctx* c, Prec p, const nb::JLayout& jl, const int32_t* idx
         f.nact_lo = v == 0 ? 0 : c->nact_split;
         f.nact_hi = v == 0 ? c->nact_split : 0x7fffffff;
         if (n_act_host >= 0 && (n_act_host < f.nact_lo || n_act_host >= f.nact_hi)) continue;
-        NB_CK(c, nb::force_launch(f, c->stream));
+        NB_CK(c, nb::force_launch(f, (fork && v == 0) ? c->aux : c->stream));
+    }
+    if (fork) {
+        NB_CK(c, cudaEventRecord(c->ev_join, c->aux));
+        NB_CK(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0));
     }
     return NB_OK;
 }
@@ -577,6 +594,10 @@ nb_status nb_create(const nb_config* cfg, nb_ctx** out)
             return bail(NB_ECUDA);
         c->own_stream = true;
     }
+    if (cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)
+        return bail(NB_ECUDA);
     // Default launch shapes (measured on GB300 for N = 16384): one i per
     // thread for small blocks, two for large MIXED blocks; at most 4
     // persistent CTAs per SM.  nb_autotune replaces them by measurement.
@@ -619,6 +640,9 @@ nb_status nb_destroy(nb_ctx* c)
     if (c->st.bound) cudaFree(c->st.bound);
     if (c->ctr64) cudaFree(c->ctr64);
     if (c->pinned) cudaFreeHost(c->pinned);
+    if (c->aux) cudaStreamSynchronize(c->aux), cudaStreamDestroy(c->aux);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
     return NB_OK;

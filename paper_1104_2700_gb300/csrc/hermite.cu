@@ -446,17 +446,17 @@ __global__ void __launch_bounds__(SEL1_THREADS)
     unsigned long long best = ~0ull;
     uint32_t mask = 0u;
     const int tiles = static_cast<int>((n + SEL1_THREADS - 1) / SEL1_THREADS);  // <= 32
-    // keys in batches of 8 independent loads (one memory round trip each);
+    // keys in batches of 16 independent loads (one memory round trip each);
     // slots past n read as the largest key and never join the mask
-    for (int u0 = 0; u0 < tiles; u0 += 8) {
-        unsigned long long kk[8];
+    for (int u0 = 0; u0 < tiles; u0 += 16) {
+        unsigned long long kk[16];
 #pragma unroll
-        for (int v = 0; v < 8; ++v) {
+        for (int v = 0; v < 16; ++v) {
             const int64_t i = tid + static_cast<int64_t>(SEL1_THREADS) * (u0 + v);
             kk[v] = (u0 + v < tiles && i < n) ? __ldcg(nkey + i) : ~0ull;
         }
 #pragma unroll
-        for (int v = 0; v < 8; ++v) {
+        for (int v = 0; v < 16; ++v) {
             const unsigned long long k = kk[v];
             if (k < best) {
                 best = k;
@@ -769,16 +769,31 @@ __device__ __forceinline__ double norm3_rn(double x, double y, double z)
 // 2^k <= eta sqrt((|a||s| + |j|^2) / (|j||c| + |s|^2)) < 2^(k+1).  That is
 // taken in FP32: each norm after scaling its vector by a power of two
 // (|v| = nrm 2^E, the vector's largest component then in [0.5, 1)), the two
-// sums after aligning their terms' exponents.  About fifteen FP32 roundings
-// leave it within ~1e-6 of the FP64 value, so k is certain unless the value
+// sums after aligning their terms' exponents.  The truncated inputs and about
+// fifteen FP32 roundings leave it within ~2e-6 of the FP64 value, so k is certain unless the value
 // lies within 1e-5 of a power of two; then, or when a vector is zero, tiny or
 // not finite, the function declines and the caller evaluates the formula in
 // FP64 as written.  Either way the timestep chosen is the oracle's.
+// A double truncated to a float from its two 32-bit words (within an ulp; a
+// hardware conversion costs as much as an FP64 operation on GB300); values
+// outside [2^-100, 2^100] become 0 or NaN, which the caller's range test
+// rejects.
+__device__ __forceinline__ float trunc_to_float(double x)
+{
+    const unsigned hw = static_cast<unsigned>(__double2hiint(x));
+    const unsigned lw = static_cast<unsigned>(__double2loint(x));
+    const unsigned e = (hw >> 20) & 0x7ffu;
+    if (((hw & 0x7fffffffu) | lw) == 0u) return 0.f;
+    if (e - (1023u - 100u) > 200u) return __int_as_float(0x7fc00000);  // NaN
+    return __uint_as_float((hw & 0x80000000u) | ((e - 1023u + 127u) << 23) |
+                           ((hw & 0xfffffu) << 3) | (lw >> 29));
+}
+
 __device__ __forceinline__ bool norm3_scaled(const double (&v)[3], float& nrm, int& E)
 {
-    const float f0 = __double2float_rn(v[0]);
-    const float f1 = __double2float_rn(v[1]);
-    const float f2 = __double2float_rn(v[2]);
+    const float f0 = trunc_to_float(v[0]);
+    const float f1 = trunc_to_float(v[1]);
+    const float f2 = trunc_to_float(v[2]);
     const float mx = fmaxf(fabsf(f0), fmaxf(fabsf(f1), fabsf(f2)));
     if (!(mx >= 1e-30f && mx <= 1e30f)) return false;  // NaN fails too
     frexpf(mx, &E);
