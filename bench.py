@@ -9,14 +9,16 @@ steps 1-8 of Sec. 2) for each active-block size n_act in {32, 256, 2048,
 step does identical work.  The active block of size n_act is the first n_act
 particles of a seeded permutation (their dt is 2^-10, everyone else's 2^-4).
 
-Three precision modes run the same timed step: MIXED (the paper's scheme on
-FP32 pipes), DS (double-single pair arithmetic) and FP64.  Each is checked on
-every particle against the FP64 GPU path (itself held within 1e-10 of the
-FP64 CPU oracle by the parity tests); the headline value is acc+jerk
-interactions per second (n_act * N per block step, self pair counted) of the
-fastest mode whose largest relative error in acc, jerk and pot is <= 1e-6.
-The force kernel's roofline, an end-to-end figure through host buffers and
-the CPU oracle baseline are reported on the same JSON line.
+Four precision modes run the same timed step: MIXED (the paper's scheme on
+FP32 pipes), HYBRID (FP32 far pairs, double-single near pairs), DS
+(double-single pair arithmetic) and FP64.  Each is checked on every particle
+against the FP64 GPU path (itself held within 1e-10 of the FP64 CPU oracle by
+the parity tests); the headline value is acc+jerk interactions per second
+(n_act * N per block step, self pair counted) of the fastest mode whose
+largest relative error in acc, jerk and pot is <= 1e-6.  Every mode's launch
+shapes are autotuned on the workload first.  The force kernel's roofline, an
+end-to-end figure through host buffers, the CPU oracle baseline and the
+paper's own mixed-precision CPU loop are reported on the same JSON line.
 
 Under torchrun (--gpus N > 1) every rank runs an independent replica of the
 workload on its own GPU (weak scaling); the timed region is bracketed by a
