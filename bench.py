@@ -847,7 +847,8 @@ def run_integration(args):
     (wall clock around nb_step_until, CUDA-synchronised), the smallest
     timestep reached and the relative energy drift with the FP64 potential
     (Sec. 4 measures the energy error the same way).  For the N = 1024
-    workload the FP64 oracle runs the same integration on the host cores."""
+    workload the FP64 oracle runs the same integration on the host cores as
+    the CPU baseline ("cpu_baseline", kind "oracle")."""
     name, t_default = INTEGRATIONS[args.integrate]
     wl = getattr(ics, name)
     t_end = args.t_end if args.t_end is not None else t_default
@@ -910,7 +911,8 @@ def run_integration(args):
         status = s.run(t_end)
         e1 = s.energy()
         wall = time.perf_counter() - t0
-        out["oracle"] = {"status": int(status), "block_steps": s.n_steps,
+        # the CPU baseline of this workload: the oracle's own integration
+        out["cpu_baseline"] = {"kind": "oracle", "status": int(status), "block_steps": s.n_steps,
                          "interactions": s.n_inter, "wall_s": wall,
                          "value": s.n_inter / wall,
                          "rel_energy_drift": abs(e1 - e0) / abs(e0),
@@ -923,7 +925,8 @@ def run_energy_study(args):
     energy, averaged over the outputs t = k/16 up to 1/8 of a crossing time
     (t = 0.375, as Sec. 4 states it), against the number of steps per
     particle per crossing time (2 sqrt 2), for a range of eta.  The potential is the FP64 one in every
-    mode, so the error is the integration's.  The FP64 oracle runs the same
+    mode, so the error is the integration's.  As the CPU baseline of each row
+    ("cpu_baseline", kind "oracle"), the FP64 oracle runs the same
     integrations on the host cores."""
     import torch
     from paper_1104_2700_gb300 import build as nb_build
@@ -965,9 +968,11 @@ def run_energy_study(args):
         for t in outs:
             s.run(t)
             errs.append(abs(s.energy() - e0) / abs(e0))
-        row["oracle"] = {"n_step": s.n_inter / n / n * crossing / t_end,
-                         "mean_rel_energy_error": float(np.mean(errs)),
-                         "final_rel_energy_error": errs[-1]}
+        # the CPU baseline of each row: the oracle's own integration
+        row["cpu_baseline"] = {"kind": "oracle",
+                               "n_step": s.n_inter / n / n * crossing / t_end,
+                               "mean_rel_energy_error": float(np.mean(errs)),
+                               "final_rel_energy_error": errs[-1]}
         rows.append(row)
         print(json.dumps(row), file=sys.stderr, flush=True)
     print(json.dumps({"study": "energy error vs steps per crossing time (Sec. 4)",
