@@ -81,7 +81,7 @@ struct nb_ctx {
 namespace {
 
 constexpr size_t PINNED_BYTES = 256;
-constexpr int GRAPH_STEPS = 16;  // block steps per replay of the step graph
+constexpr int GRAPH_STEPS = 32;  // block steps per replay of the step graph
 
 void drop_graph(nb_ctx* c)
 {

@@ -35,7 +35,6 @@ __global__ void predict_fp64_kernel(const StateDev st, const JLayout jl, const d
 {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // j-layout slot
     if (q >= st.n_pad) return;
-    if (n_act_dev && *n_act_dev == 0) return;
     const int64_t n = st.n;
     // particle in this slot (-1: a ghost that pads its system to the tile)
     const int64_t i = jsrc ? jsrc[q] : (q < n ? q : -1);
@@ -57,6 +56,9 @@ __global__ void predict_fp64_kernel(const StateDev st, const JLayout jl, const d
         vp[0] = vp[1] = vp[2] = 0.0;
         gm = 0.0;
     }
+    // an empty block step writes nothing (checked after the state loads, so
+    // they need not wait for this one)
+    if (n_act_dev && *n_act_dev == 0) return;
     double2* P = static_cast<double2*>(jl.arr[0]) + 2 * q;
     double2* V = static_cast<double2*>(jl.arr[1]) + 2 * q;
     P[0] = make_double2(xp[0], xp[1]);
@@ -155,10 +157,12 @@ __global__ void predict_ds_kernel(const StateDev st, const JLayout jl, const dou
 {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // j-layout slot
     if (q >= st.n_pad) return;
-    if (n_act_dev && *n_act_dev == 0) return;
     const int64_t n = st.n;
     const int64_t i = jsrc ? jsrc[q] : (q < n ? q : -1);
+    // an empty block step writes nothing; the ghosts' check is cheap, the
+    // particles' comes after their state loads so that they need not wait
     if (i < 0) {  // a ghost: far away, zero mass
+        if (n_act_dev && *n_act_dev == 0) return;
         const float g = static_cast<float>(GHOST_POS);
         if (PREC == static_cast<int>(Prec::MIXED)) {
             static_cast<float4*>(jl.arr[0])[q] = make_float4(g, g, g, 0.f);
@@ -191,6 +195,7 @@ __global__ void predict_ds_kernel(const StateDev st, const JLayout jl, const dou
         grid_split_ds(dsf_fma(h, u, x), qx, iqx, hi[c], lo[c]);
         vp[c] = dsf_fma(h, dsf_fma(h, dsf_scale(j, 0.5f), a), v);
     }
+    if (n_act_dev && *n_act_dev == 0) return;
     if (PREC == static_cast<int>(Prec::MIXED)) {
         static_cast<float4*>(jl.arr[0])[q] = make_float4(hi[0], hi[1], hi[2], __fadd_rn(gm.hi, gm.lo));
         static_cast<float4*>(jl.arr[1])[q] =
