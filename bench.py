@@ -69,6 +69,9 @@ def parse_args():
     p.add_argument("--profile", choices=["mixed", "hybrid", "ds", "fp64"], default=None,
                    help="only run --launches force launches (for ncu), no timing")
     p.add_argument("--profile-nact", type=int, default=16384)
+    p.add_argument("--profile-steps", choices=["sweep", "ensemble"], default=None,
+                   help="only run a few eager HYBRID block steps of the N = 16384 "
+                        "workload or the 256-system ensemble (for ncu), no timing")
     p.add_argument("--profile-shape", default="0,0,0",
                    help="i per thread, j split, CTAs per SM of the profiled launch "
                         "(0 = the default)")
@@ -118,6 +121,27 @@ def profiled_metric(prec, key="traffic_bytes_per_launch", shape=None):
         if not sh or tuple(int(x) for x in sh.groups())[:2] != tuple(shape)[:2]:
             return None
     return float(t.group(1))
+
+
+def run_profile_steps(args):
+    """Load a workload in HYBRID and run eight eager block steps (for ncu
+    captures of the select, predictor and corrector kernels)."""
+    from paper_1104_2700_gb300 import build as nb_build
+    from paper_1104_2700_gb300 import nbody
+    nb_build.build()
+    with nbody.Context("hybrid") as ctx:
+        if args.profile_steps == "ensemble":
+            sizes, off, ms, rs, vs, eps = ics.ensemble()
+            ctx.set_ensemble(off, ms, rs, vs, eps, ics.ENSEMBLE_K256["eta"])
+            n = int(off[-1])
+        else:
+            m, r, v = WL.particles()
+            ctx.set_particles(m, r, v, WL.eps, WL.eta)
+            n = WL.n
+        for _ in range(8):
+            ctx.block_step(1.0)
+        ctx.synchronize()
+    print(json.dumps({"profile_steps": args.profile_steps, "n": n, "block_steps": 8}))
 
 
 def run_profile(args):
@@ -1055,6 +1079,8 @@ def main():
         run_integration(args)
     elif args.profile:
         run_profile(args)
+    elif args.profile_steps:
+        run_profile_steps(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
