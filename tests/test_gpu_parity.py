@@ -102,7 +102,7 @@ def test_force_mixed_within_fp32_bound(gpu, orc, n, n_act, eps):
                                          (4096, 4096, 4 / 4096)])
 def test_force_ds_within_1e6_per_particle(gpu, orc, n, n_act, eps):
     """Double-single pair arithmetic: every particle within 1e-6 relative
-    (the benchmark spec's bound); the arithmetic carries ~44 bits, so the actual
+    (the 1e-6 gate); the arithmetic carries ~44 bits, so the actual
     errors sit near 1e-11 even for particles whose forces nearly cancel."""
     m, r, v = ics.plummer(n, 200 + n)
     idx = ics.permutation(n, 8)[:n_act].astype(np.int32)
