@@ -92,7 +92,9 @@ typedef struct nb_config {
                            * split over 1, 2, 4 or 8 lanes of a warp and the
                            * partial sums are added with warp shuffles (a
                            * group then holds 32 / j_split i); 0 = default 1.
-                           * Only with i_per_thread 1 above 1.            */
+                           * Values above 1 need i_per_thread 0 or 1; any
+                           * other value, or 2 i per thread with a split, is
+                           * NB_EINVAL at nb_create.                        */
     int64_t wait_limit_cycles; /* GPU clock cycles a force kernel waits for
                               * one staged j tile before it gives up and the
                               * call fails with NB_ETIMEOUT; 0 = about one
@@ -131,8 +133,9 @@ typedef struct nb_tuning {
  * loaded system (probe blocks of 32, 256, 2048 and min(n, 16384) particles,
  * the first by index) and keep the fastest for each bucket, with the bucket
  * boundary nact_split at 1024 (probes 32 and 256 small) or 4096 (2048 small
- * too), whichever gives the least total.  Predicts all particles to the time of particle
- * 0 first, so call nb_predict again before nb_force.  *out (may be NULL)
+ * too), whichever gives the least total.  Predicts all particles to the
+ * time of particle 0 first, so call nb_predict again before nb_force.  *out
+ * (may be NULL)
  * receives the choice.  Blocks.  Errors: NB_ESTATE (nothing loaded),
  * NB_ECUDA. */
 nb_status nb_autotune(nb_ctx* ctx, nb_tuning* out);
