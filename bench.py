@@ -93,11 +93,18 @@ def parse_args():
 
 
 def kernel_source_hash():
+    """sha256 (first 16 hex) of the force kernel's code, csrc/force.cu and
+    csrc/nb_device.cuh with comments and whitespace stripped, so that a
+    comment edit does not orphan the ncu summaries taken of the same code."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in ("force.cu", "nb_device.cuh"):
-        with open(os.path.join(ROOT, "paper_1104_2700_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1104_2700_gb300", "csrc", f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -4,12 +4,14 @@
 // force-loop step 3).
 //
 // Work decomposition (GB300-first, not the paper's 2 i x 4 j AVX pairing):
-//   * an i-group is 32*IT consecutive entries of the active list; each lane
-//     of a warp holds IT i particles in registers;
+//   * an i-group is 32*IT/S consecutive entries of the active list; each lane
+//     of a warp holds IT i particles in registers, and S lanes (the j split,
+//     1, 2, 4 or 8) share each i;
 //   * the j particles stream through shared memory in tiles of TJ, staged by
 //     1-D bulk copies (cp.async.bulk) into a STAGES-deep ring owned by the
-//     warp and completed on mbarriers; every lane reads the same j (a
-//     shared-memory broadcast);
+//     warp and completed on mbarriers; lane slice s reads tile slots s,
+//     s + S, ... (a shared-memory broadcast within the slice), and the
+//     slices' partial sums are added by warp shuffles at the end of a group;
 //   * the flattened (i-group, j-tile) space is cut into equal contiguous
 //     ranges, one per persistent warp ("stream-K"), so every warp does the
 //     same number of tiles whatever n_act is.  A group split across several
