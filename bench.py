@@ -47,6 +47,8 @@ from paper_1104_2700_gb300 import ics  # noqa: E402
 METRIC = "acc+jerk interactions/s on 1 GB300, mixed vs FP64, at rel. force err ≤1e-6"
 UNIT = "interactions/s"
 FLOPS_PER_INTERACTION = 60  # the paper's convention (Sec. 5)
+CROSSING_TIME = 2.0 * math.sqrt(2.0)  # one crossing time in N-body units (Sec. 4)
+ENERGY_STUDY_T_END = 0.375  # the span of Sec. 4's energy test, as the paper states it
 NACTS = ics.FORCE_SWEEP_NACT
 WL = ics.FORCE_SWEEP_N16K
 L2_FLUSH_BYTES = 512 << 20
@@ -966,7 +968,7 @@ def run_energy_study(args):
     nb_build.build()
     oracle.build()
     n, seed = 1024, 1
-    eps, t_end, crossing = 4.0 / n, 0.375, 2.0 * math.sqrt(2.0)
+    eps, t_end, crossing = 4.0 / n, ENERGY_STUDY_T_END, CROSSING_TIME
     m, r, v = ics.plummer(n, seed)
     # eta enters Eq. timestep outside the square root (dt = eta (...)^(1/2));
     # the start rule scales with it (eta_start = eta / 4), since a fixed

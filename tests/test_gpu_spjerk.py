@@ -93,3 +93,24 @@ def test_spj_jerk_error_exceeds_compensated_at_large_n(gpu):
     _, js, _ = _forces(gpu, "mixed_spj", m, r, v, eps, idx)
     em, es = np.median(_rel(jm, j0)), np.median(_rel(js, j0))
     assert es > 2.0 * em
+
+
+def test_mixed_accuracy_matches_fig_err_snp(gpu, orc):
+    """MIXED (the paper's scheme on FP32 pipes) against Sec. 4's stated
+    accuracy (tests/golden/paper_figures.json): on Plummer models with eps = 4/N
+    and every particle active, median acceleration errors within a factor of
+    10 of 1e-8, potentials no worse, jerks less accurate than accelerations."""
+    import json
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                           "paper_figures.json")) as fh:
+        typical = json.load(fh)["acc_pot_relative_error_typical"]["value"]
+    for n in (1024, 4096):
+        m, r, v = ics.plummer(n, 11)
+        eps = 4.0 / n
+        idx = np.arange(n, dtype=np.int32)
+        acc, jerk, pot = _forces(gpu, "mixed", m, r, v, eps, idx)
+        a0, j0, p0 = orc.force(m, r, v, eps, idx=idx, nthreads=NTHREADS)
+        acc_med = np.median(_rel(acc, a0))
+        assert typical / 10 < acc_med < typical * 10
+        assert np.median(np.abs(pot - p0) / np.abs(p0)) < typical * 10
+        assert np.median(_rel(jerk, j0)) > acc_med
