@@ -12,8 +12,8 @@ particles of a seeded permutation (their dt is 2^-10, everyone else's 2^-4).
 Four precision modes run the same timed step: MIXED (the paper's scheme on
 FP32 pipes), HYBRID (FP32 far pairs, double-single near pairs), DS
 (double-single pair arithmetic) and FP64.  Each is checked on every particle
-against the FP64 GPU path (itself held within 1e-10 of the FP64 CPU oracle by
-the parity tests); the headline value is acc+jerk interactions per second
+against the FP64 CPU oracle (evaluated by the CPU-baseline leg on rank 0
+before any GPU work); the headline value is acc+jerk interactions per second
 (n_act * N per block step, self pair counted) of the fastest mode whose
 largest relative error in acc, jerk and pot is <= 1e-6.  Every mode's launch
 shapes are autotuned on the workload first.  The force kernel's roofline, an
@@ -95,18 +95,22 @@ def parse_args():
 
 
 def kernel_source_hash():
-    """sha256 (first 16 hex) of the force kernel's code, csrc/force.cu and
-    csrc/nb_device.cuh with comments and whitespace stripped, so that a
-    comment edit does not orphan the ncu summaries taken of the same code."""
+    """sha256 (first 16 hex) of what the force kernel is built from:
+    csrc/force.cu, csrc/nb_device.cuh and csrc/nb_launch.h with comments and
+    whitespace stripped (so that a comment edit does not orphan the ncu
+    summaries taken of the same code), plus force.cu's compiler flags."""
     import hashlib
     import re
+    from paper_1104_2700_gb300 import build as nb_build
     h = hashlib.sha256()
-    for f in ("force.cu", "nb_device.cuh"):
+    for f in ("force.cu", "nb_device.cuh", "nb_launch.h"):
         with open(os.path.join(ROOT, "paper_1104_2700_gb300", "csrc", f)) as fh:
             src = fh.read()
         src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
         src = re.sub(r"//[^\n]*", " ", src)
         h.update(" ".join(src.split()).encode())
+    flags = nb_build.COMMON + nb_build.PER_FILE.get("force.cu", [])
+    h.update(" ".join(x for x in flags if not x.startswith("/")).encode())
     return h.hexdigest()[:16]
 
 
@@ -301,24 +305,20 @@ def run_ours(args):
         ctx.predict(0.0)
         return ctx.force(all_idx)
 
-    # Accuracy reference for every particle: the FP64 GPU path (which the
-    # parity tests hold within 1e-10 of the FP64 CPU oracle on this workload).
-    with nbody.Context("fp64", device=local, stream=stream) as ref_ctx:
-        z3 = np.zeros((n, 3))
-        a_ref, j_ref, p_ref = forces_at_t0(ref_ctx, z3, z3)
+    # Accuracy reference of every gate on the line: the FP64 oracle, run on
+    # rank 0 by the CPU-baseline leg (which also times it) before any GPU work.
+    leg = None
+    if rank == 0:
+        leg = cpu_baseline_leg(m, r, v, eps, args.cpu_seconds,
+                               timed=not args.no_cpu_baseline, extra=not args.no_extra)
+    ref = leg["refs"]["sweep"] if leg else None
 
     def accuracy(ctx):
-        a, j, p = forces_at_t0(ctx, a_ref, j_ref)
-        ea = np.linalg.norm(a - a_ref, axis=1) / np.linalg.norm(a_ref, axis=1)
-        ej = np.linalg.norm(j - j_ref, axis=1) / np.linalg.norm(j_ref, axis=1)
-        ep = np.abs(p - p_ref) / np.abs(p_ref)
-        return {"particles": n,
-                "acc_rel_max": float(ea.max()), "acc_rel_p50": float(np.median(ea)),
-                "acc_rel_p99": float(np.quantile(ea, 0.99)),
-                "jerk_rel_max": float(ej.max()), "jerk_rel_p50": float(np.median(ej)),
-                "jerk_rel_p99": float(np.quantile(ej, 0.99)),
-                "pot_rel_max": float(ep.max()),
-                "n_above_1e-6": int(np.sum((ea > 1e-6) | (ej > 1e-6) | (ep > 1e-6)))}
+        """Every particle of the workload against the oracle (rank 0 only)."""
+        if ref is None:
+            return None
+        a, j, p = forces_at_t0(ctx, ref[0], ref[1])
+        return error_stats((a, j, p), ref)
 
     def measure(precision, steps, warmup):
         ctx = nbody.Context(precision, device=local, stream=stream)
@@ -462,11 +462,16 @@ def run_ours(args):
                        "autotuned_launch": ctx.tuning,
                        "force_interactions_per_s": n * n / t_force,
                        "per_block_size": per_nact,
-                       "accuracy_vs_fp64": acc, "clocks": c}
+                       "accuracy_vs_oracle": acc, "clocks": c}
         contexts[prec] = (ctx, states)
-    gate = {p: max(mo["accuracy_vs_fp64"][q] for q in ("acc_rel_max", "jerk_rel_max",
-                                                          "pot_rel_max")) <= 1e-6
-            for p, mo in modes.items()}
+    gate = None
+    if rank == 0:
+        gate = {p: mo["accuracy_vs_oracle"]["max_rel"] <= 1e-6 for p, mo in modes.items()}
+    if world > 1:
+        import torch.distributed as dist
+        box = [gate]
+        dist.broadcast_object_list(box, src=0)
+        gate = box[0]
     passing = [p for p in modes if gate[p]]
     # fastest mode meeting the gate; if none ran that meets it, the fastest
     # mode (its line then records meets_1e-6_gate = false)
@@ -526,8 +531,8 @@ def run_ours(args):
                                   f"hash {kernel_source_hash()}, launch shape "
                                   f"{','.join(str(x) for x in large_shape(p))}; null if the "
                                   f"kernel source or its i-tile / j split differs)",
-                "algorithmic_bytes_per_launch": n * {"mixed": 40, "ds": 64, "hybrid": 64,
-                                                     "fp64": 64}[p],
+                "algorithmic_bytes_per_launch": algorithmic_bytes(p, n, n),
+                "algorithmic_bytes_basis": ALGO_BYTES_BASIS,
                 "launch_ms": modes[p]["force_launch_ms_nact_N"],
                 "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x "
                               f"{sm_max:.0f} MHz max SM clock (derived; peak_measured is this "
@@ -579,13 +584,13 @@ def run_ours(args):
 
     extra = {}
     if not args.no_extra:
-        extra = extra_measurements(nbody, torch, dev, stream, world, peak32)
+        extra = extra_measurements(nbody, torch, dev, stream, world, peak32,
+                                   leg["refs"] if leg else None)
 
     cpu = cpu_paper = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(m, r, v, eps, args.cpu_seconds)
-        cpu_paper = paper_cpu_baseline(m, r, v, eps, args.cpu_seconds / 2,
-                                       (a_ref, j_ref, p_ref))
+        cpu = leg["cpu"]
+        cpu_paper = paper_cpu_baseline(m, r, v, eps, args.cpu_seconds / 2, ref)
 
     if rank == 0:
         line = {
@@ -601,7 +606,8 @@ def run_ours(args):
                        "l2": "flushed (512 MiB write) between timed steps",
                        "interactions_per_step": inter_per_step,
                        "gflops_60flop": hm["value"] * FLOPS_PER_INTERACTION / 1e9,
-                       "gate": "max over all N particles of rel. err of acc, jerk, pot <= 1e-6"},
+                       "gate": "max over all N particles of rel. err of acc, jerk, pot "
+                               "against the FP64 oracle <= 1e-6"},
             "roofline": roofline,
             "roofline_mixed_kernel": roofline_mixed,
             "modes": modes,
@@ -616,6 +622,42 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
 
 
+def error_stats(got, ref):
+    """Relative errors of (acc, jerk, pot) against a reference (the oracle's):
+    |x - x_ref| / |x_ref| per particle (Sec. 4's error definition)."""
+    a, j, p = got
+    a0, j0, p0 = ref
+    ea = np.linalg.norm(a - a0, axis=1) / np.linalg.norm(a0, axis=1)
+    ej = np.linalg.norm(j - j0, axis=1) / np.linalg.norm(j0, axis=1)
+    ep = np.abs(p - p0) / np.abs(p0)
+    return {"particles": int(len(ea)),
+            "acc_rel_max": float(ea.max()), "acc_rel_p50": float(np.median(ea)),
+            "acc_rel_p99": float(np.quantile(ea, 0.99)),
+            "jerk_rel_max": float(ej.max()), "jerk_rel_p50": float(np.median(ej)),
+            "jerk_rel_p99": float(np.quantile(ej, 0.99)),
+            "pot_rel_max": float(ep.max()),
+            "max_rel": float(max(ea.max(), ej.max(), ep.max())),
+            "n_above_1e-6": int(np.sum((ea > 1e-6) | (ej > 1e-6) | (ep > 1e-6))),
+            "reference": "FP64 CPU oracle"}
+
+
+# Algorithmic DRAM bytes of one force launch: the j layout once (bytes per j
+# record), and per active i its layout record, its index, the state it reads
+# (HYBRID: a, j, dt and the noise estimate for the near test and the guard)
+# and the acc, jerk, pot it writes (HYBRID also its noise estimate).
+J_RECORD_BYTES = {"mixed": 40, "mixed_spj": 40, "ds": 64, "hybrid": 64, "fp64": 64}
+I_BYTES = {"mixed": 40 + 4 + 56, "mixed_spj": 40 + 4 + 56, "ds": 64 + 4 + 56,
+           "fp64": 64 + 4 + 56, "hybrid": 64 + 4 + 64 + 56 + 8}
+ALGO_BYTES_BASIS = ("n_j x j-record bytes (mixed 40, ds/hybrid/fp64 64) + n_act x (i record + "
+                    "4 B index + 56 B acc/jerk/pot written; hybrid also 48 B state a, j + "
+                    "8 B dt + 8 B noise estimate read and 8 B written)")
+
+
+def algorithmic_bytes(prec, n_j, n_act):
+    return n_j * J_RECORD_BYTES[prec] + n_act * I_BYTES[prec]
+
+
+
 # Kernels of one graph-replayed block step of the sweep (N = 16384): the
 # state roll-back (nb_restore), the one-CTA select (systems up to 32768
 # particles), predict, the two force launch variants (each returns at once
@@ -626,59 +668,93 @@ DTYPES = {"ds": "f32x2 (double-single on the FP32 pipes)", "mixed": "f32", "fp64
           "hybrid": "f32 (far pairs) + f32x2 double-single (near pairs)"}
 
 
-def extra_measurements(nbody, torch, dev, stream, world, peak32):
+def extra_measurements(nbody, torch, dev, stream, world, peak32, refs):
     """Context beside the headline (not part of `value`):
-    * the force kernel at N = 65536, n_act = N (the size the FP32-roofline
-      target is stated for), MIXED and DS, CUDA events;
+    * the force kernel at n_act = N for N = 65536 (Plummer, the size the
+      FP32-roofline target is stated for) and N = 262144 (Plummer with
+      Salpeter masses, eps = 1e-4), in MIXED, HYBRID and DS (CUDA events),
+      each with its errors against the oracle on 256 random + the 64 most
+      central particles (rank 0);
     * the 256-system ensemble (log-uniform N in [256, 8192], eps = 4/N)
-      integrated from t = 0 to 1/32 in one context, DS: total interactions
-      per second of the whole integration;
+      integrated from t = 0 to 1 in one HYBRID context: total interactions
+      per second of the whole integration and per-system energy drift; DS to
+      t = 1/16 beside it; and 16 sampled members integrated together to
+      t = 1/16 against the oracle's integration of each alone;
     * block steps, smallest timestep and energy drift of short integrations
-      in all three modes (MIXED's timestep collapse)."""
+      in every mode (MIXED's timestep collapse)."""
     out = {}
-    wl = ics.MIXED_N64K
-    m, r, v = wl.particles()
-    n = wl.n
-    idx = torch.arange(n, dtype=torch.int32, device=dev)
-    roof = {}
-    for prec in ("mixed", "hybrid", "ds"):
-        with nbody.Context(prec, device=dev.index, stream=stream) as ctx:
-            ctx.set_particles(m, r, v, wl.eps, wl.eta)
-            tun = ctx.autotune()
-            ctx.predict(0.0)
-            ctx.force(idx)
-            reps = 5
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(reps):
-                ctx.force(idx)
-            e1.record(stream)
-            e1.synchronize()
-            t = e0.elapsed_time(e1) / 1e3 / reps
+
+    def force_roofline(wl, key, modes):
+        m, r, v = wl.particles()
+        n = wl.n
+        idx = torch.arange(n, dtype=torch.int32, device=dev)
+        acc = torch.empty((n, 3), dtype=torch.float64, device=dev)
+        jerk = torch.empty((n, 3), dtype=torch.float64, device=dev)
+        pot = torch.empty(n, dtype=torch.float64, device=dev)
+        res = {"workload": wl.name, "n": n, "eps": wl.eps}
+        for prec in modes:
+            with nbody.Context(prec, device=dev.index, stream=stream) as ctx:
+                # loading evaluates every force once and leaves a, j in the
+                # state, which the hybrid near-pair test reads
+                ctx.set_particles(m, r, v, wl.eps, wl.eta)
+                tun = ctx.autotune()
+                ctx.predict(0.0)
+                ctx.force(idx, acc, jerk, pot)
+                reps = max(2, min(5, int(4e11 // (n * n))))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps):
+                    ctx.force(idx, acc, jerk, pot)
+                e1.record(stream)
+                e1.synchronize()
+                t = e0.elapsed_time(e1) / 1e3 / reps
             ach = FLOPS_PER_INTERACTION * n * n / t / 1e12
-            roof[prec] = {"bound": "alu", "achieved": ach, "peak": peak32, "unit": "TFLOP/s",
-                          "frac": ach / peak32, "launch_ms": t * 1e3,
-                          "interactions_per_s": n * n / t, "autotuned_launch": tun}
-    out["roofline_n65536"] = roof
-    sizes, off, ms, rs, vs, eps = ics.ensemble(**{k: ics.ENSEMBLE_K256[k]
-                                                  for k in ("k", "size_seed", "member_seed0")})
-    ens = {"systems": int(len(sizes)), "particles": int(off[-1]), "t_end": 1.0 / 32,
+            row = {"bound": "alu", "achieved": ach, "peak": peak32, "unit": "TFLOP/s",
+                   "frac": ach / peak32, "launch_ms": t * 1e3,
+                   "interactions_per_s": n * n / t, "autotuned_launch": tun,
+                   "algorithmic_bytes_per_launch": algorithmic_bytes(prec, n, n)}
+            if refs is not None and key in refs:
+                sidx, ref = refs[key]
+                got = (acc.cpu().numpy()[sidx], jerk.cpu().numpy()[sidx], pot.cpu().numpy()[sidx])
+                row["accuracy_vs_oracle"] = error_stats(got, ref)
+                row["accuracy_vs_oracle"]["sample"] = "256 random + the 64 most central particles"
+                row["meets_1e-6_gate"] = row["accuracy_vs_oracle"]["max_rel"] <= 1e-6
+            res[prec] = row
+        return res
+
+    out["roofline_n65536"] = force_roofline(ics.MIXED_N64K, "n65536", ("mixed", "hybrid", "ds"))
+    out["salpeter_n262144"] = force_roofline(ics.SALPETER_N256K, "n262144",
+                                             ("mixed", "hybrid", "ds"))
+
+    kw = {k: ics.ENSEMBLE_K256[k] for k in ("k", "size_seed", "member_seed0")}
+    sizes, off, ms, rs, vs, eps = ics.ensemble(**kw)
+    eta = ics.ENSEMBLE_K256["eta"]
+    ens = {"systems": int(len(sizes)), "particles": int(off[-1]),
            "precision_note": "hybrid and DS: with FP32 pair arithmetic (MIXED) the "
                              "Aarseth timesteps collapse (see precision_ablation)"}
-    for prec in ("hybrid", "ds"):
+    # t_end is a multiple of dt_max = 1/16, so every particle ends synchronised
+    # and the per-system energies are those of one time
+    for prec, t_end in (("hybrid", 1.0), ("ds", 1.0 / 16)):
         with nbody.Context(prec, device=dev.index, stream=stream) as ctx:
-            ctx.set_ensemble(off, ms, rs, vs, eps, ics.ENSEMBLE_K256["eta"])
+            ctx.set_ensemble(off, ms, rs, vs, eps, eta)
             tun = ctx.autotune()
-            ctx.set_ensemble(off, ms, rs, vs, eps, ics.ENSEMBLE_K256["eta"])
+            ctx.set_ensemble(off, ms, rs, vs, eps, eta)
+            k0, w0 = ctx.energy_systems(fp64_potential=True)
             torch.cuda.synchronize(dev)
-            w0 = time.perf_counter()
-            steps, inter = ctx.step_until(1.0 / 32)
+            w0c = time.perf_counter()
+            steps, inter = ctx.step_until(t_end)
             torch.cuda.synchronize(dev)
-            w = time.perf_counter() - w0
-            ens[prec] = {"value": world * inter / w, "unit": UNIT, "block_steps": int(steps),
-                         "interactions": int(inter), "wall_s": w,
+            w = time.perf_counter() - w0c
+            k1, w1 = ctx.energy_systems(fp64_potential=True)
+            de = np.abs((k1 + w1) - (k0 + w0)) / np.abs(k0 + w0)
+            ens[prec] = {"t_end": t_end, "value": world * inter / w, "unit": UNIT,
+                         "block_steps": int(steps), "interactions": int(inter), "wall_s": w,
                          "us_per_block_step": 1e6 * w / max(steps, 1),
+                         "rel_energy_drift_max": float(de.max()),
+                         "rel_energy_drift_p50": float(np.median(de)),
                          "autotuned_launch": tun}
+    if refs is not None and "ensemble16" in refs:
+        ens["oracle_check_16"] = ensemble_oracle_check(nbody, dev, stream, refs["ensemble16"])
     out["ensemble_k256"] = ens
     # Precision ablation of the integration (Sec. 4 measures energy error
     # against step count in mixed and DP): block steps, smallest timestep and
@@ -712,12 +788,101 @@ def extra_measurements(nbody, torch, dev, stream, world, peak32):
     return out
 
 
+def ensemble_oracle_check(nbody, dev, stream, ref):
+    """16 ensemble members integrated together (one HYBRID context) to
+    t = 1/16, each against the oracle's integration of that member alone:
+    energy drift ratio, final position / velocity differences, share of
+    particles on the oracle's timestep, total interactions."""
+    pick, off, m, r, v, eps, t_end, orc = ref
+    with nbody.Context("hybrid", device=dev.index, stream=stream) as ctx:
+        ctx.set_ensemble(off, m, r, v, eps, ics.ENSEMBLE_K256["eta"])
+        steps, inter = ctx.step_until(t_end)
+        k1, w1 = ctx.energy_systems(fp64_potential=True)
+        st = ctx.get_state()
+    rows = []
+    for q in range(len(pick)):
+        lo, hi = off[q], off[q + 1]
+        o = orc[q]
+        de = abs(k1[q] + w1[q] - o["e0"]) / abs(o["e0"])
+        rows.append({"member": int(pick[q]), "n": int(hi - lo), "rel_energy_drift": float(de),
+                     "oracle_rel_energy_drift": o["de"],
+                     "drift_ratio": float(de / o["de"]) if o["de"] > 0 else None,
+                     "max_abs_dr": float(np.max(np.abs(st["r"][lo:hi] - o["r"]))),
+                     "max_abs_dv": float(np.max(np.abs(st["v"][lo:hi] - o["v"]))),
+                     "same_dt_share": float(np.mean(st["dt"][lo:hi] == o["dt"]))})
+    orc_inter = sum(o["inter"] for o in orc)
+    ok = all(x["rel_energy_drift"] <= 2 * x["oracle_rel_energy_drift"] + 1e-13 and
+             x["max_abs_dr"] < 1e-6 and x["max_abs_dv"] < 1e-5 and x["same_dt_share"] >= 0.95
+             for x in rows) and abs(inter / orc_inter - 1) <= 0.05
+    return {"t_end": t_end, "members": [int(x) for x in pick], "block_steps": int(steps),
+            "interactions": int(inter), "oracle_interactions": float(orc_inter),
+            "max_drift_ratio": max(x["drift_ratio"] or 0.0 for x in rows),
+            "max_abs_dr": max(x["max_abs_dr"] for x in rows),
+            "max_abs_dv": max(x["max_abs_dv"] for x in rows),
+            "min_same_dt_share": min(x["same_dt_share"] for x in rows),
+            "gate": "per member: drift <= 2x oracle's (+1e-13), |dr| < 1e-6, |dv| < 1e-5, "
+                    ">= 95 % on the oracle's dt; interactions within 5 %",
+            "meets_gate": bool(ok), "rows": rows}
+
+
 def ctypes_ptr(t):
     import ctypes
     return ctypes.c_void_p(t.data_ptr())
 
 
 # --- CPU baseline: the oracle as it stands ------------------------------------------
+def cpu_baseline_leg(m, r, v, eps, seconds, timed=True, extra=True):
+    """The CPU-baseline leg (rank 0, before any GPU work): the FP64 oracle,
+    as it stands, on the host cores.  Its outputs are also the reference of
+    every accuracy gate on the bench line:
+      * "sweep": every particle of the N = 16384 workload at t = 0 (timed as
+        one whole-workload sample);
+      * "n65536", "n262144": 256 random + the 64 most central particles of
+        the N = 65536 and N = 262144 (Salpeter) workloads at t = 0;
+      * "ensemble16": 16 members of the ensemble workload, each integrated
+        alone to t = 1/16.
+    With `timed`, the repeated-sample timing of the oracle force follows."""
+    from oracle import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    n = len(m)
+    out = {"refs": {}, "samples": {}}
+    t0 = time.perf_counter()
+    out["refs"]["sweep"] = oracle.force(m, r, v, eps, nthreads=cores)
+    dt = time.perf_counter() - t0
+    out["samples"]["sweep_all_particles"] = {"value": n * n / dt, "unit": UNIT, "wall_s": dt,
+                                             "cores": cores}
+    if extra:
+        for key, wl in (("n65536", ics.MIXED_N64K), ("n262144", ics.SALPETER_N256K)):
+            mm, rr, vv = wl.particles()
+            sidx = ics.gate_sample(rr, wl.seed)
+            out["refs"][key] = (sidx, oracle.force(mm, rr, vv, wl.eps, idx=sidx, nthreads=cores))
+        t_end = 1.0 / 16
+        pick, off, ms, rs, vs, es = ics.ensemble_subset(16, 2048)
+        orc = []
+        t0 = time.perf_counter()
+        for q in range(len(pick)):
+            lo, hi = off[q], off[q + 1]
+            st = oracle.State(ms[lo:hi], rs[lo:hi], vs[lo:hi], float(es[q]),
+                              ics.ENSEMBLE_K256["eta"], nthreads=cores)
+            e0 = st.energy()
+            status = st.run(t_end)
+            if status != oracle.OK:
+                raise RuntimeError(f"oracle integration of member {pick[q]} failed: {status}")
+            orc.append({"e0": e0, "de": abs(st.energy() - e0) / abs(e0), "r": st.r.copy(),
+                        "v": st.v.copy(), "dt": st.dt.copy(), "inter": st.n_inter})
+        dt = time.perf_counter() - t0
+        out["refs"]["ensemble16"] = (pick, off, ms, rs, vs, es, t_end, orc)
+        inter = sum(o["inter"] for o in orc)
+        out["samples"]["ensemble16_integration"] = {
+            "value": inter / dt, "unit": UNIT, "wall_s": dt, "cores": cores,
+            "sample": "16 ensemble members (N <= 2048) each integrated alone to t = 1/16"}
+    if timed:
+        out["cpu"] = cpu_baseline(m, r, v, eps, seconds)
+        out["cpu"]["other_samples"] = out["samples"]
+    return out
+
+
 def cpu_baseline(m, r, v, eps, seconds):
     from oracle import oracle
     n = len(m)
@@ -800,7 +965,7 @@ def paper_cpu_baseline(m, r, v, eps, seconds, ref):
             "one_core": {"value": k1 * n / dt1, "unit": UNIT,
                          "gflops_60flop": k1 * n / dt1 * FLOPS_PER_INTERACTION / 1e9,
                          "sample": f"{k1} of the {n} particles, 1 thread, {dt1:.1f} s"},
-            "accuracy_vs_fp64": {"particles": k,
+            "accuracy_vs_oracle": {"particles": k,
                                  "acc_rel_p50": float(np.median(ea)),
                                  "acc_rel_max": float(ea.max()),
                                  "jerk_rel_p50": float(np.median(ej)),

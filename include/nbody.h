@@ -301,13 +301,23 @@ const char* nb_status_string(nb_status s);
  * and the call returns after it has finished.
  *
  * Its only working memory is one fixed device array of
- * NB_STATIC_SCRATCH_BYTES inside the library, present on every GPU that
- * loads the library until the process exits.  Limit: n <= NB_STATIC_MAX_N
- * (larger n returns NB_EINVAL with a message on stderr).  The first call on
- * a device performs a one-time set-up (the array's device address, kernel
- * attributes); make that first call before any stream capture.  Every call
- * shares the array: calls that overlap on the GPU (other threads, other
- * streams) race and must be serialised by the caller.
+ * NB_STATIC_SCRATCH_BYTES inside the library, held on each GPU where it has
+ * been materialised until the process exits.  Limit: n <= NB_STATIC_MAX_N
+ * on any GPU (the force kernel's grid is sized so that this holds whatever
+ * the SM count); larger n returns NB_EINVAL with a message on stderr.
+ *
+ * First call on a device: a one-time set-up (the array's device address,
+ * kernel attributes).  Under the CUDA runtime's default lazy module
+ * loading, that is also when the driver loads this part of the library onto
+ * the device and so reserves the array's NB_STATIC_SCRATCH_BYTES: a caller
+ * that later reserves all remaining GPU memory must make its first call
+ * (a call with n_act = 0 is enough) before it does so, and before any stream capture.
+ * Later calls allocate nothing.
+ *
+ * Every call synchronises `stream` to read back the kernel's status word, so
+ * the call cannot be made while `stream` is being captured into a graph.
+ * Every call shares the array: calls that overlap on the GPU (other
+ * threads, other streams) race and must be serialised by the caller.
  * Errors: NB_EINVAL (sizes, NULL pointers, an index outside [0, n)),
  * NB_ECUDA, NB_ETIMEOUT. */
 #define NB_STATIC_MAX_N 131072

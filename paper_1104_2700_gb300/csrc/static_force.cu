@@ -118,8 +118,14 @@ nb_status setup_device(int dev, DeviceSetup*& out)
         int per_sm = nb::force_ctas_per_sm(nb::Prec::DS, 1, 1);
         if (per_sm < 1) return NB_ECUDA;
         if (per_sm > STATIC_CTAS_PER_SM) per_sm = STATIC_CTAS_PER_SM;
+        // The scratch of the split-group sums grows with the number of
+        // persistent warps; shrink the grid until the largest system allowed
+        // fits the array, so the limit on n holds whatever the SM count.
+        int grid = per_sm * sms;
+        while (grid > 1 && plan_for(NB_STATIC_MAX_N, grid).total > NB_STATIC_SCRATCH_BYTES)
+            grid -= grid / 8 > 0 ? grid / 8 : 1;
         s.base = static_cast<unsigned char*>(addr);
-        s.grid = per_sm * sms;
+        s.grid = grid;
         s.ready = true;
     }
     out = &s;

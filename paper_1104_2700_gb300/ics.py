@@ -195,3 +195,30 @@ def ensemble(k: int = 256, size_seed: int = 4, member_seed0: int = 1000,
     eps = 4.0 / sizes.astype(np.float64)
     return (sizes, offsets, np.concatenate(ms), np.concatenate(rs),
             np.concatenate(vs), eps)
+
+
+def gate_sample(r: np.ndarray, seed: int, n_random: int = 256, n_central: int = 64) -> np.ndarray:
+    """Particles an accuracy check samples at sizes where every particle would
+    be too slow for the oracle: `n_random` drawn by a seeded permutation and
+    the `n_central` closest to the origin (the densest region, where near
+    neighbours cancel most), ascending, without repeats."""
+    n = len(r)
+    central = np.argsort(np.einsum("ij,ij->i", r, r), kind="stable")[:n_central]
+    pick = np.concatenate([permutation(n, seed)[:n_random], central])
+    return np.unique(pick).astype(np.int32)
+
+
+def ensemble_subset(count: int = 16, n_max: int = 2048, **kw):
+    """`count` members of the ensemble workload, drawn by a seeded permutation
+    from those with N <= n_max: (member numbers, offsets, m, r, v, eps) of
+    the sub-ensemble, members in ascending order."""
+    sizes, off, ms, rs, vs, eps = ensemble(**kw)
+    small = [q for q in range(len(sizes)) if sizes[q] <= n_max]
+    pick = sorted(small[i] for i in permutation(len(small), 16)[:count])
+    sub_off = np.zeros(count + 1, dtype=np.int64)
+    sub_off[1:] = np.cumsum([sizes[q] for q in pick])
+
+    def cat(a):
+        return np.concatenate([a[off[q]:off[q + 1]] for q in pick])
+
+    return pick, sub_off, cat(ms), cat(rs), cat(vs), np.array([eps[q] for q in pick])

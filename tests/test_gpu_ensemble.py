@@ -111,3 +111,46 @@ def test_ensemble_rejects_bad_input(gpu):
         with pytest.raises(gpu.NbError) as e:
             ctx.correct(0.1, np.array([0], dtype=np.int32))
         assert e.value.status == gpu.NB_ESTATE
+
+
+def test_hybrid_ensemble_integration_matches_oracle_per_system(gpu, orc):
+    """The batched mode the benchmark times: 16 members of the ensemble
+    workload integrated together in one HYBRID context (one launch per kernel
+    per block step for all of them) from t = 0 to 1/16, each compared with
+    the FP64 oracle's integration of that system alone (Sec. 2, steps 1-9):
+      * relative energy drift within 2x the oracle's (plus 1e-13, the
+        rounding of the FP64 energy sums themselves);
+      * final positions within 1e-6 and velocities within 1e-5 (absolute,
+        N-body units): force errors of <= 1e-6 relative move a particle by
+        ~1e-6 |a| t^2, and a timestep chosen one power of two apart changes
+        it by the Hermite truncation error, both far below these;
+      * at least 95 % of each system's particles on the oracle's timestep,
+        and the total interactions within 5 % of the oracle's sum (the
+        ensemble's block steps interleave all systems, so its own step count
+        is not comparable with one system's)."""
+    pick, off, m, r, v, eps = ics.ensemble_subset(16, 2048)
+    t_end = 1.0 / 16
+    with gpu.Context("hybrid") as ens:
+        ens.set_ensemble(off, m, r, v, eps, 0.02)
+        steps, inter = ens.step_until(t_end)
+        k1, w1 = ens.energy_systems(fp64_potential=True)
+        out = ens.get_state()
+    assert np.all(out["t"] == t_end)
+    orc_inter = 0.0
+    report = []
+    for q in range(len(pick)):
+        lo, hi = off[q], off[q + 1]
+        s = orc.State(m[lo:hi], r[lo:hi], v[lo:hi], float(eps[q]), 0.02, nthreads=NTHREADS)
+        e0 = s.energy()
+        assert s.run(t_end) == orc.OK
+        de_orc = abs(s.energy() - e0) / abs(e0)
+        de_gpu = abs(k1[q] + w1[q] - e0) / abs(e0)
+        orc_inter += s.n_inter
+        dr = np.max(np.abs(out["r"][lo:hi] - s.r))
+        dv = np.max(np.abs(out["v"][lo:hi] - s.v))
+        same_dt = np.mean(out["dt"][lo:hi] == s.dt)
+        report.append((pick[q], hi - lo, de_gpu, de_orc, dr, dv, same_dt))
+        assert de_gpu <= 2.0 * de_orc + 1e-13, report[-1]
+        assert dr < 1e-6 and dv < 1e-5, report[-1]
+        assert same_dt >= 0.95, report[-1]
+    assert inter == pytest.approx(orc_inter, rel=0.05)
