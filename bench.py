@@ -392,11 +392,21 @@ def run_ours(args):
                 total += e0.elapsed_time(e1) / 1e3
         return total / reps
 
+    def spatial_list(ctx, members):
+        """`members` (particle indices) as the block step lists them: in the
+        context's spatial order (the order the force kernel's i-groups are
+        cut in), as a device tensor."""
+        order = ctx.spatial_order()
+        rank = np.empty(n, dtype=np.int64)
+        rank[order] = np.arange(n)
+        members = np.asarray(members)
+        return torch.from_numpy(members[np.argsort(rank[members])].astype(np.int32)).to(dev)
+
     def force_launch_time(ctx, reps=20):
         """Average duration of one force launch with n_act = N."""
         ctx.restore(ctx.snaps[-1])
         ctx.predict(0.0)
-        idx_all = torch.arange(n, dtype=torch.int32, device=dev)
+        idx_all = spatial_list(ctx, np.arange(n))
         return timed_forces(ctx, ctx.snaps[-1], idx_all, reps)
 
     def breakdown(ctx, dstates, reps=50):
@@ -432,7 +442,7 @@ def run_ours(args):
                 del g
             restore()
             ctx.predict(0.0)
-            idx_k = torch.from_numpy(np.sort(perm[:k]).astype(np.int32)).to(dev)
+            idx_k = spatial_list(ctx, perm[:k])
             row["force_us"] = timed_forces(ctx, buf, idx_k, reps) * 1e6
             row["block_step_us"] = row["restore_and_block_step_us"] - row["restore_us"]
             row["non_force_us"] = row["block_step_us"] - row["force_us"]
@@ -687,35 +697,71 @@ def extra_measurements(nbody, torch, dev, stream, world, peak32, refs):
     def force_roofline(wl, key, modes):
         m, r, v = wl.particles()
         n = wl.n
-        idx = torch.arange(n, dtype=torch.int32, device=dev)
         acc = torch.empty((n, 3), dtype=torch.float64, device=dev)
         jerk = torch.empty((n, 3), dtype=torch.float64, device=dev)
         pot = torch.empty(n, dtype=torch.float64, device=dev)
-        res = {"workload": wl.name, "n": n, "eps": wl.eps}
+        res = {"workload": wl.name, "n": n, "eps": wl.eps,
+               "state": "a, j and dt from the load evaluation, no far-field noise history "
+                        "(as the sweep's blocks: the hybrid integration guard idle); every "
+                        "particle active, listed in the context's spatial order"}
+
+        def time_force(ctx, idx, snap=None):
+            """Mean force-launch time (CUDA events around each launch); with
+            `snap`, the state is rolled back to it before every launch, so
+            each evaluation starts from the same noise history."""
+            reps = max(2, min(5, int(4e11 // (n * n))))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            total = 0.0
+            for rep in range(reps + 1):
+                if snap is not None:
+                    ctx.restore(snap)
+                ctx.predict(0.0)
+                e0.record(stream)
+                ctx.force(idx, acc, jerk, pot)
+                e1.record(stream)
+                e1.synchronize()
+                if rep > 0:
+                    total += e0.elapsed_time(e1) / 1e3
+            return total / reps
+
         for prec in modes:
             with nbody.Context(prec, device=dev.index, stream=stream) as ctx:
                 # loading evaluates every force once and leaves a, j in the
                 # state, which the hybrid near-pair test reads
                 ctx.set_particles(m, r, v, wl.eps, wl.eta)
                 tun = ctx.autotune()
-                ctx.predict(0.0)
-                ctx.force(idx, acc, jerk, pot)
-                reps = max(2, min(5, int(4e11 // (n * n))))
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                for _ in range(reps):
-                    ctx.force(idx, acc, jerk, pot)
-                e1.record(stream)
-                e1.synchronize()
-                t = e0.elapsed_time(e1) / 1e3 / reps
+                order = ctx.spatial_order()
+                idx = torch.from_numpy(order).to(dev)
+                t_guard = None
+                if prec == "hybrid":
+                    snap = torch.empty(ctx.snapshot_bytes() // 8 + 1, dtype=torch.float64,
+                                       device=dev)
+                    ctx.snapshot(snap)
+                    t_guard = time_force(ctx, idx, snap)
+                # reloading the same state clears the noise history
+                st = ctx.get_state()
+                ctx.set_state(m, st["r"], st["v"], st["a"], st["j"], st["t"], st["dt"],
+                              wl.eps, wl.eta)
+                snap = torch.empty(ctx.snapshot_bytes() // 8 + 1, dtype=torch.float64, device=dev)
+                ctx.snapshot(snap)
+                t = time_force(ctx, idx, snap)
             ach = FLOPS_PER_INTERACTION * n * n / t / 1e12
             row = {"bound": "alu", "achieved": ach, "peak": peak32, "unit": "TFLOP/s",
                    "frac": ach / peak32, "launch_ms": t * 1e3,
                    "interactions_per_s": n * n / t, "autotuned_launch": tun,
                    "algorithmic_bytes_per_launch": algorithmic_bytes(prec, n, n)}
+            if t_guard is not None:
+                row["launch_ms_right_after_load"] = t_guard * 1e3
+                row["right_after_load_note"] = (
+                    "the first evaluation after nb_set_particles, with the noise history "
+                    "of the load's own evaluation: the integration guard sends particles "
+                    "whose start-rule timestep is short to double-single")
             if refs is not None and key in refs:
                 sidx, ref = refs[key]
-                got = (acc.cpu().numpy()[sidx], jerk.cpu().numpy()[sidx], pot.cpu().numpy()[sidx])
+                rows = np.empty(n, dtype=np.int64)
+                rows[order] = np.arange(n)  # output row of each particle
+                sel = rows[sidx]
+                got = (acc.cpu().numpy()[sel], jerk.cpu().numpy()[sel], pot.cpu().numpy()[sel])
                 row["accuracy_vs_oracle"] = error_stats(got, ref)
                 row["accuracy_vs_oracle"]["sample"] = "256 random + the 64 most central particles"
                 row["meets_1e-6_gate"] = row["accuracy_vs_oracle"]["max_rel"] <= 1e-6

@@ -130,8 +130,10 @@ typedef struct nb_tuning {
 } nb_tuning;
 
 /* Autotuner: time every candidate launch shape of the force kernel on the
- * loaded system (probe blocks of 32, 256, 2048 and min(n, 16384) particles,
- * the first by index) and keep the fastest for each bucket, with the bucket
+ * loaded system (probe blocks of 32, 256, 2048 and min(n, 16384) particles
+ * spread evenly over the context's stored order, nb_spatial_order, like the
+ * scattered members of a block step; for the hybrid precision with the
+ * integration guard idle, as in a steady integration) and keep the fastest for each bucket, with the bucket
  * boundary nact_split at 1024 (probes 32 and 256 small) or 4096 (2048 small
  * too), whichever gives the least total.  Predicts all particles to the
  * time of particle 0 first, so call nb_predict again before nb_force.  *out
@@ -187,9 +189,10 @@ nb_status nb_get_state(nb_ctx* ctx, double* r, double* v, double* a, double* j,
  * a rollback point that never leaves the GPU.  nb_snapshot_bytes() is the
  * size of one snapshot of the loaded system (0 if none is loaded).
  * nb_snapshot copies m, x, v, a, j, t, dt, the per-particle derived data
- * (next-time keys, hybrid noise estimates) and the layout bounds into the
- * caller's device buffer `buf` (at least nb_snapshot_bytes, 16-byte
- * aligned); nb_restore copies such a snapshot back.  Both are one kernel on
+ * (next-time keys, hybrid noise estimates), the layout bounds and the
+ * context's spatial order (nb_spatial_order) into the caller's device
+ * buffer `buf` (at least nb_snapshot_bytes, 16-byte aligned); nb_restore
+ * copies such a snapshot back.  Both are one kernel on
  * the context stream, asynchronous and capturable in a CUDA graph.  A
  * snapshot belongs to the system it was taken from (same n and, for an
  * ensemble, the same systems); restoring into another is undefined.
@@ -215,8 +218,17 @@ nb_status nb_select(nb_ctx* ctx, double t_end, double* t_next, int32_t* n_act,
  * output pointer may be NULL.  With on_device = 0, idx and the outputs are
  * host arrays and the call blocks; with on_device = 1 they are device arrays
  * and the call is stream-ordered.  The results are also kept for
- * nb_correct.  Errors: NB_EINVAL (n_act < 0 or > n, bad index), NB_ESTATE
- * (no particles loaded). */
+ * nb_correct.
+ * Order: the force kernel cuts its i-groups from the list as it receives
+ * it.  A host list is first put in the context's spatial order
+ * (nb_spatial_order), as the lists of nb_block_step are, and the outputs
+ * are returned in the caller's order; a device list is processed in its own
+ * order, so a device list in spatial order is the fast one (and gives the
+ * same bits as the same particles given as a host list).  Results are
+ * reproducible for a given list; another order of the same particles may
+ * change the last bits.
+ * Errors: NB_EINVAL (n_act < 0 or > n, bad index), NB_ESTATE (no particles
+ * loaded). */
 nb_status nb_force(nb_ctx* ctx, int32_t n_act, const int32_t* idx, double* acc,
                    double* jerk, double* pot, int32_t on_device);
 
@@ -273,6 +285,21 @@ nb_status nb_energy_systems(nb_ctx* ctx, int32_t fp64_potential, double* kin, do
 /* Number of systems loaded (1 after nb_set_particles, k after
  * nb_set_ensemble, 0 before either). */
 int32_t nb_num_systems(const nb_ctx* ctx);
+
+/* The context's spatial order (no counterpart in the paper): the context
+ * stores its particles in this order, order[k] being the caller's index of
+ * the k-th stored particle (n host entries).  Within each system the
+ * particles follow a space-filling (Morton) curve through the system's
+ * bounding box, so consecutive particles are close in space; the force
+ * kernel's j tiles and the i-groups it cuts from a list are then compact,
+ * which the hybrid precision's far-tile path needs.  Every index the calls
+ * take or return is the caller's; the order only changes the summation
+ * order.  It is computed from the positions at every load and at the start
+ * of every nb_step_until (a pure function of those positions, so a run
+ * resumed from a checkpoint gets the order the original had), and
+ * nb_restore restores the order stored with the snapshot.  Blocks.
+ * Errors: NB_ESTATE (nothing loaded), NB_EINVAL (NULL order). */
+nb_status nb_spatial_order(nb_ctx* ctx, int32_t* order);
 
 /* Number of particles loaded (0 before nb_set_particles). */
 int64_t nb_num_particles(const nb_ctx* ctx);

@@ -76,6 +76,26 @@ struct nb_ctx {
     // CUDA graph of GRAPH_STEPS device-resident block steps for one t_end.
     cudaGraphExec_t step_graph = nullptr;
     double graph_t_end = 0.0;
+    // The particles are stored in a spatial order: internal index k holds the
+    // caller's particle perm[k] (inv is the inverse).  Within each system the
+    // order follows a Morton curve through the system's bounding box, so the
+    // j tiles and the i-groups cut from the (ascending) active lists are each
+    // close together in space, which the hybrid precision's far-tile test
+    // needs.  The order is a pure function of the caller-order positions it
+    // was computed from (kept in order_pos, with the systems' offsets in
+    // order_off): it is recomputed at every load and at the start of every
+    // nb_step_until, so a run resumed from a checkpoint gets the order the
+    // original had.  Device copies perm_dev / inv_dev are the reference;
+    // the host copies are refreshed from them when host_order_stale (after
+    // nb_restore, which restores the order stored with a snapshot).
+    std::vector<int32_t> h_perm, h_inv;
+    int32_t* perm_dev = nullptr;
+    int32_t* inv_dev = nullptr;
+    double* order_buf = nullptr;  // 17 n + 1 doubles: the state while it is re-ordered
+    std::vector<double> order_pos;
+    std::vector<int64_t> order_off;
+    bool order_fresh = false;       // no step has moved the particles since
+    bool host_order_stale = false;
 };
 
 namespace {
@@ -131,6 +151,10 @@ void free_buffers(nb_ctx* c)
 {
     dfree(c->st.m), dfree(c->st.x), dfree(c->st.v), dfree(c->st.a), dfree(c->st.j);
     dfree(c->st.t), dfree(c->st.dt), dfree(c->st.hq), dfree(c->st.nkey);
+    dfree(c->st.tile_box), dfree(c->perm_dev), dfree(c->inv_dev), dfree(c->order_buf);
+    c->order_pos.clear();
+    c->order_fresh = false;
+    c->host_order_stale = false;
     for (int k = 0; k < 4; ++k) {
         if (c->jl.arr[k]) cudaFree(c->jl.arr[k]);
         if (c->jl64.arr[k]) cudaFree(c->jl64.arr[k]);
@@ -216,6 +240,10 @@ nb_status ensure_capacity(nb_ctx* c, int64_t n, int64_t n_pad, int64_t k)
     NB_CK(c, cudaMalloc(&c->st.dt, n * d));
     NB_CK(c, cudaMalloc(&c->st.hq, n * d));
     NB_CK(c, cudaMalloc(&c->st.nkey, n * sizeof(unsigned long long)));
+    NB_CK(c, cudaMalloc(&c->perm_dev, n * sizeof(int32_t)));
+    NB_CK(c, cudaMalloc(&c->inv_dev, n * sizeof(int32_t)));
+    if (c->prec == Prec::HYBRID)
+        NB_CK(c, cudaMalloc(&c->st.tile_box, 2 * (n_pad / nb::TJ) * sizeof(float4)));
     // i-groups never mix systems: at most n / 32 + k of them
     const int64_t groups_bound = n + 32 * k;
     nb_status s = alloc_layout(c, c->prec, c->jl, n_pad);
@@ -362,6 +390,7 @@ nb::ForceArgs force_args(nb_ctx* c, Prec p, const nb::JLayout& jl, const int32_t
     f.n_pad = c->n_pad;
     f.idx = idx;
     f.n_act_dev = n_act_dev;
+    f.tile_box = c->st.tile_box;
     f.acc = c->acc1;
     f.jerk = c->jerk1;
     f.pot = c->pot1;
@@ -406,22 +435,175 @@ nb_status run_force_list(nb_ctx* c, Prec p, const nb::JLayout& jl, const int32_t
     return run_force(c, p, jl, idx, n_act_dev, n_act_host);
 }
 
-nb_status upload_vec3(nb_ctx* c, const double* src, double* dst_soa, int on_device)
+// Caller arrays in, through the spatial order: w doubles per particle (3: an
+// n x 3 row-major array into SoA; 1: a scalar per particle).
+nb_status upload_perm(nb_ctx* c, const double* src, double* dst, int w, int on_device)
 {
-    NB_CK(c, cudaMemcpyAsync(c->staging, src, 3 * c->n * sizeof(double),
+    NB_CK(c, cudaMemcpyAsync(c->staging, src, w * c->n * sizeof(double),
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                              c->stream));
-    NB_CK(c, nb::aos_to_soa_launch(c->staging, dst_soa, c->n, c->stream));
+    NB_CK(c, nb::permute_in_launch(c->staging, dst, c->n, w, c->perm_dev, c->stream));
     return NB_OK;
 }
 
-nb_status download_vec3(nb_ctx* c, const double* src_soa, double* dst, int on_device)
+nb_status upload_vec3(nb_ctx* c, const double* src, double* dst_soa, int on_device)
 {
-    NB_CK(c, nb::soa_to_aos_launch(src_soa, c->staging, c->n, c->stream));
-    NB_CK(c, cudaMemcpyAsync(dst, c->staging, 3 * c->n * sizeof(double),
+    return upload_perm(c, src, dst_soa, 3, on_device);
+}
+
+// State arrays out to the caller's order (w doubles per particle).
+nb_status download_perm(nb_ctx* c, const double* src, double* dst, int w, int on_device)
+{
+    NB_CK(c, nb::permute_out_launch(src, c->staging, c->n, w, c->perm_dev, c->stream));
+    NB_CK(c, cudaMemcpyAsync(dst, c->staging, w * c->n * sizeof(double),
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                              c->stream));
     return NB_OK;
+}
+
+// The host copies of the order, from the device copy when they are stale.
+nb_status sync_host_order(nb_ctx* c)
+{
+    if (!c->host_order_stale) return NB_OK;
+    c->h_perm.resize(c->n);
+    NB_CK(c, cudaMemcpyAsync(c->h_perm.data(), c->perm_dev, c->n * sizeof(int32_t),
+                             cudaMemcpyDeviceToHost, c->stream));
+    NB_CK(c, cudaStreamSynchronize(c->stream));
+    c->h_inv.resize(c->n);
+    for (int64_t k = 0; k < c->n; ++k) c->h_inv[c->h_perm[k]] = static_cast<int32_t>(k);
+    c->host_order_stale = false;
+    return NB_OK;
+}
+
+// Morton key of a point of the box [lo, lo + ext): 16 bits per axis,
+// interleaved (bit b of axis d at bit 3 b + d).
+uint64_t morton48(const double* x, const double* lo, const double* ext)
+{
+    uint64_t key = 0;
+    for (int d = 0; d < 3; ++d) {
+        double u = ext[d] > 0.0 ? (x[d] - lo[d]) / ext[d] : 0.0;
+        if (!(u >= 0.0)) u = 0.0;  // also NaN
+        if (u > 1.0) u = 1.0;
+        const uint32_t q = static_cast<uint32_t>(u * 65535.0);
+        for (int b = 0; b < 16; ++b) key |= static_cast<uint64_t>((q >> b) & 1u) << (3 * b + d);
+    }
+    return key;
+}
+
+// The spatial order of caller-order positions r[n][3]: within each system
+// (particles [off[q], off[q+1])), the particles sorted by the Morton key of
+// their position in the system's bounding box, ties by index.  perm[k] is
+// the caller's particle at internal index k.  An ensemble keeps the order it
+// was given: its systems are small and its blocks few particles each, so its
+// i-groups would not be compact anyway, and the far-tile path pays only for
+// large blocks of large systems.
+std::vector<int32_t> order_of(const double* r, const std::vector<int64_t>& off)
+{
+    std::vector<int32_t> perm(off.back());
+    if (off.size() > 2) {
+        for (int64_t k = 0; k < off.back(); ++k) perm[k] = static_cast<int32_t>(k);
+        return perm;
+    }
+    std::vector<std::pair<uint64_t, int32_t>> keys;
+    for (size_t q = 0; q + 1 < off.size(); ++q) {
+        double lo[3], hi[3], ext[3];
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = HUGE_VAL;
+            hi[d] = -HUGE_VAL;
+        }
+        for (int64_t i = off[q]; i < off[q + 1]; ++i)
+            for (int d = 0; d < 3; ++d) {
+                const double x = r[3 * i + d];
+                if (!std::isfinite(x)) continue;
+                lo[d] = std::min(lo[d], x);
+                hi[d] = std::max(hi[d], x);
+            }
+        for (int d = 0; d < 3; ++d) {
+            if (!(lo[d] <= hi[d])) lo[d] = hi[d] = 0.0;  // no finite coordinate
+            ext[d] = hi[d] - lo[d];
+        }
+        keys.clear();
+        for (int64_t i = off[q]; i < off[q + 1]; ++i)
+            keys.emplace_back(morton48(r + 3 * i, lo, ext), static_cast<int32_t>(i));
+        std::sort(keys.begin(), keys.end());
+        for (size_t k = 0; k < keys.size(); ++k) perm[off[q] + k] = keys[k].second;
+    }
+    return perm;
+}
+
+// Order of a load (caller-order host positions r): kept when the positions
+// and systems are those the current order was computed from.  Returns in
+// *same whether the order is unchanged.
+nb_status load_order(nb_ctx* c, const double* r, bool* same = nullptr)
+{
+    const int64_t n = c->n;
+    const std::vector<int64_t> off = c->ens ? c->h_off : std::vector<int64_t>{0, n};
+    if (same) *same = false;
+    if (c->order_pos.size() == static_cast<size_t>(3 * n) && c->order_off == off &&
+        std::memcmp(c->order_pos.data(), r, 3 * n * sizeof(double)) == 0) {
+        c->order_fresh = true;
+        if (same) *same = true;
+        return NB_OK;
+    }
+    c->h_perm = order_of(r, off);
+    c->h_inv.assign(n, 0);
+    for (int64_t k = 0; k < n; ++k) c->h_inv[c->h_perm[k]] = static_cast<int32_t>(k);
+    c->host_order_stale = false;
+    NB_CK(c, cudaMemcpyAsync(c->perm_dev, c->h_perm.data(), n * sizeof(int32_t),
+                             cudaMemcpyHostToDevice, c->stream));
+    NB_CK(c, cudaMemcpyAsync(c->inv_dev, c->h_inv.data(), n * sizeof(int32_t),
+                             cudaMemcpyHostToDevice, c->stream));
+    NB_CK(c, cudaStreamSynchronize(c->stream));  // the host vectors are copy sources
+    c->order_pos.assign(r, r + 3 * n);
+    c->order_off = off;
+    c->order_fresh = true;
+    return NB_OK;
+}
+
+// Re-order the stored particles to the spatial order of their current
+// positions, when steps have moved them since the order was computed.
+nb_status refresh_order(nb_ctx* c)
+{
+    if (c->order_fresh) return NB_OK;
+    nb_status s = sync_host_order(c);
+    if (s != NB_OK) return s;
+    const int64_t n = c->n;
+    std::vector<double> soa(3 * n), aos(3 * n);
+    NB_CK(c, cudaMemcpyAsync(soa.data(), c->st.x, soa.size() * sizeof(double),
+                             cudaMemcpyDeviceToHost, c->stream));
+    NB_CK(c, cudaStreamSynchronize(c->stream));
+    for (int64_t k = 0; k < n; ++k)
+        for (int d = 0; d < 3; ++d) aos[3 * static_cast<int64_t>(c->h_perm[k]) + d] = soa[d * n + k];
+    const std::vector<int32_t> old_inv = c->h_inv;
+    bool same = false;
+    if ((s = load_order(c, aos.data(), &same)) != NB_OK) return s;
+    if (same) return NB_OK;
+    // new internal index k holds the particle that sat at old_inv[perm[k]]
+    std::vector<int32_t> map(n);
+    for (int64_t k = 0; k < n; ++k) map[k] = old_inv[c->h_perm[k]];
+    if (!c->order_buf) NB_CK(c, cudaMalloc(&c->order_buf, (17 * n + 1) * sizeof(double)));
+    NB_CK(c, cudaMemcpyAsync(c->idx_user, map.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice,
+                             c->stream));
+    NB_CK(c, nb::snapshot_launch(c->st, c->order_buf, true, c->stream));
+    NB_CK(c, nb::reorder_state_launch(c->st, c->order_buf, c->idx_user, c->stream));
+    NB_CK(c, cudaStreamSynchronize(c->stream));  // map is a copy source
+    c->last_force_n_act = -1;
+    return NB_OK;
+}
+
+// A caller's host list in internal indices, ascending (the order the select
+// gives its own lists): sorted[k] = inv[idx[perm[k]]].
+std::vector<int32_t> internal_sorted(const nb_ctx* c, int32_t n_act, const int32_t* idx,
+                                     std::vector<int32_t>& perm)
+{
+    perm.resize(n_act);
+    for (int32_t k = 0; k < n_act; ++k) perm[k] = k;
+    std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) {
+        return c->h_inv[idx[a]] < c->h_inv[idx[b]];
+    });
+    std::vector<int32_t> sorted(n_act);
+    for (int32_t k = 0; k < n_act; ++k) sorted[k] = c->h_inv[idx[perm[k]]];
+    return sorted;
 }
 
 nb_status validate_idx(nb_ctx* c, int32_t n_act, const int32_t* idx)
@@ -463,6 +645,7 @@ nb_status block_step(nb_ctx* c, double t_end)
     ca.inter_counter = c->ctr64 + 1;
     NB_CK(c, nb::correct_launch(c->st, ca, c->stream));
     c->last_force_n_act = -1;
+    c->order_fresh = false;  // the positions move
     return NB_OK;
 }
 
@@ -655,7 +838,8 @@ nb_status nb_set_particles(nb_ctx* c, int64_t n, const double* m, const double* 
     if (!m || !r || !v) return fail(c, NB_EINVAL, "NULL array");
     nb_status s = begin_load(c, n, eps, eta);
     if (s != NB_OK) return s;
-    NB_CK(c, cudaMemcpyAsync(c->st.m, m, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if ((s = load_order(c, r)) != NB_OK) return s;
+    if ((s = upload_perm(c, m, c->st.m, 1, 0)) != NB_OK) return s;
     if ((s = upload_vec3(c, r, c->st.x, 0)) != NB_OK) return s;
     if ((s = upload_vec3(c, v, c->st.v, 0)) != NB_OK) return s;
     NB_CK(c, cudaMemsetAsync(c->st.a, 0, 3 * n * sizeof(double), c->stream));
@@ -685,14 +869,23 @@ nb_status nb_set_state(nb_ctx* c, int64_t n, const double* m, const double* r, c
     if (!m || !r || !v || !a || !j || !t || !dt) return fail(c, NB_EINVAL, "NULL array");
     nb_status s = begin_load(c, n, eps, eta);
     if (s != NB_OK) return s;
-    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    NB_CK(c, cudaMemcpyAsync(c->st.m, m, n * sizeof(double), k, c->stream));
+    if (on_device) {
+        // the order is computed on the host from the positions
+        std::vector<double> hr(3 * n);
+        NB_CK(c, cudaMemcpyAsync(hr.data(), r, hr.size() * sizeof(double),
+                                 cudaMemcpyDeviceToHost, c->stream));
+        NB_CK(c, cudaStreamSynchronize(c->stream));
+        if ((s = load_order(c, hr.data())) != NB_OK) return s;
+    } else if ((s = load_order(c, r)) != NB_OK) {
+        return s;
+    }
+    if ((s = upload_perm(c, m, c->st.m, 1, on_device)) != NB_OK) return s;
     if ((s = upload_vec3(c, r, c->st.x, on_device)) != NB_OK) return s;
     if ((s = upload_vec3(c, v, c->st.v, on_device)) != NB_OK) return s;
     if ((s = upload_vec3(c, a, c->st.a, on_device)) != NB_OK) return s;
     if ((s = upload_vec3(c, j, c->st.j, on_device)) != NB_OK) return s;
-    NB_CK(c, cudaMemcpyAsync(c->st.t, t, n * sizeof(double), k, c->stream));
-    NB_CK(c, cudaMemcpyAsync(c->st.dt, dt, n * sizeof(double), k, c->stream));
+    if ((s = upload_perm(c, t, c->st.t, 1, on_device)) != NB_OK) return s;
+    if ((s = upload_perm(c, dt, c->st.dt, 1, on_device)) != NB_OK) return s;
     if ((s = refresh_bounds(c)) != NB_OK) return s;
     if (!on_device) NB_CK(c, cudaStreamSynchronize(c->stream));
     c->loaded = true;
@@ -702,7 +895,8 @@ nb_status nb_set_state(nb_ctx* c, int64_t n, const double* m, const double* r, c
 int64_t nb_snapshot_bytes(const nb_ctx* c)
 {
     if (!c || !c->loaded) return 0;
-    return (17 * c->n + 1) * static_cast<int64_t>(sizeof(double));
+    // the state (17 n words and the bounds), then the order (perm, inv)
+    return (18 * c->n + 1) * static_cast<int64_t>(sizeof(double));
 }
 
 nb_status nb_snapshot(nb_ctx* c, void* buf)
@@ -710,7 +904,13 @@ nb_status nb_snapshot(nb_ctx* c, void* buf)
     nb_status s = enter(c, true);
     if (s != NB_OK) return s;
     if (!buf || (reinterpret_cast<uintptr_t>(buf) & 15u)) return fail(c, NB_EINVAL, "buf NULL or not 16-byte aligned");
-    NB_CK(c, nb::snapshot_launch(c->st, static_cast<double*>(buf), true, c->stream));
+    double* b = static_cast<double*>(buf);
+    NB_CK(c, nb::snapshot_launch(c->st, b, true, c->stream));
+    int32_t* ord = reinterpret_cast<int32_t*>(b + 17 * c->n + 1);
+    NB_CK(c, cudaMemcpyAsync(ord, c->perm_dev, c->n * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                             c->stream));
+    NB_CK(c, cudaMemcpyAsync(ord + c->n, c->inv_dev, c->n * sizeof(int32_t),
+                             cudaMemcpyDeviceToDevice, c->stream));
     return NB_OK;
 }
 
@@ -719,8 +919,17 @@ nb_status nb_restore(nb_ctx* c, const void* buf)
     nb_status s = enter(c, true);
     if (s != NB_OK) return s;
     if (!buf || (reinterpret_cast<uintptr_t>(buf) & 15u)) return fail(c, NB_EINVAL, "buf NULL or not 16-byte aligned");
-    NB_CK(c, nb::snapshot_launch(c->st, static_cast<double*>(const_cast<void*>(buf)), false,
-                                 c->stream));
+    double* b = static_cast<double*>(const_cast<void*>(buf));
+    NB_CK(c, nb::snapshot_launch(c->st, b, false, c->stream));
+    const int32_t* ord = reinterpret_cast<const int32_t*>(b + 17 * c->n + 1);
+    NB_CK(c, cudaMemcpyAsync(c->perm_dev, ord, c->n * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                             c->stream));
+    NB_CK(c, cudaMemcpyAsync(c->inv_dev, ord + c->n, c->n * sizeof(int32_t),
+                             cudaMemcpyDeviceToDevice, c->stream));
+    // the host copies of the order follow the device ones when next needed
+    c->host_order_stale = true;
+    c->order_pos.clear();
+    c->order_fresh = false;
     return NB_OK;
 }
 
@@ -729,17 +938,14 @@ nb_status nb_get_state(nb_ctx* c, double* r, double* v, double* a, double* j, do
 {
     nb_status s = enter(c, true);
     if (s != NB_OK) return s;
-    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    double* src[4] = {c->st.x, c->st.v, c->st.a, c->st.j};
-    double* dst[4] = {r, v, a, j};
-    for (int q = 0; q < 4; ++q) {
+    double* src[6] = {c->st.x, c->st.v, c->st.a, c->st.j, c->st.t, c->st.dt};
+    double* dst[6] = {r, v, a, j, t, dt};
+    for (int q = 0; q < 6; ++q) {
         if (!dst[q]) continue;
-        if ((s = download_vec3(c, src[q], dst[q], on_device)) != NB_OK) return s;
+        if ((s = download_perm(c, src[q], dst[q], q < 4 ? 3 : 1, on_device)) != NB_OK) return s;
+        // (one staging buffer: each host copy completes before the next)
         if (!on_device) NB_CK(c, cudaStreamSynchronize(c->stream));
     }
-    if (t) NB_CK(c, cudaMemcpyAsync(t, c->st.t, c->n * sizeof(double), k, c->stream));
-    if (dt) NB_CK(c, cudaMemcpyAsync(dt, c->st.dt, c->n * sizeof(double), k, c->stream));
-    if (!on_device) NB_CK(c, cudaStreamSynchronize(c->stream));
     return NB_OK;
 }
 
@@ -776,9 +982,13 @@ nb_status nb_select(nb_ctx* c, double t_end, double* t_next, int32_t* n_act, int
     if (t_next) *t_next = nb::time_from_key(*hk);
     if (n_act) *n_act = *hn;
     if (idx && *hn > 0) {
+        if ((s = sync_host_order(c)) != NB_OK) return s;
         NB_CK(c, cudaMemcpyAsync(idx, c->sd.idx, (size_t)*hn * sizeof(int32_t),
                                  cudaMemcpyDeviceToHost, c->stream));
         NB_CK(c, cudaStreamSynchronize(c->stream));
+        // internal indices to the caller's, reported ascending
+        for (int32_t k = 0; k < *hn; ++k) idx[k] = c->h_perm[idx[k]];
+        std::sort(idx, idx + *hn);
     }
     return NB_OK;
 }
@@ -795,24 +1005,45 @@ nb_status nb_force(nb_ctx* c, int32_t n_act, const int32_t* idx, double* acc, do
         for (int32_t k = 1; k < n_act; ++k)
             if (idx[k] <= idx[k - 1])
                 return fail(c, NB_EINVAL, "ensemble force needs idx strictly ascending");
-    const int32_t* idx_dev = idx;
+    std::vector<int32_t> perm;  // host list: entry k of the internal list is idx[perm[k]]
     if (n_act > 0 && !on_device) {
-        NB_CK(c, cudaMemcpyAsync(c->idx_user, idx, (size_t)n_act * sizeof(int32_t),
+        if ((s = sync_host_order(c)) != NB_OK) return s;
+        const std::vector<int32_t> sorted = internal_sorted(c, n_act, idx, perm);
+        NB_CK(c, cudaMemcpyAsync(c->idx_user, sorted.data(), (size_t)n_act * sizeof(int32_t),
                                  cudaMemcpyHostToDevice, c->stream));
-        idx_dev = c->idx_user;
+        NB_CK(c, cudaStreamSynchronize(c->stream));  // sorted is a copy source
+    } else if (n_act > 0) {
+        NB_CK(c, nb::map_index_launch(idx, c->idx_user, n_act, c->n, c->inv_dev, c->stream));
     }
     NB_CK(c, nb::set_scalars_launch(c->n_act_user, n_act, nullptr, 0.0, c->stream));
     if (n_act > 0 &&
-        (s = run_force_list(c, c->prec, c->jl, idx_dev, c->n_act_user, n_act)) != NB_OK)
+        (s = run_force_list(c, c->prec, c->jl, c->idx_user, c->n_act_user, n_act)) != NB_OK)
         return s;
     c->last_force_n_act = n_act;
-    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    if (n_act > 0) {
+    if (n_act > 0 && on_device) {
+        const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
         if (acc) NB_CK(c, cudaMemcpyAsync(acc, c->acc1, 3 * (size_t)n_act * sizeof(double), k, c->stream));
         if (jerk) NB_CK(c, cudaMemcpyAsync(jerk, c->jerk1, 3 * (size_t)n_act * sizeof(double), k, c->stream));
         if (pot) NB_CK(c, cudaMemcpyAsync(pot, c->pot1, (size_t)n_act * sizeof(double), k, c->stream));
     }
-    if (!on_device) return check_status(c);
+    if (on_device || n_act == 0) return on_device ? NB_OK : check_status(c);
+    // rows of the internal (ascending) list back to the caller's order
+    std::vector<double> h(7 * (size_t)n_act);
+    const auto d2h = cudaMemcpyDeviceToHost;
+    NB_CK(c, cudaMemcpyAsync(h.data(), c->acc1, 3 * (size_t)n_act * sizeof(double), d2h, c->stream));
+    NB_CK(c, cudaMemcpyAsync(h.data() + 3 * (size_t)n_act, c->jerk1,
+                             3 * (size_t)n_act * sizeof(double), d2h, c->stream));
+    NB_CK(c, cudaMemcpyAsync(h.data() + 6 * (size_t)n_act, c->pot1, (size_t)n_act * sizeof(double),
+                             d2h, c->stream));
+    if ((s = check_status(c)) != NB_OK) return s;
+    for (int32_t k = 0; k < n_act; ++k) {
+        const size_t u = static_cast<size_t>(perm[k]);
+        for (int d = 0; d < 3; ++d) {
+            if (acc) acc[3 * u + d] = h[3 * (size_t)k + d];
+            if (jerk) jerk[3 * u + d] = h[3 * ((size_t)n_act + k) + d];
+        }
+        if (pot) pot[u] = h[6 * (size_t)n_act + k];
+    }
     return NB_OK;
 }
 
@@ -832,13 +1063,24 @@ nb_status nb_correct(nb_ctx* c, double t, int32_t n_act, const int32_t* idx, con
         return fail(c, NB_ESTATE, "no nb_force result for a block of %d particles", n_act);
     if (n_act == 0) return NB_OK;
     if (!on_device && (s = validate_idx(c, n_act, idx)) != NB_OK) return s;
-    const int32_t* idx_dev = idx;
+    const int32_t* idx_dev = c->idx_user;
     const double* a1 = acc ? acc : c->acc1;
     const double* j1 = jerk ? jerk : c->jerk1;
-    if (!on_device) {
-        NB_CK(c, cudaMemcpyAsync(c->idx_user, idx, (size_t)n_act * sizeof(int32_t),
+    std::vector<int32_t> list, perm;
+    if (on_device) {
+        NB_CK(c, nb::map_index_launch(idx, c->idx_user, n_act, c->n, c->inv_dev, c->stream));
+    } else {
+        // internal indices; without acc / jerk the last nb_force rows are used,
+        // which follow the ascending internal order nb_force gave a host list
+        if ((s = sync_host_order(c)) != NB_OK) return s;
+        if (acc) {
+            list.resize(n_act);
+            for (int32_t k = 0; k < n_act; ++k) list[k] = c->h_inv[idx[k]];
+        } else {
+            list = internal_sorted(c, n_act, idx, perm);
+        }
+        NB_CK(c, cudaMemcpyAsync(c->idx_user, list.data(), (size_t)n_act * sizeof(int32_t),
                                  cudaMemcpyHostToDevice, c->stream));
-        idx_dev = c->idx_user;
         if (acc) {
             NB_CK(c, cudaMemcpyAsync(c->acc1, acc, 3 * (size_t)n_act * sizeof(double),
                                      cudaMemcpyHostToDevice, c->stream));
@@ -861,7 +1103,8 @@ nb_status nb_correct(nb_ctx* c, double t, int32_t n_act, const int32_t* idx, con
     ca.status = c->status_dev;
     NB_CK(c, nb::correct_launch(c->st, ca, c->stream));
     c->last_force_n_act = -1;
-    if (!on_device) return check_status(c);
+    c->order_fresh = false;  // the positions move
+    if (!on_device) return check_status(c);  // (also keeps list alive until the copy ran)
     return NB_OK;
 }
 
@@ -877,6 +1120,9 @@ nb_status nb_step_until(nb_ctx* c, double t_end, uint64_t* n_steps, uint64_t* n_
     nb_status s = enter(c, true);
     if (s != NB_OK) return s;
     if (!std::isfinite(t_end)) return fail(c, NB_EINVAL, "t_end not finite");
+    // the stored order from the current positions (a function of them, so a
+    // run resumed from a checkpoint gets the order the original had)
+    if ((s = refresh_order(c)) != NB_OK) return s;
     NB_CK(c, cudaMemsetAsync(c->ctr64, 0, 2 * sizeof(unsigned long long), c->stream));
     if (!c->step_graph || c->graph_t_end != t_end) {
         if ((s = build_step_graph(c, t_end)) != NB_OK) return s;
@@ -996,7 +1242,8 @@ nb_status nb_set_ensemble(nb_ctx* c, int32_t k, const int64_t* offsets, const do
     NB_CK(c, cudaMemcpyAsync(c->cl.jsrc, jsrc.data(), n_pad * sizeof(int32_t), h2d, c->stream));
     NB_CK(c, cudaMemsetAsync(c->status_dev, 0, sizeof(uint32_t), c->stream));
     NB_CK(c, cudaMemsetAsync(c->counters, 0, c->counter_words * sizeof(uint32_t), c->stream));
-    NB_CK(c, cudaMemcpyAsync(c->st.m, m, n * sizeof(double), h2d, c->stream));
+    if ((s = load_order(c, r)) != NB_OK) return s;
+    if ((s = upload_perm(c, m, c->st.m, 1, 0)) != NB_OK) return s;
     if ((s = upload_vec3(c, r, c->st.x, 0)) != NB_OK) return s;
     if ((s = upload_vec3(c, v, c->st.v, 0)) != NB_OK) return s;
     NB_CK(c, cudaMemsetAsync(c->st.a, 0, 3 * n * sizeof(double), c->stream));
@@ -1117,13 +1364,28 @@ nb_status nb_autotune(nb_ctx* c, nb_tuning* out)
     NB_CK(c, nb::predict_launch(c->st, c->prec, c->jl, c->cfg.G, nullptr, *ht, nullptr, c->stream,
                                 c->ens ? &c->cl : nullptr));
     NB_CK(c, nb::iota_launch(c->idx_user, n, c->n_act_user, c->stream));
+    // Hybrid: the shapes are timed with the integration guard idle (no noise
+    // history), the steady state of an integration; the probe evaluations
+    // write noise estimates of their own, so the particles' estimates are
+    // kept aside and put back afterwards.
+    double* hq_keep = nullptr;
+    if (c->prec == Prec::HYBRID) {
+        if (!c->order_buf) NB_CK(c, cudaMalloc(&c->order_buf, (17 * n + 1) * sizeof(double)));
+        hq_keep = c->order_buf;
+        NB_CK(c, cudaMemcpyAsync(hq_keep, c->st.hq, n * sizeof(double), cudaMemcpyDeviceToDevice,
+                                 c->stream));
+        NB_CK(c, cudaMemsetAsync(c->st.hq, 0, n * sizeof(double), c->stream));
+    }
     cudaEvent_t e0, e1;
     NB_CK(c, cudaEventCreate(&e0));
     NB_CK(c, cudaEventCreate(&e1));
     nb_status st = NB_OK;
     for (int q = 0; q < 4 && st == NB_OK; ++q) {
-        if (cudaSuccess != nb::set_scalars_launch(c->n_act_user, probes[q], nullptr, 0.0, c->stream))
-            st = fail(c, NB_ECUDA, "autotune: set n_act");
+        // a probe block: particles spread evenly over the stored order, like
+        // the scattered members of a real block step
+        if (cudaSuccess != nb::strided_list_launch(c->idx_user, probes[q], n, c->n_act_user,
+                                                   c->stream))
+            st = fail(c, NB_ECUDA, "autotune: probe list");
         for (auto& cd : cands) {
             if (st != NB_OK) break;
             if (c->ens && cudaSuccess != nb::plan_launch(c->cl, c->idx_user, c->n_act_user,
@@ -1147,6 +1409,9 @@ nb_status nb_autotune(nb_ctx* c, nb_tuning* out)
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (hq_keep)
+        NB_CK(c, cudaMemcpyAsync(c->st.hq, hq_keep, n * sizeof(double), cudaMemcpyDeviceToDevice,
+                                 c->stream));
     if (st != NB_OK) return st;
     if ((s = check_status(c)) != NB_OK) return s;
     // Best shape per bucket; ties go to the smaller grid (listed first).  The
@@ -1202,6 +1467,16 @@ nb_status nb_autotune(nb_ctx* c, nb_tuning* out)
         out->small_us = bucket_us(*best[0], 0, split_probe);
         out->large_us = bucket_us(*best[1], split_probe, 4);
     }
+    return NB_OK;
+}
+
+nb_status nb_spatial_order(nb_ctx* c, int32_t* order)
+{
+    nb_status s = enter(c, true);
+    if (s != NB_OK) return s;
+    if (!order) return fail(c, NB_EINVAL, "NULL order");
+    if ((s = sync_host_order(c)) != NB_OK) return s;
+    std::memcpy(order, c->h_perm.data(), c->n * sizeof(int32_t));
     return NB_OK;
 }
 

@@ -34,6 +34,7 @@ struct ForceParams {
     int64_t n_pad;
     const int32_t* idx;
     const int32_t* n_act_dev;
+    const float4* tile_box;   // HYBRID: per-tile bounds (two float4 per tile)
     double* acc;
     double* jerk;
     double* pot;
@@ -76,6 +77,7 @@ struct ForceParams {
 template <int IT>
 struct PolicyFP64 {
     static constexpr bool GUARDED = false;
+    static constexpr int MIN_CTAS = 1;
     static constexpr int NARR = 2;
     __host__ __device__ static constexpr int elem(int a) { return a < 2 ? 32 : 0; }
     static constexpr int TILE_BYTES = TJ * 64;
@@ -161,6 +163,7 @@ struct PolicyFP64 {
 template <int IT, bool SPJ = false>
 struct PolicyMixed {
     static constexpr bool GUARDED = false;
+    static constexpr int MIN_CTAS = 1;
     static constexpr int NARR = 3;
     __host__ __device__ static constexpr int elem(int a) { return a < 2 ? 16 : (a == 2 ? 8 : 0); }
     static constexpr int TILE_BYTES = TJ * 40;
@@ -321,9 +324,23 @@ __device__ __forceinline__ void ds_load_i(const ForceParams& f, int p, DSI& s)
     s.vxl = D.x, s.vyl = D.y, s.vzl = D.z;
 }
 
+// (jh + jl) - (ih + il) for double-single values whose hi parts share no
+// grid (the hybrid layout's velocities): TwoSum of the hi parts, the lo
+// parts added to its error, renormalised by TwoSum.
+__device__ __forceinline__ void ds_diff(float jh, float jl, float ih, float il, float& dh,
+                                        float& dl)
+{
+    float s, e;
+    two_sum(jh, -ih, s, e);
+    e = __fadd_rn(e, __fsub_rn(jl, il));
+    two_sum(s, e, dh, dl);
+}
+
 // One pair (i = s, j = layout record A..D at slot j) in double-single,
 // added to the accumulators.  With MASK the self pair (j == s.p) adds zero.
-template <bool MASK>
+// GRIDV: the velocity hi parts lie on the layout's grid (DS); otherwise
+// (HYBRID) they are plain FP32 values.
+template <bool MASK, bool GRIDV = true>
 __device__ __forceinline__ void ds_pair(const float4& A, const float4& B, const float4& C,
                                         const float4& D, const DSI& s, float e2h, float e2l,
                                         int64_t j, DSAccs& ac)
@@ -333,9 +350,15 @@ __device__ __forceinline__ void ds_pair(const float4& A, const float4& B, const 
     grid_diff(A.y, B.y, s.yh, s.yl, dyh, dyl);
     grid_diff(A.z, B.z, s.zh, s.zl, dzh, dzl);
     float vxh, vxl, vyh, vyl, vzh, vzl;
-    grid_diff(C.x, D.x, s.vxh, s.vxl, vxh, vxl);
-    grid_diff(C.y, D.y, s.vyh, s.vyl, vyh, vyl);
-    grid_diff(C.z, D.z, s.vzh, s.vzl, vzh, vzl);
+    if (GRIDV) {
+        grid_diff(C.x, D.x, s.vxh, s.vxl, vxh, vxl);
+        grid_diff(C.y, D.y, s.vyh, s.vyl, vyh, vyl);
+        grid_diff(C.z, D.z, s.vzh, s.vzl, vzh, vzl);
+    } else {
+        ds_diff(C.x, D.x, s.vxh, s.vxl, vxh, vxl);
+        ds_diff(C.y, D.y, s.vyh, s.vyl, vyh, vyl);
+        ds_diff(C.z, D.z, s.vzh, s.vzl, vzh, vzl);
+    }
     // r^2 = dx^2 + dy^2 + dz^2 + eps^2 (all terms >= 0)
     float px, pxe, py, pye, pz, pze;
     ds_mul(dxh, dxl, dxh, dxl, px, pxe);
@@ -410,6 +433,7 @@ __device__ __forceinline__ void ds_pair(const float4& A, const float4& B, const 
 template <int IT>
 struct PolicyDS {
     static constexpr bool GUARDED = false;
+    static constexpr int MIN_CTAS = 1;
     static constexpr int NARR = 4;
     __host__ __device__ static constexpr int elem(int a) { return a < 4 ? 16 : 0; }
     static constexpr int TILE_BYTES = TJ * 64;
@@ -456,23 +480,39 @@ struct PolicyDS {
 // with r^2 the softened distance, V_i = |v_i| + sqrt(3) B_v >= |v_j - v_i|,
 // and |a_i|, |j_i| the particle's values at its last correction (its state
 // a, j); a particle with no such values yet (a = j = 0) treats every pair as
-// near, so the first evaluation after a load is plain DS.  The FP32 terms of
-// the far pairs are summed in runs of HY_RUN consecutive j and each run is
-// folded into the double-single accumulators, so far-field rounding stays at
-// the FP32 level of each term and never accumulates; the rsqrt estimate is
-// refined once through its residual.  The near pairs, which carry the
-// cancellation that FP32 cannot resolve, are marked during the FP32 pass and
-// evaluated in DS after it, each lane walking its own list, so the warp runs
-// the DS pair about max-over-lanes(near pairs in the tile) times per tile.
+// near, so the first evaluation after a load is plain DS.
+//
+// Two tile paths.  The j layout is in spatial order (a space-filling curve
+// per system) and the active list in the same order, so a tile's 64 j and a
+// warp's i are each close together in space.  The predictor stores a box
+// around each tile and its largest G m and (G m)^(2/3); when the box is far
+// enough from every i of the warp that no pair of the tile can be near by
+// the test above (the far-tile test, evaluated with the box's distance and
+// largest masses), the warp takes the far path: every pair in FP32 with no
+// per-pair test, terms summed in FP32 runs of HY_RUN_FAR j.  Any other tile
+// takes the near path: the per-pair test, far pairs in FP32 in runs of
+// HY_RUN_NEAR j (short: these tiles hold the largest far terms, side by side
+// in space, and long runs of them raise the rounding of the run sums enough
+// to switch on the integration guard below for many more particles), near
+// pairs marked in a per-lane mask
+// during the FP32 pass and evaluated in double-single after it, each lane
+// walking its own list, so the warp runs the DS pair about
+// max-over-lanes(near pairs in the tile) times per tile.  Each run is folded
+// into double-single accumulators, so far-field rounding stays at the FP32
+// level of each term and never accumulates; the rsqrt estimate is refined
+// once through its residual.  Velocity differences of far pairs are taken
+// between FP32 velocities (the layout stores v as its FP32 value plus the
+// rest), positions as double-single differences.
 constexpr float HY_THETA = 0.1f;
-constexpr int HY_RUN = 16;
+constexpr int HY_RUN_FAR = 32;
+constexpr int HY_RUN_NEAR = 8;
 // Integration guard.  The Hermite interpolation divides a0 - a1 by dt^3
 // (crackle), so an absolute force noise da sets a floor 12 da / dt^3 under
 // the crackle that Eq. timestep sees; once that floor rivals the true value
 // the timestep shrinks and keeps shrinking.  Each evaluation estimates its
 // far-field noise from the FP32 roundings it made, bounded through the run
-// sums: with b = G m / r^2 the |a| bound of a far pair, each HY_RUN-term run
-// contributes (sum of its b)^2 >= sum of its b^2, and the estimate is
+// sums: with b = G m / r^2 the |a| bound of a far pair, each run contributes
+// (sum of its b)^2 >= sum of its b^2, and the estimate is
 // 2 u sqrt(sum over runs of (sum b)^2).  When the last estimate exceeds
 // HY_GUARD * eta |j| dt / 12 (the crackle scale of the particle's current
 // step), the particle is evaluated entirely in double-single.  Switching
@@ -500,6 +540,9 @@ struct HybridAcc : DSAccs {
 template <int IT>
 struct PolicyHybrid {
     static constexpr bool GUARDED = true;
+    // registers capped so that three CTAs (two i per lane) or four (one)
+    // fit on an SM
+    static constexpr int MIN_CTAS = IT > 1 ? 3 : 4;
     static constexpr int NARR = 4;
     __host__ __device__ static constexpr int elem(int a) { return a < 4 ? 16 : 0; }
     static constexpr int TILE_BYTES = TJ * 64;
@@ -562,9 +605,85 @@ struct PolicyHybrid {
 
     __device__ static bool guarded(const I& s) { return s.all_near; }
 
-    // GUARD: some lane of the warp has the integration guard on (rare); the
-    // other instantiation assumes none has, so near is the natural test and
-    // the noise estimate reuses the far-pair factor m / r.
+    // The far-tile test of one i particle against tile T's box: true when
+    // no pair of the tile can be near.  The box holds the tiles' grid-rounded
+    // positions; the 0.999 keeps the test on the safe side of that rounding.
+    __device__ static bool tile_far(const ForceParams& f, const I& s, int64_t T, float e2h)
+    {
+        if (s.p < 0) return true;  // an empty lane
+        const float4 lo = __ldg(f.tile_box + 2 * T);
+        const float4 hi = __ldg(f.tile_box + 2 * T + 1);
+        const float dx = fmaxf(fmaxf(lo.x - s.xh, s.xh - hi.x), 0.f);
+        const float dy = fmaxf(fmaxf(lo.y - s.yh, s.yh - hi.y), 0.f);
+        const float dz = fmaxf(fmaxf(lo.z - s.zh, s.zh - hi.z), 0.f);
+        const float d2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, e2h))) * 0.999f;
+        return d2 >= fmaxf(lo.w * s.ca, hi.w * s.cj);
+    }
+
+    // Far path: no pair of the tile is near for any lane of the warp, and no
+    // lane's own particle is in it.  Lane slice sl takes records sl + S u.
+    template <int S>
+    __device__ static void far_tile(const unsigned char* buf, const double eps2d, I (&is)[IT],
+                                    Acc (&ac)[IT], int sl)
+    {
+        constexpr int R = TJ / S;
+        constexpr int RUN = R < HY_RUN_FAR ? R : HY_RUN_FAR;
+        const float4* sA = reinterpret_cast<const float4*>(buf);
+        const float4* sB = reinterpret_cast<const float4*>(buf + TJ * 16);
+        const float4* sC = reinterpret_cast<const float4*>(buf + TJ * 32);
+        const float e2h = static_cast<float>(eps2d);
+#pragma unroll 1
+        for (int u0 = 0; u0 < R; u0 += RUN) {
+            float ax[IT], ay[IT], az[IT], jx[IT], jy[IT], jz[IT], ph[IT], bs[IT];
+#pragma unroll
+            for (int q = 0; q < IT; ++q) ax[q] = ay[q] = az[q] = jx[q] = jy[q] = jz[q] = ph[q] = bs[q] = 0.f;
+#pragma unroll 4
+            for (int du = 0; du < RUN; ++du) {
+                const int k = sl + S * (u0 + du);
+                const float4 A = sA[k];
+                const float4 B = sB[k];
+                const float4 C = sC[k];
+#pragma unroll
+                for (int q = 0; q < IT; ++q) {
+                    const DSI& s = is[q];
+                    const float dx = (A.x - s.xh) + (B.x - s.xl);
+                    const float dy = (A.y - s.yh) + (B.y - s.yl);
+                    const float dz = (A.z - s.zh) + (B.z - s.zl);
+                    const float dvx = C.x - s.vxh;
+                    const float dvy = C.y - s.vyh;
+                    const float dvz = C.z - s.vzh;
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, e2h)));
+                    float y = rsqrtf(r2);
+                    const float h = fmaf(-r2, y * y, 1.f);
+                    y = fmaf(0.5f * y, h, y);
+                    const float mr = A.w * y;
+                    bs[q] = fmaf(mr, y, bs[q]);
+                    const float ri2 = y * y;
+                    const float g = mr * ri2;
+                    const float rv = fmaf(dx, dvx, fmaf(dy, dvy, dz * dvz));
+                    const float t = rv * (-3.f * ri2);
+                    ax[q] = fmaf(g, dx, ax[q]);
+                    ay[q] = fmaf(g, dy, ay[q]);
+                    az[q] = fmaf(g, dz, az[q]);
+                    jx[q] = fmaf(g, fmaf(t, dx, dvx), jx[q]);
+                    jy[q] = fmaf(g, fmaf(t, dy, dvy), jy[q]);
+                    jz[q] = fmaf(g, fmaf(t, dz, dvz), jz[q]);
+                    ph[q] += mr;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < IT; ++q) {
+                ac[q].ax.fold(ax[q]), ac[q].ay.fold(ay[q]), ac[q].az.fold(az[q]);
+                ac[q].jx.fold(jx[q]), ac[q].jy.fold(jy[q]), ac[q].jz.fold(jz[q]);
+                ac[q].ph.fold(ph[q]);
+                ac[q].q = fmaf(bs[q], bs[q], ac[q].q);
+            }
+        }
+    }
+
+    // Near path.  GUARD: some lane of the warp has the integration guard on
+    // (rare); the other instantiation assumes none has, so near is the
+    // natural test and the noise estimate reuses the far-pair factor m / r.
     template <bool MASK, bool GUARD, int S>
     __device__ static void tile(const unsigned char* buf, int64_t j0, const double eps2d,
                                 I (&is)[IT], Acc (&ac)[IT], int sl)
@@ -572,7 +691,7 @@ struct PolicyHybrid {
         static_assert(TJ == 64, "one 64-bit near mask per lane and tile");
         // this lane's records: tile slots sl + S u, u < R, in runs of RUN
         constexpr int R = TJ / S;
-        constexpr int RUN = R < HY_RUN ? R : HY_RUN;
+        constexpr int RUN = R < HY_RUN_NEAR ? R : HY_RUN_NEAR;
         const float4* sA = reinterpret_cast<const float4*>(buf);
         const float4* sB = reinterpret_cast<const float4*>(buf + TJ * 16);
         const float4* sC = reinterpret_cast<const float4*>(buf + TJ * 32);
@@ -599,7 +718,6 @@ struct PolicyHybrid {
                 const float4 A = sA[k];
                 const float4 B = sB[k];
                 const float4 C = sC[k];
-                const float4 D = sD[k];
 #pragma unroll
                 for (int q = 0; q < IT; ++q) {
                     const DSI& s = is[q];
@@ -607,9 +725,9 @@ struct PolicyHybrid {
                     const float dx = (A.x - s.xh) + (B.x - s.xl);
                     const float dy = (A.y - s.yh) + (B.y - s.yl);
                     const float dz = (A.z - s.zh) + (B.z - s.zl);
-                    const float dvx = (C.x - s.vxh) + (D.x - s.vxl);
-                    const float dvy = (C.y - s.vyh) + (D.y - s.vyl);
-                    const float dvz = (C.z - s.vzh) + (D.z - s.vzl);
+                    const float dvx = C.x - s.vxh;
+                    const float dvy = C.y - s.vyh;
+                    const float dvz = C.z - s.vzh;
                     const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, e2h)));
                     const bool self = MASK && (j0 + k == s.p);
                     const bool nat = r2 < fmaxf(A.w * is[q].ca, C.w * is[q].cj);
@@ -674,7 +792,8 @@ struct PolicyHybrid {
                         hi &= hi - 1u;
                     }
                     const int k = sl + S * u;
-                    ds_pair<false>(sA[k], sB[k], sC[k], sD[k], is[q], e2h, e2l, j0 + k, ac[q]);
+                    ds_pair<false, false>(sA[k], sB[k], sC[k], sD[k], is[q], e2h, e2l, j0 + k,
+                                          ac[q]);
                 }
             }
         }
@@ -721,13 +840,39 @@ struct GroupInfo {
     int64_t act_begin, act_count;  // active-list entries
     int64_t tile0, ntiles;         // flattened tiles of the group
     int64_t jtile0;                // first j tile of its system in the j layout
+    int64_t jstride;               // tile walk: rank k -> j tile k * jstride mod ntiles
     int64_t pj_shift;              // j-layout slot of particle p = p + pj_shift
     double eps2;
 };
 
+// A group walks its system's j tiles in the order k -> k * stride mod
+// ntiles (a bijection, the stride being a prime that does not divide
+// ntiles).  In the spatial order the tiles next to a group in space, where
+// its near pairs are, sit side by side; walked in index order they would
+// all fall to the one or two warps whose stream-K range covers them, and
+// those warps would finish last.  The stride spreads them over the group's
+// whole range, so equal tile counts per warp are also equal work.
+__device__ __forceinline__ int64_t tile_stride(int64_t nt)
+{
+    const uint32_t m = static_cast<uint32_t>(nt);
+    if (m <= 8u) return 1;
+    const uint32_t primes[8] = {37u, 41u, 43u, 47u, 53u, 59u, 61u, 67u};
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        if (m % primes[k] != 0u) return static_cast<int64_t>(primes[k] % m);
+    return 1;
+}
+
+// The j tile of rank k (0 <= k < ntiles) of a group.
+__device__ __forceinline__ int64_t tile_at(const GroupInfo& g, int64_t k)
+{
+    return static_cast<int64_t>((static_cast<uint64_t>(k) * static_cast<uint64_t>(g.jstride)) %
+                                static_cast<uint64_t>(g.ntiles));
+}
+
 // One system over the whole j layout: groups of GI consecutive entries.
 struct UniformPlan {
-    int64_t n_act, G, NT, T;
+    int64_t n_act, G, NT, T, jstride;
     double eps2;
     int GI;
     __device__ void init(const ForceParams& f, int gi)
@@ -737,6 +882,7 @@ struct UniformPlan {
         G = (n_act + GI - 1) / GI;
         NT = f.n_pad / TJ;
         T = G * NT;
+        jstride = tile_stride(NT);
         eps2 = f.eps2;
     }
     __device__ int64_t find(int64_t t) const { return t / NT; }
@@ -748,6 +894,7 @@ struct UniformPlan {
         gi.tile0 = g * NT;
         gi.ntiles = NT;
         gi.jtile0 = 0;
+        gi.jstride = jstride;
         gi.pj_shift = 0;
         gi.eps2 = eps2;
         return gi;
@@ -782,6 +929,7 @@ struct ClusterPlan {
         gi.tile0 = f->grp_tile0[g];
         gi.ntiles = f->grp_tile0[g + 1] - gi.tile0;
         gi.jtile0 = f->cl_joff[c] / TJ;
+        gi.jstride = tile_stride(gi.ntiles);
         gi.pj_shift = f->cl_joff[c] - f->cl_off[c];
         gi.eps2 = f->cl_eps2[c];
         return gi;
@@ -792,7 +940,7 @@ struct ClusterPlan {
 // of the warp's IW = 32 / S, j slice sl; the S slices of an i are summed with
 // shuffles before the split-group tree.
 template <class K, int IT, int S, class Plan>
-__global__ void __launch_bounds__(FORCE_WARPS * 32)
+__global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
     force_kernel(const ForceParams f)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -838,12 +986,18 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
     int64_t lg = g;
     GroupInfo lgi = gi;
     int64_t tl = t0;
+    int64_t lpos = tile_at(lgi, tl - lgi.tile0);  // j tile of the next load
     auto issue_next = [&](int s) {
-        while (tl >= lgi.tile0 + lgi.ntiles) lgi = plan.group(++lg);
+        if (tl >= lgi.tile0 + lgi.ntiles) {
+            while (tl >= lgi.tile0 + lgi.ntiles) lgi = plan.group(++lg);
+            lpos = tile_at(lgi, tl - lgi.tile0);
+        }
         // (self-test: with unfed_first_tile the first tile is never staged,
         // so its barrier never completes and the bounded wait runs out)
         if (lane == 0 && !(f.unfed_first_tile && tl == t0))
-            issue_tile<K>(f, ring + s * K::TILE_BYTES, &bars[s], lgi.jtile0 + (tl - lgi.tile0));
+            issue_tile<K>(f, ring + s * K::TILE_BYTES, &bars[s], lgi.jtile0 + lpos);
+        lpos += lgi.jstride;
+        if (lpos >= lgi.ntiles) lpos -= lgi.ntiles;
         ++tl;
     };
     for (int s = 0; s < K::STAGES && t0 + s < t1; ++s) issue_next(s);
@@ -852,6 +1006,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
     typename K::Acc ac[IT];
     bool fresh = true;
     bool guard_any = false;  // some lane of this group has the hybrid guard on
+    int64_t cpos = 0;        // j tile of the tile being computed (rank in the walk)
 
     for (int64_t t = t0; t < t1; ++t) {
         const int64_t k = t - t0;
@@ -863,6 +1018,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
         }
         if (fresh) {
             fresh = false;
+            cpos = tile_at(gi, t - gi.tile0);
 #pragma unroll
             for (int q = 0; q < IT; ++q) {
                 const int64_t a = gi.act_begin + q * IW + ir;
@@ -899,8 +1055,10 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
             }
             return;
         }
-        const int64_t jt = t - gi.tile0;
-        const int64_t j0 = (gi.jtile0 + jt) * TJ;
+        const int64_t jt = t - gi.tile0;  // rank of the tile in the group's walk
+        const int64_t j0 = (gi.jtile0 + cpos) * TJ;
+        cpos += gi.jstride;
+        if (cpos >= gi.ntiles) cpos -= gi.ntiles;
         bool self_here = false;
 #pragma unroll
         for (int q = 0; q < IT; ++q)
@@ -908,7 +1066,17 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32)
         const unsigned char* buf = ring + s * K::TILE_BYTES;
         const bool mask_self = __any_sync(0xffffffffu, self_here);
         if constexpr (K::GUARDED) {
-            if (guard_any) {
+            // the far path when no lane's particle is in the tile, no lane
+            // has the guard on and the tile is far from every lane's i
+            bool far = !mask_self && !guard_any;
+            if (far) {
+                const float e2h = static_cast<float>(gi.eps2);
+#pragma unroll
+                for (int q = 0; q < IT; ++q) far &= K::tile_far(f, is[q], j0 / TJ, e2h);
+                far = __all_sync(0xffffffffu, far);
+            }
+            if (far) K::template far_tile<S>(buf, gi.eps2, is, ac, sl);
+            else if (guard_any) {
                 if (mask_self) K::template tile<true, true, S>(buf, j0, gi.eps2, is, ac, sl);
                 else K::template tile<false, true, S>(buf, j0, gi.eps2, is, ac, sl);
             } else {
@@ -1156,6 +1324,7 @@ cudaError_t force_launch(const ForceArgs& a, cudaStream_t s)
     f.n_pad = a.n_pad;
     f.idx = a.idx;
     f.n_act_dev = a.n_act_dev;
+    f.tile_box = a.tile_box;
     f.acc = a.acc;
     f.jerk = a.jerk;
     f.pot = a.pot;
@@ -1182,7 +1351,8 @@ cudaError_t force_launch(const ForceArgs& a, cudaStream_t s)
     f.st_dt = a.st_dt;
     f.st_hq = a.st_hq;
     f.eta = a.eta;
-    if (a.prec == Prec::HYBRID && (!f.st_a || !f.st_j || !f.bound_v || !f.st_dt || !f.st_hq))
+    if (a.prec == Prec::HYBRID &&
+        (!f.st_a || !f.st_j || !f.bound_v || !f.st_dt || !f.st_hq || !f.tile_box))
         return cudaErrorInvalidValue;
     void* args[] = {&f};
     return cudaLaunchKernel(fn, dim3(a.grid), dim3(FORCE_WARPS * 32), args,

@@ -149,19 +149,53 @@ __device__ __forceinline__ void grid_split_ds(Dsf x, float q, float inv_q, float
     lo = __fadd_rn(__fsub_rn(x.hi, hi), x.lo);
 }
 
+// Largest and smallest of a value over the 64 threads of a tile (two
+// warps): butterfly within each warp, then the two warps through shared
+// memory.  Every thread of the block must call it.
+struct TileExtent {
+    float lo[3], hi[3], gm, g23;
+};
+
+__device__ __forceinline__ void tile_extent_reduce(TileExtent& e)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            e.lo[c] = fminf(e.lo[c], __shfl_xor_sync(0xffffffffu, e.lo[c], o));
+            e.hi[c] = fmaxf(e.hi[c], __shfl_xor_sync(0xffffffffu, e.hi[c], o));
+        }
+        e.gm = fmaxf(e.gm, __shfl_xor_sync(0xffffffffu, e.gm, o));
+        e.g23 = fmaxf(e.g23, __shfl_xor_sync(0xffffffffu, e.g23, o));
+    }
+    __shared__ TileExtent other;
+    if (threadIdx.x == 32) other = e;
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        e.lo[c] = fminf(e.lo[c], other.lo[c]);
+        e.hi[c] = fmaxf(e.hi[c], other.hi[c]);
+    }
+    e.gm = fmaxf(e.gm, other.gm);
+    e.g23 = fmaxf(e.g23, other.g23);
+}
+
 template <int PREC>
 __global__ void predict_ds_kernel(const StateDev st, const JLayout jl, const double G,
                                   const unsigned long long* t_bits, const double t_host,
                                   const int32_t* n_act_dev, const int32_t* jsrc,
                                   const int32_t* cluster_of)
 {
+    constexpr bool HYB = PREC == static_cast<int>(Prec::HYBRID);
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // j-layout slot
+    // (the hybrid layout's tile boxes need every thread of the tile: one
+    // block is one tile, and n_pad is a whole number of tiles)
     if (q >= st.n_pad) return;
     const int64_t n = st.n;
     const int64_t i = jsrc ? jsrc[q] : (q < n ? q : -1);
     // an empty block step writes nothing; the ghosts' check is cheap, the
     // particles' comes after their state loads so that they need not wait
-    if (i < 0) {  // a ghost: far away, zero mass
+    if (i < 0 && !HYB) {  // a ghost: far away, zero mass
         if (n_act_dev && *n_act_dev == 0) return;
         const float g = static_cast<float>(GHOST_POS);
         if (PREC == static_cast<int>(Prec::MIXED)) {
@@ -176,26 +210,33 @@ __global__ void predict_ds_kernel(const StateDev st, const JLayout jl, const dou
         }
         return;
     }
-    const double t = t_bits ? dkey_decode(t_bits[cluster_of ? cluster_of[i] : 0]) : t_host;
-    const Dsf h = dsf_of(t - st.t[i]);  // exact: both times are dyadic
-    const Dsf gm = dsf_fma(dsf_of(G), dsf_of(st.m[i]), Dsf{0.f, 0.f});
-    const Dsf sixth = {0x1.555556p-3f, -0x1.555556p-28f};  // 1/6 to ~2^-50
-    float qx, iqx;
-    grid_quantum_f(st.bound[0], qx, iqx);
     float hi[3], lo[3];
     Dsf vp[3];
+    Dsf gm = {0.f, 0.f};
+    if (i >= 0) {
+        const double t = t_bits ? dkey_decode(t_bits[cluster_of ? cluster_of[i] : 0]) : t_host;
+        const Dsf h = dsf_of(t - st.t[i]);  // exact: both times are dyadic
+        gm = dsf_fma(dsf_of(G), dsf_of(st.m[i]), Dsf{0.f, 0.f});
+        const Dsf sixth = {0x1.555556p-3f, -0x1.555556p-28f};  // 1/6 to ~2^-50
+        float qx, iqx;
+        grid_quantum_f(st.bound[0], qx, iqx);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const Dsf x = dsf_of(st.x[c * n + i]), v = dsf_of(st.v[c * n + i]);
-        const Dsf a = dsf_of(st.a[c * n + i]), j = dsf_of(st.j[c * n + i]);
-        // Eq. xpred: x + h (v + h (a / 2 + h j / 6)); Eq. vpred: v + h (a + h j / 2)
-        Dsf u = dsf_fma(j, sixth, Dsf{0.f, 0.f});
-        u = dsf_fma(h, u, dsf_scale(a, 0.5f));
-        u = dsf_fma(h, u, v);
-        grid_split_ds(dsf_fma(h, u, x), qx, iqx, hi[c], lo[c]);
-        vp[c] = dsf_fma(h, dsf_fma(h, dsf_scale(j, 0.5f), a), v);
+        for (int c = 0; c < 3; ++c) {
+            const Dsf x = dsf_of(st.x[c * n + i]), v = dsf_of(st.v[c * n + i]);
+            const Dsf a = dsf_of(st.a[c * n + i]), j = dsf_of(st.j[c * n + i]);
+            // Eq. xpred: x + h (v + h (a / 2 + h j / 6)); Eq. vpred: v + h (a + h j / 2)
+            Dsf u = dsf_fma(j, sixth, Dsf{0.f, 0.f});
+            u = dsf_fma(h, u, dsf_scale(a, 0.5f));
+            u = dsf_fma(h, u, v);
+            grid_split_ds(dsf_fma(h, u, x), qx, iqx, hi[c], lo[c]);
+            vp[c] = dsf_fma(h, dsf_fma(h, dsf_scale(j, 0.5f), a), v);
+        }
+    } else {  // a ghost of the hybrid layout
+        hi[0] = hi[1] = hi[2] = static_cast<float>(GHOST_POS);
+        lo[0] = lo[1] = lo[2] = 0.f;
+        vp[0] = vp[1] = vp[2] = Dsf{0.f, 0.f};
     }
-    if (n_act_dev && *n_act_dev == 0) return;
+    if (n_act_dev && *n_act_dev == 0) return;  // the same for every thread
     if (PREC == static_cast<int>(Prec::MIXED)) {
         static_cast<float4*>(jl.arr[0])[q] = make_float4(hi[0], hi[1], hi[2], __fadd_rn(gm.hi, gm.lo));
         static_cast<float4*>(jl.arr[1])[q] =
@@ -203,17 +244,46 @@ __global__ void predict_ds_kernel(const StateDev st, const JLayout jl, const dou
         static_cast<float2*>(jl.arr[2])[q] =
             make_float2(__fadd_rn(vp[1].hi, vp[1].lo), __fadd_rn(vp[2].hi, vp[2].lo));
     } else {
-        float qv, iqv;
-        grid_quantum_f(st.bound[1], qv, iqv);
         float vh[3], vl[3];
+        if (HYB) {
+            // the FP32 value of v and the rest: far pairs difference FP32
+            // velocities, near pairs the whole double-single value
 #pragma unroll
-        for (int c = 0; c < 3; ++c) grid_split_ds(vp[c], qv, iqv, vh[c], vl[c]);
+            for (int c = 0; c < 3; ++c) {
+                vh[c] = __fadd_rn(vp[c].hi, vp[c].lo);
+                vl[c] = __fadd_rn(__fsub_rn(vp[c].hi, vh[c]), vp[c].lo);
+            }
+        } else {
+            float qv, iqv;
+            grid_quantum_f(st.bound[1], qv, iqv);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) grid_split_ds(vp[c], qv, iqv, vh[c], vl[c]);
+        }
         static_cast<float4*>(jl.arr[0])[q] = make_float4(hi[0], hi[1], hi[2], gm.hi);
         static_cast<float4*>(jl.arr[1])[q] = make_float4(lo[0], lo[1], lo[2], gm.lo);
         // (G m)^(2/3): the hybrid precision's near-pair test
         const float g23 = cbrtf(gm.hi);
         static_cast<float4*>(jl.arr[2])[q] = make_float4(vh[0], vh[1], vh[2], g23 * g23);
         static_cast<float4*>(jl.arr[3])[q] = make_float4(vl[0], vl[1], vl[2], 0.f);
+        if (HYB) {
+            // the tile's box (hi parts; a ghost adds nothing) and its
+            // largest G m and (G m)^(2/3), for the force kernel's test of
+            // whether a whole tile is far from an i particle
+            TileExtent e;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                e.lo[c] = i >= 0 ? hi[c] : CUDART_INF_F;
+                e.hi[c] = i >= 0 ? hi[c] : -CUDART_INF_F;
+            }
+            e.gm = gm.hi;
+            e.g23 = g23 * g23;
+            tile_extent_reduce(e);
+            if (threadIdx.x == 0) {
+                const int64_t T = q / TJ;
+                st.tile_box[2 * T] = make_float4(e.lo[0], e.lo[1], e.lo[2], e.gm);
+                st.tile_box[2 * T + 1] = make_float4(e.hi[0], e.hi[1], e.hi[2], e.g23);
+            }
+        }
     }
 }
 
@@ -273,8 +343,10 @@ cudaError_t predict_launch(const StateDev& st, Prec p, const JLayout& jl, double
 {
     if (st.n_pad <= 0) return cudaSuccess;
     // Small blocks: the predictor is FP64-pipe bound per SM (GB300's FP64
-    // rate is a small fraction of FP32), so it should reach every SM.
-    const int threads = 64;
+    // rate is a small fraction of FP32), so it should reach every SM.  One
+    // block is one tile of the j layout.
+    constexpr int threads = 64;
+    static_assert(threads == TJ, "the hybrid predictor reduces each tile in one block");
     const unsigned blocks = static_cast<unsigned>((st.n_pad + threads - 1) / threads);
     const int32_t* jsrc = cl ? cl->jsrc : nullptr;
     const int32_t* cof = cl ? cl->cluster_of : nullptr;
@@ -284,11 +356,17 @@ cudaError_t predict_launch(const StateDev& st, Prec p, const JLayout& jl, double
         break;
     case Prec::MIXED:
     case Prec::MIXED_SPJ:  // same j layout
-        predict_ds_kernel<1><<<blocks, threads, 0, s>>>(st, jl, G, t_bits, t_host, n_act_dev, jsrc, cof);
+        predict_ds_kernel<static_cast<int>(Prec::MIXED)>
+            <<<blocks, threads, 0, s>>>(st, jl, G, t_bits, t_host, n_act_dev, jsrc, cof);
         break;
     case Prec::DS:
-    case Prec::HYBRID:  // same j layout
-        predict_ds_kernel<2><<<blocks, threads, 0, s>>>(st, jl, G, t_bits, t_host, n_act_dev, jsrc, cof);
+        predict_ds_kernel<static_cast<int>(Prec::DS)>
+            <<<blocks, threads, 0, s>>>(st, jl, G, t_bits, t_host, n_act_dev, jsrc, cof);
+        break;
+    case Prec::HYBRID:
+        if (!st.tile_box) return cudaErrorInvalidValue;
+        predict_ds_kernel<static_cast<int>(Prec::HYBRID)>
+            <<<blocks, threads, 0, s>>>(st, jl, G, t_bits, t_host, n_act_dev, jsrc, cof);
         break;
     }
     return cudaGetLastError();
@@ -1254,6 +1332,118 @@ cudaError_t snapshot_launch(const StateDev& st, double* buf, bool to_buf, cudaSt
     const int64_t want = (3 * st.n + threads - 1) / threads;  // the longest row
     const unsigned bx = static_cast<unsigned>(want < 512 ? want : 512);
     snapshot_kernel<<<dim3(bx, 9), threads, 0, s>>>(st, buf, to_buf ? 1 : 0);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// The context's particles are stored in its spatial order: internal index k
+// holds the caller's particle perm[k].  These kernels move arrays across
+// that boundary and re-order the stored state.
+// ---------------------------------------------------------------------------
+__global__ void permute_in_kernel(const double* __restrict__ src, double* __restrict__ dst,
+                                  int64_t n, int w, const int32_t* __restrict__ perm)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < w * n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e / n, k = e - c * n;
+        dst[e] = src[w * static_cast<int64_t>(perm[k]) + c];
+    }
+}
+
+__global__ void permute_out_kernel(const double* __restrict__ src, double* __restrict__ dst,
+                                   int64_t n, int w, const int32_t* __restrict__ perm)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < w * n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e / n, k = e - c * n;
+        dst[w * static_cast<int64_t>(perm[k]) + c] = src[e];
+    }
+}
+
+cudaError_t permute_in_launch(const double* src_aos, double* dst_soa, int64_t n, int w,
+                              const int32_t* perm, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const int64_t want = (w * n + 255) / 256;
+    permute_in_kernel<<<static_cast<unsigned>(want < 2048 ? want : 2048), 256, 0, s>>>(
+        src_aos, dst_soa, n, w, perm);
+    return cudaGetLastError();
+}
+
+cudaError_t permute_out_launch(const double* src_soa, double* dst_aos, int64_t n, int w,
+                               const int32_t* perm, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const int64_t want = (w * n + 255) / 256;
+    permute_out_kernel<<<static_cast<unsigned>(want < 2048 ? want : 2048), 256, 0, s>>>(
+        src_soa, dst_aos, n, w, perm);
+    return cudaGetLastError();
+}
+
+__global__ void map_index_kernel(const int32_t* __restrict__ in, int32_t* __restrict__ out,
+                                 int32_t count, int64_t n, const int32_t* __restrict__ inv)
+{
+    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= count) return;
+    const int32_t u = in[a];
+    out[a] = (u >= 0 && u < n) ? inv[u] : -1;  // -1: flagged by the kernel that reads it
+}
+
+cudaError_t map_index_launch(const int32_t* in, int32_t* out, int32_t count, int64_t n,
+                             const int32_t* inv, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    map_index_kernel<<<static_cast<unsigned>((count + 255) / 256), 256, 0, s>>>(in, out, count,
+                                                                                n, inv);
+    return cudaGetLastError();
+}
+
+// Row r of the snapshot layout (m, x, v, a, j as 3 rows each, t, dt, hq,
+// nkey: 17 rows of n words) gathered through map into the state.
+__global__ void reorder_state_kernel(StateDev st, const double* __restrict__ buf,
+                                     const int32_t* __restrict__ map)
+{
+    const int64_t n = st.n;
+    const int r = blockIdx.y;
+    unsigned long long* dst;
+    if (r == 0) dst = reinterpret_cast<unsigned long long*>(st.m);
+    else if (r < 4) dst = reinterpret_cast<unsigned long long*>(st.x) + (r - 1) * n;
+    else if (r < 7) dst = reinterpret_cast<unsigned long long*>(st.v) + (r - 4) * n;
+    else if (r < 10) dst = reinterpret_cast<unsigned long long*>(st.a) + (r - 7) * n;
+    else if (r < 13) dst = reinterpret_cast<unsigned long long*>(st.j) + (r - 10) * n;
+    else if (r == 13) dst = reinterpret_cast<unsigned long long*>(st.t);
+    else if (r == 14) dst = reinterpret_cast<unsigned long long*>(st.dt);
+    else if (r == 15) dst = reinterpret_cast<unsigned long long*>(st.hq);
+    else dst = st.nkey;
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(buf) + r * n;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x)
+        dst[k] = src[map[k]];
+}
+
+cudaError_t reorder_state_launch(const StateDev& st, const double* buf, const int32_t* map,
+                                 cudaStream_t s)
+{
+    if (st.n <= 0) return cudaSuccess;
+    const int64_t want = (st.n + 255) / 256;
+    reorder_state_kernel<<<dim3(static_cast<unsigned>(want < 512 ? want : 512), 17), 256, 0, s>>>(
+        st, buf, map);
+    return cudaGetLastError();
+}
+
+__global__ void strided_list_kernel(int32_t* idx, int64_t k, int64_t n, int32_t* n_act_dev)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < k) idx[i] = static_cast<int32_t>(i * n / k);
+    if (i == 0 && n_act_dev) *n_act_dev = static_cast<int32_t>(k);
+}
+
+cudaError_t strided_list_launch(int32_t* idx, int64_t k, int64_t n, int32_t* n_act_dev,
+                                cudaStream_t s)
+{
+    const int64_t m = k > 0 ? k : 1;
+    strided_list_kernel<<<static_cast<unsigned>((m + 255) / 256), 256, 0, s>>>(idx, k, n,
+                                                                               n_act_dev);
     return cudaGetLastError();
 }
 

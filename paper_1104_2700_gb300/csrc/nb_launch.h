@@ -45,6 +45,10 @@ struct StateDev {
     // Per particle, the order-preserving key of its next time t_i + dt_i,
     // kept by every writer of t and dt so that step 1 compares integers.
     unsigned long long* nkey = nullptr;
+    // HYBRID only: per j tile, a box around its predicted positions and its
+    // largest masses (written by the predictor): tile_box[2T] = (lo_x, lo_y,
+    // lo_z, max G m), tile_box[2T + 1] = (hi_x, hi_y, hi_z, max (G m)^(2/3)).
+    float4* tile_box = nullptr;
 };
 
 // bound[0] = max |a_k|, bound[1] = max |b_k| over k < count (float bits,
@@ -60,9 +64,12 @@ cudaError_t next_key_launch(const StateDev& st, cudaStream_t s);
 //          y_lo, z_lo, vx), arr[2] = float2 (vy, vz)
 //   Position (and DS velocity) hi/lo pairs are grid-aligned splits
 //   (grid_split): every hi part of the layout lies on one power-of-two grid.
-//   DS, HYBRID: arr[0] = float4 (x_hi, y_hi, z_hi, Gm_hi), arr[1] = float4
+//   DS:    arr[0] = float4 (x_hi, y_hi, z_hi, Gm_hi), arr[1] = float4
 //          (x_lo, y_lo, z_lo, Gm_lo), arr[2] = float4 (vx_hi, vy_hi, vz_hi,
 //          (Gm)^(2/3)), arr[3] = float4 (vx_lo, vy_lo, vz_lo, 0)
+//   HYBRID: as DS, except that the velocity is split as hi = fl32(v) (its
+//          FP32 value, the far pairs' operand) and lo = fl32(v - hi), off
+//          the grid.
 struct JLayout {
     void* arr[4] = {nullptr, nullptr, nullptr, nullptr};
 };
@@ -127,6 +134,7 @@ struct ForceArgs {
     int64_t n_pad = 0;   // j count incl. ghosts, multiple of TJ
     const int32_t* idx = nullptr;
     const int32_t* n_act_dev = nullptr;
+    const float4* tile_box = nullptr;  // HYBRID: per-tile bounds (StateDev::tile_box)
     double* acc = nullptr;   // [n_act][3]
     double* jerk = nullptr;  // [n_act][3]
     double* pot = nullptr;   // [n_act]
@@ -225,8 +233,29 @@ cudaError_t energy_launch(const StateDev& st, const double* pot_all, double* par
 cudaError_t aos_to_soa_launch(const double* aos, double* soa, int64_t n, cudaStream_t s);
 cudaError_t soa_to_aos_launch(const double* soa, double* aos, int64_t n, cudaStream_t s);
 cudaError_t iota_launch(int32_t* idx, int64_t n, int32_t* n_act_dev, cudaStream_t s);
+// idx[i] = floor(i n / k), i < k: k particles spread evenly over the stored
+// order (ascending); *n_act_dev = k.
+cudaError_t strided_list_launch(int32_t* idx, int64_t k, int64_t n, int32_t* n_act_dev,
+                                cudaStream_t s);
 // Copy the whole state (17 n words: m, x, v, a, j, t, dt, hq, nkey, then
 // the two bounds) to (to_buf) or from a device buffer of 17 n + 1 doubles.
 cudaError_t snapshot_launch(const StateDev& st, double* buf, bool to_buf, cudaStream_t s);
+
+// The context stores its particles in its spatial order (internal index k
+// holds the caller's particle perm[k]).  Boundary permutations of arrays of
+// w doubles per particle:
+//   permute_in:  dst_soa[c n + k] = src_aos[w perm[k] + c]   (caller -> state)
+//   permute_out: dst_aos[w perm[k] + c] = src_soa[c n + k]   (state -> caller)
+cudaError_t permute_in_launch(const double* src_aos, double* dst_soa, int64_t n, int w,
+                              const int32_t* perm, cudaStream_t s);
+cudaError_t permute_out_launch(const double* src_soa, double* dst_aos, int64_t n, int w,
+                               const int32_t* perm, cudaStream_t s);
+// Caller indices to internal ones: out[a] = inv[in[a]] (-1 outside [0, n)).
+cudaError_t map_index_launch(const int32_t* in, int32_t* out, int32_t count, int64_t n,
+                             const int32_t* inv, cudaStream_t s);
+// Re-order the state from a snapshot buf (snapshot_launch layout): every
+// per-particle word of internal index k takes the value of index map[k].
+cudaError_t reorder_state_launch(const StateDev& st, const double* buf, const int32_t* map,
+                                 cudaStream_t s);
 
 }  // namespace nb

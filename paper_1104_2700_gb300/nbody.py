@@ -103,6 +103,7 @@ def load(path: str = LIB_PATH):
         "nb_snapshot_bytes": (c_int64, [P]),
         "nb_snapshot": (c_int32, [P, P]),
         "nb_restore": (c_int32, [P, P]),
+        "nb_spatial_order": (c_int32, [P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -234,6 +235,10 @@ def nb_snapshot(ctx, buf):
 
 def nb_restore(ctx, buf):
     return load().nb_restore(ctx, buf)
+
+
+def nb_spatial_order(ctx, order):
+    return load().nb_spatial_order(ctx, order)
 
 
 def nb_measure_peaks(device, fp32_ref, fp64_ref):
@@ -369,6 +374,12 @@ class Context:
         tun = NbTuning()
         self._ck(nb_autotune(self.handle, ctypes.byref(tun)))
         return {name: getattr(tun, name) for name, _ in NbTuning._fields_}
+
+    def spatial_order(self):
+        """The particles in the context's spatial (j-layout slot) order."""
+        order = np.empty(self.n, dtype=np.int32)
+        self._ck(nb_spatial_order(self.handle, order.ctypes.data_as(c_void_p)))
+        return order
 
     def predict(self, t):
         self._ck(nb_predict(self.handle, float(t)))

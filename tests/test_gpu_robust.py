@@ -68,7 +68,8 @@ def test_snapshot_restore_replays_bitwise(gpu, prec):
     with gpu.Context(prec) as ctx:
         ctx.set_particles(m, r, v, 1.0 / 64, 0.02)
         nbytes = ctx.snapshot_bytes()
-        assert nbytes == (17 * n + 1) * 8
+        # the state (17 words per particle and the bounds) and its spatial order
+        assert nbytes == (18 * n + 1) * 8
         buf = torch.empty(nbytes // 8, dtype=torch.float64, device="cuda")
         ctx.snapshot(buf)
         first = ctx.step_until(1.0 / 16)
