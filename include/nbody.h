@@ -130,7 +130,7 @@ typedef struct nb_tuning {
 } nb_tuning;
 
 /* Autotuner: time every candidate launch shape of the force kernel on the
- * loaded system (probe blocks of 32, 256, 2048 and min(n, 16384) particles
+ * loaded system (probe blocks of 32, 256, 2048 and min(n, 65536) particles
  * spread evenly over the context's stored order, nb_spatial_order, like the
  * scattered members of a block step; for the hybrid precision with the
  * integration guard idle, as in a steady integration) and keep the fastest for each bucket, with the bucket

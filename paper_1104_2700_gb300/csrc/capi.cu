@@ -1328,7 +1328,7 @@ nb_status nb_autotune(nb_ctx* c, nb_tuning* out)
     const int32_t probes[4] = {static_cast<int32_t>(std::min<int64_t>(32, n)),
                                static_cast<int32_t>(std::min<int64_t>(256, n)),
                                static_cast<int32_t>(std::min<int64_t>(2048, n)),
-                               static_cast<int32_t>(std::min<int64_t>(16384, n))};
+                               static_cast<int32_t>(std::min<int64_t>(65536, n))};
     // candidates: (i per thread, j split) x CTAs per SM; two i per thread
     // only for MIXED and HYBRID single systems, and only without a j split
     std::vector<std::pair<int, int>> shapes = {{1, 1}, {1, 2}, {1, 4}, {1, 8}};

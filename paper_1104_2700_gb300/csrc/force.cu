@@ -78,6 +78,7 @@ template <int IT>
 struct PolicyFP64 {
     static constexpr bool GUARDED = false;
     static constexpr int MIN_CTAS = 1;
+    static constexpr int CHUNKS = 1;
     static constexpr int NARR = 2;
     __host__ __device__ static constexpr int elem(int a) { return a < 2 ? 32 : 0; }
     static constexpr int TILE_BYTES = TJ * 64;
@@ -164,6 +165,7 @@ template <int IT, bool SPJ = false>
 struct PolicyMixed {
     static constexpr bool GUARDED = false;
     static constexpr int MIN_CTAS = 1;
+    static constexpr int CHUNKS = 1;
     static constexpr int NARR = 3;
     __host__ __device__ static constexpr int elem(int a) { return a < 2 ? 16 : (a == 2 ? 8 : 0); }
     static constexpr int TILE_BYTES = TJ * 40;
@@ -434,6 +436,7 @@ template <int IT>
 struct PolicyDS {
     static constexpr bool GUARDED = false;
     static constexpr int MIN_CTAS = 1;
+    static constexpr int CHUNKS = 1;
     static constexpr int NARR = 4;
     __host__ __device__ static constexpr int elem(int a) { return a < 4 ? 16 : 0; }
     static constexpr int TILE_BYTES = TJ * 64;
@@ -489,7 +492,9 @@ struct PolicyDS {
 // enough from every i of the warp that no pair of the tile can be near by
 // the test above (the far-tile test, evaluated with the box's distance and
 // largest masses), the warp takes the far path: every pair in FP32 with no
-// per-pair test, terms summed in FP32 runs of HY_RUN_FAR j.  Any other tile
+// per-pair test, terms summed in FP32 runs of HY_RUN_FAR j (the whole tile:
+// each term is small there, so one run per tile keeps the rounding of the
+// run sums at the level of the shorter runs of the near path).  Any other tile
 // takes the near path: the per-pair test, far pairs in FP32 in runs of
 // HY_RUN_NEAR j (short: these tiles hold the largest far terms, side by side
 // in space, and long runs of them raise the rounding of the run sums enough
@@ -504,7 +509,7 @@ struct PolicyDS {
 // between FP32 velocities (the layout stores v as its FP32 value plus the
 // rest), positions as double-single differences.
 constexpr float HY_THETA = 0.1f;
-constexpr int HY_RUN_FAR = 32;
+constexpr int HY_RUN_FAR = 64;
 constexpr int HY_RUN_NEAR = 8;
 // Integration guard.  The Hermite interpolation divides a0 - a1 by dt^3
 // (crackle), so an absolute force noise da sets a floor 12 da / dt^3 under
@@ -543,6 +548,7 @@ struct PolicyHybrid {
     // registers capped so that three CTAs (two i per lane) or four (one)
     // fit on an SM
     static constexpr int MIN_CTAS = IT > 1 ? 3 : 4;
+    static constexpr int CHUNKS = 4;  // tiles of unequal cost
     static constexpr int NARR = 4;
     __host__ __device__ static constexpr int elem(int a) { return a < 4 ? 16 : 0; }
     static constexpr int TILE_BYTES = TJ * 64;
@@ -828,11 +834,16 @@ constexpr int RB = 16;
 constexpr int RLEVELS = 4;  // RB^RLEVELS >= any warp count
 constexpr int MAX_NV = 8;   // values a policy reduces (scratch is sized for the most)
 
-// Warp that owns flattened tile x when T tiles are cut into Pu ranges.
+// Chunk that holds flattened tile x when T tiles are cut into Pu ranges.
 __device__ __forceinline__ int64_t owner_warp(int64_t x, int64_t T, int64_t Pu)
 {
     return ((x + 1) * Pu - 1) / T;
 }
+
+// Stream-K chunks per warp (largest; policies choose theirs) and the
+// fewest tiles a chunk is cut down to.
+constexpr int MAX_CHUNKS = 4;
+constexpr int64_t CHUNK_MIN_TILES = 32;
 
 // One i-group of a launch: up to 32*IT consecutive active-list entries of
 // one system and the j tiles of that system, placed at flattened tile0.
@@ -872,6 +883,7 @@ __device__ __forceinline__ int64_t tile_at(const GroupInfo& g, int64_t k)
 
 // One system over the whole j layout: groups of GI consecutive entries.
 struct UniformPlan {
+    static constexpr bool CHUNKED = true;
     int64_t n_act, G, NT, T, jstride;
     double eps2;
     int GI;
@@ -901,8 +913,11 @@ struct UniformPlan {
     }
 };
 
-// Independent systems (ensemble): group descriptors from plan_launch.
+// Independent systems (ensemble): group descriptors from plan_launch.  Its
+// groups are small and many, so one stream-K range per warp already mixes
+// them (no chunks).
 struct ClusterPlan {
+    static constexpr bool CHUNKED = false;
     const ForceParams* f;
     int64_t G, T;
     __device__ void init(const ForceParams& fp, int)
@@ -964,10 +979,15 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
     plan.init(f, GI);
     const int64_t T = plan.T;
     if (T <= 0) return;
-    const int64_t Pu = P < T ? P : T;
-    if (w >= Pu) return;
-    const int64_t t0 = T * w / Pu;
-    const int64_t t1 = T * (w + 1) / Pu;
+    // The flattened (group, tile) space is cut into NCH equal chunks (the
+    // stream-K split) and warp w takes chunks w, w + P, ...: KC chunks from
+    // KC stretches of the space, so that regions of dearer tiles (the near
+    // tiles of the hybrid precision crowd where the particles do) are shared
+    // by all warps.  Chunks keep at least CHUNK_MIN_TILES tiles.
+    int64_t KC = Plan::CHUNKED ? K::CHUNKS : 1;
+    while (KC > 1 && T < P * KC * CHUNK_MIN_TILES) --KC;
+    const int64_t NCH = P * KC < T ? P * KC : T;
+    if (w >= NCH) return;
 
     unsigned char* wsm = smem + (size_t)wib * WarpSmem<K>::BYTES;
     uint64_t* bars = reinterpret_cast<uint64_t*>(wsm);
@@ -979,6 +999,15 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
         fence_mbar_init();
     }
     __syncwarp();
+
+    typename K::I is[IT];
+    typename K::Acc ac[IT];
+    int64_t used = 0;    // tiles this warp has consumed: ring slot used % STAGES
+    int64_t issued = 0;  // tiles this warp has staged
+
+    for (int64_t ch = w; ch < NCH; ch += P) {
+    const int64_t t0 = T * ch / NCH;
+    const int64_t t1 = T * (ch + 1) / NCH;
     // Compute cursor (g, gi) and load cursor (lg, lgi): both start at the
     // group of tile t0; the load cursor runs STAGES tiles ahead.
     int64_t g = plan.find(t0);
@@ -987,29 +1016,30 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
     GroupInfo lgi = gi;
     int64_t tl = t0;
     int64_t lpos = tile_at(lgi, tl - lgi.tile0);  // j tile of the next load
-    auto issue_next = [&](int s) {
+    auto issue_next = [&]() {
         if (tl >= lgi.tile0 + lgi.ntiles) {
             while (tl >= lgi.tile0 + lgi.ntiles) lgi = plan.group(++lg);
             lpos = tile_at(lgi, tl - lgi.tile0);
         }
-        // (self-test: with unfed_first_tile the first tile is never staged,
-        // so its barrier never completes and the bounded wait runs out)
-        if (lane == 0 && !(f.unfed_first_tile && tl == t0))
+        const int s = static_cast<int>(issued % K::STAGES);
+        // (self-test: with unfed_first_tile the warp's first tile is never
+        // staged, so its barrier never completes and the bounded wait runs out)
+        if (lane == 0 && !(f.unfed_first_tile && issued == 0))
             issue_tile<K>(f, ring + s * K::TILE_BYTES, &bars[s], lgi.jtile0 + lpos);
         lpos += lgi.jstride;
         if (lpos >= lgi.ntiles) lpos -= lgi.ntiles;
         ++tl;
+        ++issued;
     };
-    for (int s = 0; s < K::STAGES && t0 + s < t1; ++s) issue_next(s);
+    // the ring is empty at a chunk's start: every staged tile was consumed
+    for (int s = 0; s < K::STAGES && t0 + s < t1; ++s) issue_next();
 
-    typename K::I is[IT];
-    typename K::Acc ac[IT];
     bool fresh = true;
     bool guard_any = false;  // some lane of this group has the hybrid guard on
     int64_t cpos = 0;        // j tile of the tile being computed (rank in the walk)
 
     for (int64_t t = t0; t < t1; ++t) {
-        const int64_t k = t - t0;
+        const int64_t k = used;
         const int s = static_cast<int>(k % K::STAGES);
         const uint32_t parity = static_cast<uint32_t>((k / K::STAGES) & 1);
         while (t >= gi.tile0 + gi.ntiles) {
@@ -1046,15 +1076,16 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
         if (!__all_sync(0xffffffffu, ok)) {
             if (lane == 0) atomicOr(f.status, ST_TIMEOUT);
             // Give up on this launch, but first let every bulk copy this warp
-            // still has in flight (tiles k .. tl - t0 - 1) land, each wait
-            // bounded again, so no copy outlives the CTA.
-            for (int64_t kk = k; kk < tl - t0; ++kk) {
+            // still has in flight (ring positions k .. issued - 1) land, each
+            // wait bounded again, so no copy outlives the CTA.
+            for (int64_t kk = k; kk < issued; ++kk) {
                 if (f.unfed_first_tile && kk == 0) continue;  // never issued
                 mbar_wait_bounded(&bars[kk % K::STAGES],
                                   static_cast<uint32_t>((kk / K::STAGES) & 1));
             }
             return;
         }
+        ++used;
         const int64_t jt = t - gi.tile0;  // rank of the tile in the group's walk
         const int64_t j0 = (gi.jtile0 + cpos) * TJ;
         cpos += gi.jstride;
@@ -1090,7 +1121,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
         __syncwarp();
         if (t + K::STAGES < t1) {
             if (lane == 0) fence_proxy_async_smem();
-            issue_next(s);
+            issue_next();
         }
 
         if (jt == gi.ntiles - 1 || t == t1 - 1) {
@@ -1100,8 +1131,8 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
             // the chunk in order and carries the sum one level up.  Level-L
             // entry r lives in scratch slot key + r * RB^L (the first slot of
             // the chunk it replaces); each level has its own counters.
-            const int64_t wf = owner_warp(gi.tile0, T, Pu);
-            const int64_t wl = owner_warp(gi.tile0 + gi.ntiles - 1, T, Pu);
+            const int64_t wf = owner_warp(gi.tile0, T, NCH);
+            const int64_t wl = owner_warp(gi.tile0 + gi.ntiles - 1, T, NCH);
             constexpr int NV = K::NV;
             using TV = typename K::TV;
             TV v[IT][NV];
@@ -1116,7 +1147,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
                     for (int c = 0; c < NV; ++c) tree_xor(v[q][c], o);
             const int64_t key = wf + g;
             int64_t kk = wl - wf + 1;  // entries at this level
-            int64_t r = w - wf;        // my entry at this level
+            int64_t r = ch - wf;       // my entry at this level
             int64_t stride = 1;
             bool final_here = true;
             for (int level = 0; kk > 1; ++level) {
@@ -1186,6 +1217,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
             }
         }
     }
+    }  // chunks
 }
 
 // ---------------------------------------------------------------------------
@@ -1298,12 +1330,13 @@ size_t force_scratch_doubles(int it, int64_t n_act_max, int warps)
 {
     const int64_t GI = 32 * it;
     const int64_t G = (n_act_max + GI - 1) / GI;
-    return (size_t)(warps + G) * MAX_NV * GI;
+    return (size_t)((int64_t)warps * MAX_CHUNKS + G) * MAX_NV * GI;
 }
 
 int64_t force_counter_stride(int64_t n_act_max, int warps)
 {
-    return warps + (n_act_max + 3) / 4;  // groups are at least 32 / 8 wide
+    // chunks + groups (groups are at least 32 / 8 wide)
+    return (int64_t)warps * MAX_CHUNKS + (n_act_max + 3) / 4;
 }
 
 int64_t force_counter_entries(int64_t n_act_max, int warps)
