@@ -286,6 +286,24 @@ nb_status nb_energy_systems(nb_ctx* ctx, int32_t fp64_potential, double* kin, do
  * nb_set_ensemble, 0 before either). */
 int32_t nb_num_systems(const nb_ctx* ctx);
 
+/* j-partitioned force (the paper's parallel scheme splits the j sum of
+ * Eqs. acc, jrk, pot over processes, Sec. 4-5): from this call on, every
+ * force evaluation of the context precision (nb_force and the force step of
+ * nb_block_step / nb_step_until) sums only over part `part` of `parts`
+ * contiguous ranges of the j layout's tiles (tiles [T part / parts,
+ * T (part + 1) / parts) of the T = ceil(n / 64) tiles, in the context's
+ * stored order).  The parts of all `parts` contexts holding the same state
+ * add up to the whole force; a distributed driver keeps the state
+ * replicated, sums acc, jerk and pot over the parts (one all-reduce of
+ * 7 n_act doubles per block step) and then corrects (nb_correct with the
+ * summed acc / jerk).  nb_energy, nb_autotune and the load-time
+ * evaluations always use every j.  With the hybrid precision each part
+ * keeps its own far-field noise estimates (the integration guard acts on
+ * its part).  part 0 of 1 (the default, restored by every load) is the
+ * whole sum.  Errors: NB_EINVAL (part outside [0, parts), more parts than
+ * tiles, an ensemble), NB_ESTATE (nothing loaded). */
+nb_status nb_set_j_part(nb_ctx* ctx, int32_t part, int32_t parts);
+
 /* The context's spatial order (no counterpart in the paper): the context
  * stores its particles in this order, order[k] being the caller's index of
  * the k-th stored particle (n host entries).  Within each system the

@@ -96,6 +96,9 @@ struct nb_ctx {
     std::vector<int64_t> order_off;
     bool order_fresh = false;       // no step has moved the particles since
     bool host_order_stale = false;
+    // j partition (nb_set_j_part): force evaluations of the context
+    // precision sum over part j_part of j_parts contiguous ranges of tiles.
+    int32_t j_part = 0, j_parts = 1;
 };
 
 namespace {
@@ -348,6 +351,11 @@ nb_status run_force(nb_ctx* c, Prec p, const nb::JLayout& jl, const int32_t* idx
                     const int32_t* n_act_dev, int32_t n_act_host = -1)
 {
     nb::ForceArgs f = force_args(c, p, jl, idx, n_act_dev);
+    if (p == c->prec && c->j_parts > 1) {
+        const int64_t nt = c->n_pad / nb::TJ;
+        f.jt_lo = nt * c->j_part / c->j_parts;
+        f.jt_hi = nt * (c->j_part + 1) / c->j_parts;
+    }
     if (p != c->prec) {  // the FP64 energy pass of a lower-precision context
         f.it = 1;
         f.split = 1;
@@ -716,6 +724,8 @@ nb_status begin_load(nb_ctx* c, int64_t n, double eps, double eta)
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) return fail(c, NB_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
     c->ens = false;
+    c->j_part = 0;
+    c->j_parts = 1;
     nb_status s = ensure_capacity(c, n, (n + nb::TJ - 1) / nb::TJ * nb::TJ, 0);
     if (s != NB_OK) return s;
     c->eps = eps;
@@ -1162,9 +1172,12 @@ nb_status nb_energy(nb_ctx* c, int32_t fp64_potential, double* kin, double* pot)
     NB_CK(c, nb::predict_launch(c->st, p, jl, c->cfg.G, nullptr, *ht, nullptr, c->stream,
                                 c->ens ? &c->cl : nullptr));
     NB_CK(c, nb::iota_launch(c->idx_user, c->n, c->n_act_user, c->stream));
-    if ((s = run_force_list(c, p, jl, c->idx_user, c->n_act_user, static_cast<int32_t>(c->n))) !=
-        NB_OK)
-        return s;
+    // the energy needs the whole potential: no j partition here
+    const int32_t parts = c->j_parts;
+    c->j_parts = 1;
+    s = run_force_list(c, p, jl, c->idx_user, c->n_act_user, static_cast<int32_t>(c->n));
+    c->j_parts = parts;
+    if (s != NB_OK) return s;
     NB_CK(c, nb::energy_launch(c->st, c->pot1, c->energy_partials, c->energy_blocks,
                                c->energy_out, c->energy_ticket, c->stream));
     if (c->ens)
@@ -1223,6 +1236,8 @@ nb_status nb_set_ensemble(nb_ctx* c, int32_t k, const int64_t* offsets, const do
         }
     }
     c->ens = true;
+    c->j_part = 0;
+    c->j_parts = 1;
     nb_status s = ensure_capacity(c, n, n_pad, k);
     if (s != NB_OK) return s;
     // the ensemble plan cuts i-groups of one width for both variants
@@ -1467,6 +1482,23 @@ nb_status nb_autotune(nb_ctx* c, nb_tuning* out)
         out->small_us = bucket_us(*best[0], 0, split_probe);
         out->large_us = bucket_us(*best[1], split_probe, 4);
     }
+    return NB_OK;
+}
+
+nb_status nb_set_j_part(nb_ctx* c, int32_t part, int32_t parts)
+{
+    nb_status s = enter(c, true);
+    if (s != NB_OK) return s;
+    if (parts < 1 || part < 0 || part >= parts)
+        return fail(c, NB_EINVAL, "part %d of %d", part, parts);
+    if (parts > 1 && c->ens)
+        return fail(c, NB_EINVAL, "a j partition works on one system");
+    if (parts > c->n_pad / nb::TJ)
+        return fail(c, NB_EINVAL, "%d parts of %lld j tiles", parts,
+                    static_cast<long long>(c->n_pad / nb::TJ));
+    c->j_part = part;
+    c->j_parts = parts;
+    drop_graph(c);
     return NB_OK;
 }
 

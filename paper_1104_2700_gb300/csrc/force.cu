@@ -66,6 +66,9 @@ struct ForceParams {
     const double* st_dt;
     double* st_hq;
     double eta;
+    // One system: the j tiles [jt_lo, jt_hi) this launch sums over (its part
+    // of a j-partitioned force); jt_hi = 0 means every tile.
+    int64_t jt_lo, jt_hi;
 };
 
 // ---------------------------------------------------------------------------
@@ -884,7 +887,7 @@ __device__ __forceinline__ int64_t tile_at(const GroupInfo& g, int64_t k)
 // One system over the whole j layout: groups of GI consecutive entries.
 struct UniformPlan {
     static constexpr bool CHUNKED = true;
-    int64_t n_act, G, NT, T, jstride;
+    int64_t n_act, G, NT, T, jstride, J0;
     double eps2;
     int GI;
     __device__ void init(const ForceParams& f, int gi)
@@ -892,7 +895,8 @@ struct UniformPlan {
         GI = gi;
         n_act = *f.n_act_dev;
         G = (n_act + GI - 1) / GI;
-        NT = f.n_pad / TJ;
+        J0 = f.jt_hi > 0 ? f.jt_lo : 0;
+        NT = f.jt_hi > 0 ? f.jt_hi - f.jt_lo : f.n_pad / TJ;
         T = G * NT;
         jstride = tile_stride(NT);
         eps2 = f.eps2;
@@ -905,7 +909,7 @@ struct UniformPlan {
         gi.act_count = n_act - gi.act_begin < GI ? n_act - gi.act_begin : GI;
         gi.tile0 = g * NT;
         gi.ntiles = NT;
-        gi.jtile0 = 0;
+        gi.jtile0 = J0;
         gi.jstride = jstride;
         gi.pj_shift = 0;
         gi.eps2 = eps2;
@@ -1384,6 +1388,11 @@ cudaError_t force_launch(const ForceArgs& a, cudaStream_t s)
     f.st_dt = a.st_dt;
     f.st_hq = a.st_hq;
     f.eta = a.eta;
+    f.jt_lo = a.jt_lo;
+    f.jt_hi = a.jt_hi;
+    if (f.jt_hi > 0 && (a.plan.grp_tile0 || f.jt_lo < 0 || f.jt_hi <= f.jt_lo ||
+                        f.jt_hi > f.n_pad / TJ))
+        return cudaErrorInvalidValue;
     if (a.prec == Prec::HYBRID &&
         (!f.st_a || !f.st_j || !f.bound_v || !f.st_dt || !f.st_hq || !f.tile_box))
         return cudaErrorInvalidValue;

@@ -156,6 +156,9 @@ struct ForceArgs {
     const double* st_dt = nullptr;  // integration guard (see PolicyHybrid)
     double* st_hq = nullptr;
     double eta = 0.0;
+    // One system only: sum over the j tiles [jt_lo, jt_hi) of the layout
+    // (a part of a j-partitioned force); jt_hi = 0: every tile.
+    int64_t jt_lo = 0, jt_hi = 0;
 };
 
 cudaError_t force_setup(Prec p, int it, int split);  // one-time attribute setup

@@ -104,6 +104,7 @@ def load(path: str = LIB_PATH):
         "nb_snapshot": (c_int32, [P, P]),
         "nb_restore": (c_int32, [P, P]),
         "nb_spatial_order": (c_int32, [P, P]),
+        "nb_set_j_part": (c_int32, [P, c_int32, c_int32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -239,6 +240,10 @@ def nb_restore(ctx, buf):
 
 def nb_spatial_order(ctx, order):
     return load().nb_spatial_order(ctx, order)
+
+
+def nb_set_j_part(ctx, part, parts):
+    return load().nb_set_j_part(ctx, part, parts)
 
 
 def nb_measure_peaks(device, fp32_ref, fp64_ref):
@@ -380,6 +385,10 @@ class Context:
         order = np.empty(self.n, dtype=np.int32)
         self._ck(nb_spatial_order(self.handle, order.ctypes.data_as(c_void_p)))
         return order
+
+    def set_j_part(self, part, parts):
+        """Sum forces over part `part` of `parts` j ranges (j-partitioned force)."""
+        self._ck(nb_set_j_part(self.handle, int(part), int(parts)))
 
     def predict(self, t):
         self._ck(nb_predict(self.handle, float(t)))
