@@ -87,6 +87,11 @@ def parse_args():
                    help="instead of the sweep: energy error against step count over "
                         "eta (Sec. 4, Fig. err_itg): Plummer N = 1024, eps = 4/N, "
                         "t = 0 -> 0.375")
+    p.add_argument("--jerk-energy-study", action="store_true",
+                   help="instead of the sweep: the N = 262144 Plummer + Salpeter model "
+                        "(eps = 1e-4) integrated to t = 1/8 with the far-field jerk summed "
+                        "in runs folded into double-single sums (hybrid) and in one plain "
+                        "FP32 sum (hybrid_spj): block steps and energy drift (Sec. 4)")
     p.add_argument("--jerk-study", action="store_true",
                    help="instead of the sweep: error distributions of acc, jerk, pot "
                         "with the jerk summed in FP32 or compensated (Sec. 4, "
@@ -674,7 +679,7 @@ def algorithmic_bytes(prec, n_j, n_act):
 # outside its n_act window), correct.
 LAUNCHES_PER_BLOCK_STEP = 6
 DTYPES = {"ds": "f32x2 (double-single on the FP32 pipes)", "mixed": "f32", "fp64": "f64",
-          "mixed_spj": "f32",
+          "mixed_spj": "f32", "hybrid_spj": "f32 (far pairs) + f32x2 double-single (near pairs)",
           "hybrid": "f32 (far pairs) + f32x2 double-single (near pairs)"}
 
 
@@ -1289,9 +1294,52 @@ def run_jerk_study(args):
                       "data": "synthetic", "rows": rows}), flush=True)
 
 
+def run_jerk_energy_study(args):
+    """Sec. 4 reports that summing the jerk in SP or DP makes no significant
+    difference to the energy error up to N = 256K at t = 0.125.  The same
+    comparison on the precision that integrates: the N = 262144 Plummer model
+    with Salpeter masses (eps = 1e-4, eta = 0.02) from t = 0 to 1/8, with the
+    far pairs' jerk folded into double-single sums every run (hybrid) or kept
+    in one plain FP32 sum across each warp's j (hybrid_spj): block steps,
+    interactions per second and the relative energy drift (FP64 potential)."""
+    import torch
+    from paper_1104_2700_gb300 import build as nb_build
+    from paper_1104_2700_gb300 import nbody
+    nb_build.build()
+    wl = ics.SALPETER_N256K
+    t_end = args.t_end if args.t_end is not None else 1.0 / 8
+    m, r, v = wl.particles()
+    modes = [x for x in args.modes.split(",") if x] if args.modes != "mixed,hybrid,ds,fp64" \
+        else ["hybrid", "hybrid_spj"]
+    out = {"study": "jerk accumulation and energy drift (Sec. 4, Fig. err_snp_djerk text)",
+           "workload": wl.name, "n": wl.n, "eps": wl.eps, "eta": wl.eta, "t_end": t_end,
+           "data": "synthetic", "modes": {}}
+    for prec in modes:
+        with nbody.Context(prec) as ctx:
+            ctx.set_particles(m, r, v, wl.eps, wl.eta)
+            ctx.autotune()
+            ctx.set_particles(m, r, v, wl.eps, wl.eta)
+            k0, w0 = ctx.energy(fp64_potential=True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            steps, inter = ctx.step_until(t_end)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            k1, w1 = ctx.energy(fp64_potential=True)
+            st = ctx.get_state()
+        out["modes"][prec] = {
+            "block_steps": int(steps), "interactions": int(inter), "wall_s": wall,
+            "value": inter / wall, "unit": UNIT, "log2_min_dt": float(np.log2(st["dt"].min())),
+            "rel_energy_drift": abs((k1 + w1) - (k0 + w0)) / abs(k0 + w0)}
+        print(json.dumps({"partial": prec, **out["modes"][prec]}), file=sys.stderr, flush=True)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse_args()
-    if args.jerk_study:
+    if args.jerk_energy_study:
+        run_jerk_energy_study(args)
+    elif args.jerk_study:
         run_jerk_study(args)
     elif args.energy_study:
         run_energy_study(args)

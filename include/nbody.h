@@ -68,13 +68,19 @@ typedef enum nb_status {
  *             paper's production kernel does (Sec. 4, Fig. err_snp_djerk);
  *             acceleration and potential are bit-identical to NB_MIXED under
  *             the same launch shape.  For the accumulation study; its jerk
- *             error grows with N. */
+ *             error grows with N.
+ *   NB_HYBRID_SPJ  NB_HYBRID, except that the jerk of the far pairs is summed
+ *             in plain FP32 across each warp's whole run of j instead of in
+ *             runs folded into double-single sums (the same accumulation
+ *             study on the precision that integrates; near pairs and the
+ *             acceleration and potential as in NB_HYBRID). */
 typedef enum nb_precision {
     NB_FP64 = 0,
     NB_MIXED = 1,
     NB_DS = 2,
     NB_HYBRID = 3,
-    NB_MIXED_SPJ = 4
+    NB_MIXED_SPJ = 4,
+    NB_HYBRID_SPJ = 5
 } nb_precision;
 
 typedef struct nb_config {

@@ -245,7 +245,7 @@ nb_status ensure_capacity(nb_ctx* c, int64_t n, int64_t n_pad, int64_t k)
     NB_CK(c, cudaMalloc(&c->st.nkey, n * sizeof(unsigned long long)));
     NB_CK(c, cudaMalloc(&c->perm_dev, n * sizeof(int32_t)));
     NB_CK(c, cudaMalloc(&c->inv_dev, n * sizeof(int32_t)));
-    if (c->prec == Prec::HYBRID)
+    if (nb::is_hybrid(c->prec))
         NB_CK(c, cudaMalloc(&c->st.tile_box, 2 * (n_pad / nb::TJ) * sizeof(float4)));
     // i-groups never mix systems: at most n / 32 + k of them
     const int64_t groups_bound = n + 32 * k;
@@ -703,7 +703,7 @@ nb_status refresh_bounds(nb_ctx* c)
 // the new a, j and dt stores the estimate; its forces are discarded.
 nb_status hybrid_noise_pass(nb_ctx* c, bool ensemble)
 {
-    if (c->prec != Prec::HYBRID) return NB_OK;
+    if (!nb::is_hybrid(c->prec)) return NB_OK;
     NB_CK(c, nb::iota_launch(c->idx_user, c->n, c->n_act_user, c->stream));
     if (ensemble)
         return run_force_list(c, c->prec, c->jl, c->idx_user, c->n_act_user,
@@ -762,7 +762,7 @@ nb_status nb_create(const nb_config* cfg, nb_ctx** out)
 {
     if (!cfg || !out) return NB_EINVAL;
     *out = nullptr;
-    if (cfg->precision < NB_FP64 || cfg->precision > NB_MIXED_SPJ) return NB_EINVAL;
+    if (cfg->precision < NB_FP64 || cfg->precision > NB_HYBRID_SPJ) return NB_EINVAL;
     if (cfg->j_split != 0 && cfg->j_split != 1 && cfg->j_split != 2 && cfg->j_split != 4 &&
         cfg->j_split != 8)
         return NB_EINVAL;
@@ -1347,7 +1347,7 @@ nb_status nb_autotune(nb_ctx* c, nb_tuning* out)
     // candidates: (i per thread, j split) x CTAs per SM; two i per thread
     // only for MIXED and HYBRID single systems, and only without a j split
     std::vector<std::pair<int, int>> shapes = {{1, 1}, {1, 2}, {1, 4}, {1, 8}};
-    if ((nb::is_mixed(c->prec) || c->prec == Prec::HYBRID) && !c->ens) shapes.push_back({2, 1});
+    if ((nb::is_mixed(c->prec) || nb::is_hybrid(c->prec)) && !c->ens) shapes.push_back({2, 1});
     struct Cand {
         int it, split, cps;
         double us[4];
@@ -1384,7 +1384,7 @@ nb_status nb_autotune(nb_ctx* c, nb_tuning* out)
     // write noise estimates of their own, so the particles' estimates are
     // kept aside and put back afterwards.
     double* hq_keep = nullptr;
-    if (c->prec == Prec::HYBRID) {
+    if (nb::is_hybrid(c->prec)) {
         if (!c->order_buf) NB_CK(c, cudaMalloc(&c->order_buf, (17 * n + 1) * sizeof(double)));
         hq_keep = c->order_buf;
         NB_CK(c, cudaMemcpyAsync(hq_keep, c->st.hq, n * sizeof(double), cudaMemcpyDeviceToDevice,

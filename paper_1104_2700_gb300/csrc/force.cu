@@ -510,7 +510,10 @@ struct PolicyDS {
 // level of each term and never accumulates; the rsqrt estimate is refined
 // once through its residual.  Velocity differences of far pairs are taken
 // between FP32 velocities (the layout stores v as its FP32 value plus the
-// rest), positions as double-single differences.
+// rest), positions as double-single differences.  With SPJ the far pairs'
+// jerk is instead one plain FP32 sum across the warp's whole range of j, the
+// paper's accumulation (Sec. 4, Fig. err_snp_djerk), for the study of its
+// effect on an integration.
 constexpr float HY_THETA = 0.1f;
 constexpr int HY_RUN_FAR = 64;
 constexpr int HY_RUN_NEAR = 8;
@@ -545,7 +548,7 @@ struct HybridAcc : DSAccs {
     }
 };
 
-template <int IT>
+template <int IT, bool SPJ = false>
 struct PolicyHybrid {
     static constexpr bool GUARDED = true;
     // registers capped so that three CTAs (two i per lane) or four (one)
@@ -645,7 +648,14 @@ struct PolicyHybrid {
         for (int u0 = 0; u0 < R; u0 += RUN) {
             float ax[IT], ay[IT], az[IT], jx[IT], jy[IT], jz[IT], ph[IT], bs[IT];
 #pragma unroll
-            for (int q = 0; q < IT; ++q) ax[q] = ay[q] = az[q] = jx[q] = jy[q] = jz[q] = ph[q] = bs[q] = 0.f;
+            for (int q = 0; q < IT; ++q) {
+                ax[q] = ay[q] = az[q] = ph[q] = bs[q] = 0.f;
+                if (SPJ) {  // the jerk: one plain FP32 sum across the warp's j
+                    jx[q] = ac[q].jx.hi, jy[q] = ac[q].jy.hi, jz[q] = ac[q].jz.hi;
+                } else {
+                    jx[q] = jy[q] = jz[q] = 0.f;
+                }
+            }
 #pragma unroll 4
             for (int du = 0; du < RUN; ++du) {
                 const int k = sl + S * (u0 + du);
@@ -683,7 +693,11 @@ struct PolicyHybrid {
 #pragma unroll
             for (int q = 0; q < IT; ++q) {
                 ac[q].ax.fold(ax[q]), ac[q].ay.fold(ay[q]), ac[q].az.fold(az[q]);
-                ac[q].jx.fold(jx[q]), ac[q].jy.fold(jy[q]), ac[q].jz.fold(jz[q]);
+                if (SPJ) {
+                    ac[q].jx.hi = jx[q], ac[q].jy.hi = jy[q], ac[q].jz.hi = jz[q];
+                } else {
+                    ac[q].jx.fold(jx[q]), ac[q].jy.fold(jy[q]), ac[q].jz.fold(jz[q]);
+                }
                 ac[q].ph.fold(ph[q]);
                 ac[q].q = fmaf(bs[q], bs[q], ac[q].q);
             }
@@ -718,7 +732,12 @@ struct PolicyHybrid {
             uint32_t run[IT];
 #pragma unroll
             for (int q = 0; q < IT; ++q) {
-                ax[q] = ay[q] = az[q] = jx[q] = jy[q] = jz[q] = ph[q] = bs[q] = 0.f;
+                ax[q] = ay[q] = az[q] = ph[q] = bs[q] = 0.f;
+                if (SPJ) {
+                    jx[q] = ac[q].jx.hi, jy[q] = ac[q].jy.hi, jz[q] = ac[q].jz.hi;
+                } else {
+                    jx[q] = jy[q] = jz[q] = 0.f;
+                }
                 run[q] = 0u;
             }
 #pragma unroll 4
@@ -778,7 +797,11 @@ struct PolicyHybrid {
 #pragma unroll
             for (int q = 0; q < IT; ++q) {
                 ac[q].ax.fold(ax[q]), ac[q].ay.fold(ay[q]), ac[q].az.fold(az[q]);
-                ac[q].jx.fold(jx[q]), ac[q].jy.fold(jy[q]), ac[q].jz.fold(jz[q]);
+                if (SPJ) {
+                    ac[q].jx.hi = jx[q], ac[q].jy.hi = jy[q], ac[q].jz.hi = jz[q];
+                } else {
+                    ac[q].jx.fold(jx[q]), ac[q].jy.fold(jy[q]), ac[q].jz.fold(jz[q]);
+                }
                 ac[q].ph.fold(ph[q]);
                 ac[q].q = fmaf(bs[q], bs[q], ac[q].q);
                 if (u0 < 32) nlo[q] |= run[q] << u0;
@@ -1263,6 +1286,8 @@ const void* kernel_ptr(Prec p, int it, int split, bool ens = false)
         return kfn_split<PolicyMixed<1, true>, PolicyMixed<2, true>>(it, split, ens);
     case Prec::DS: return kfn_split<PolicyDS<1>, void>(it, split, ens);
     case Prec::HYBRID: return kfn_split<PolicyHybrid<1>, PolicyHybrid<2>>(it, split, ens);
+    case Prec::HYBRID_SPJ:
+        return kfn_split<PolicyHybrid<1, true>, PolicyHybrid<2, true>>(it, split, ens);
     }
     return nullptr;
 }
@@ -1276,7 +1301,8 @@ int jlayout_narr(Prec p)
     case Prec::MIXED:
     case Prec::MIXED_SPJ: return 3;
     case Prec::DS: return 4;
-    case Prec::HYBRID: return 4;
+    case Prec::HYBRID:
+    case Prec::HYBRID_SPJ: return 4;
     }
     return 0;
 }
@@ -1288,7 +1314,8 @@ int jlayout_elem_bytes(Prec p, int k)
     case Prec::MIXED:
     case Prec::MIXED_SPJ: return k < 2 ? 16 : (k == 2 ? 8 : 0);
     case Prec::DS: return k < 4 ? 16 : 0;
-    case Prec::HYBRID: return k < 4 ? 16 : 0;
+    case Prec::HYBRID:
+    case Prec::HYBRID_SPJ: return k < 4 ? 16 : 0;
     }
     return 0;
 }
@@ -1300,7 +1327,8 @@ size_t force_smem_bytes(Prec p)
     case Prec::MIXED:
     case Prec::MIXED_SPJ: return (size_t)FORCE_WARPS * WarpSmem<PolicyMixed<1>>::BYTES;
     case Prec::DS: return (size_t)FORCE_WARPS * WarpSmem<PolicyDS<1>>::BYTES;
-    case Prec::HYBRID: return (size_t)FORCE_WARPS * WarpSmem<PolicyHybrid<1>>::BYTES;
+    case Prec::HYBRID:
+    case Prec::HYBRID_SPJ: return (size_t)FORCE_WARPS * WarpSmem<PolicyHybrid<1>>::BYTES;
     }
     return 0;
 }
@@ -1393,7 +1421,7 @@ cudaError_t force_launch(const ForceArgs& a, cudaStream_t s)
     if (f.jt_hi > 0 && (a.plan.grp_tile0 || f.jt_lo < 0 || f.jt_hi <= f.jt_lo ||
                         f.jt_hi > f.n_pad / TJ))
         return cudaErrorInvalidValue;
-    if (a.prec == Prec::HYBRID &&
+    if (is_hybrid(a.prec) &&
         (!f.st_a || !f.st_j || !f.bound_v || !f.st_dt || !f.st_hq || !f.tile_box))
         return cudaErrorInvalidValue;
     void* args[] = {&f};

@@ -364,6 +364,7 @@ cudaError_t predict_launch(const StateDev& st, Prec p, const JLayout& jl, double
             <<<blocks, threads, 0, s>>>(st, jl, G, t_bits, t_host, n_act_dev, jsrc, cof);
         break;
     case Prec::HYBRID:
+    case Prec::HYBRID_SPJ:  // same j layout
         if (!st.tile_box) return cudaErrorInvalidValue;
         predict_ds_kernel<static_cast<int>(Prec::HYBRID)>
             <<<blocks, threads, 0, s>>>(st, jl, G, t_bits, t_host, n_act_dev, jsrc, cof);

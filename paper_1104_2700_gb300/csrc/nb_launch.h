@@ -17,9 +17,12 @@ namespace nb {
 //   HYBRID - FP32 far pairs, double-single near pairs.
 //   MIXED_SPJ - MIXED with the jerk summed in plain FP32, the accumulation
 //           the paper's own kernel uses (Sec. 4, Fig. err_snp_djerk).
-enum class Prec : int { FP64 = 0, MIXED = 1, DS = 2, HYBRID = 3, MIXED_SPJ = 4 };
+//   HYBRID_SPJ - HYBRID with the far-field jerk summed in plain FP32 (the
+//           same study on the precision that integrates).
+enum class Prec : int { FP64 = 0, MIXED = 1, DS = 2, HYBRID = 3, MIXED_SPJ = 4, HYBRID_SPJ = 5 };
 
 inline bool is_mixed(Prec p) { return p == Prec::MIXED || p == Prec::MIXED_SPJ; }
+inline bool is_hybrid(Prec p) { return p == Prec::HYBRID || p == Prec::HYBRID_SPJ; }
 
 // Device Hermite state of one context, structure of arrays.  x, v, a, j
 // hold 3*n doubles: component c of particle i at [c*n + i].

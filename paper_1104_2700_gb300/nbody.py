@@ -18,9 +18,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libnbody.so")
 
 NB_OK, NB_EINVAL, NB_ECUDA, NB_ENOMEM, NB_ENONFINITE, NB_EDTMIN, NB_ETIMEOUT, NB_ESTATE = range(8)
-NB_FP64, NB_MIXED, NB_DS, NB_HYBRID, NB_MIXED_SPJ = 0, 1, 2, 3, 4
+NB_FP64, NB_MIXED, NB_DS, NB_HYBRID, NB_MIXED_SPJ, NB_HYBRID_SPJ = 0, 1, 2, 3, 4, 5
 PRECISIONS = {"fp64": NB_FP64, "mixed": NB_MIXED, "ds": NB_DS, "hybrid": NB_HYBRID,
-              "mixed_spj": NB_MIXED_SPJ}
+              "mixed_spj": NB_MIXED_SPJ, "hybrid_spj": NB_HYBRID_SPJ}
 
 
 class NbConfig(ctypes.Structure):

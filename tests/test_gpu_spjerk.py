@@ -114,3 +114,30 @@ def test_mixed_accuracy_matches_fig_err_snp(gpu, orc):
         assert typical / 10 < acc_med < typical * 10
         assert np.median(np.abs(pot - p0) / np.abs(p0)) < typical * 10
         assert np.median(_rel(jerk, j0)) > acc_med
+
+
+def _forces_with_state(gpu, prec, m, r, v, eps, idx, a0, j0, **kw):
+    n = len(m)
+    with gpu.Context(prec, **kw) as ctx:
+        ctx.set_state(m, r, v, a0, j0, np.zeros(n), np.full(n, 1.0 / 16), eps, 0.02)
+        ctx.predict(0.0)
+        return ctx.force(idx)
+
+
+@pytest.mark.parametrize("n,n_act", [(4096, 4096), (8192, 700), (20000, 20000)])
+def test_hybrid_spj_jerk_within_plain_sum_bound(gpu, orc, n, n_act):
+    """HYBRID_SPJ: the far pairs' jerk in one plain FP32 sum per warp; its
+    jerk within (16 + N) u sum |j_ij| of the oracle, and acceleration and
+    potential bit-identical to HYBRID under the same launch shape."""
+    m, r, v = ics.plummer(n, 40 + n)
+    eps = 4.0 / n
+    idx = ics.permutation(n, 14)[:n_act].astype(np.int32)
+    a_all, j_all, _ = orc.force(m, r, v, eps, nthreads=NTHREADS)
+    shape = dict(i_per_thread=2, j_split=1, ctas_per_sm=3)
+    a1, j1, p1 = _forces_with_state(gpu, "hybrid", m, r, v, eps, idx, a_all, j_all, **shape)
+    a2, j2, p2 = _forces_with_state(gpu, "hybrid_spj", m, r, v, eps, idx, a_all, j_all, **shape)
+    assert np.array_equal(a1, a2) and np.array_equal(p1, p2)
+    _, sj, _ = _magnitude_sums(m, r, v, eps, idx)
+    assert np.all(np.linalg.norm(j2 - j_all[idx], axis=1) <= (16 + n) * U32 * sj)
+    if n_act == n:
+        assert not np.array_equal(j1, j2)
