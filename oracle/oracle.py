@@ -77,6 +77,19 @@ def _load():
         lib.orc_run.restype = i32
         lib.orc_has_openmp.argtypes = []
         lib.orc_has_openmp.restype = i32
+        lib.orc_force_snap.argtypes = [i64, P, P, P, P, d, d, i64, P, P, P, P, P, i32]
+        lib.orc_force_snap.restype = None
+        lib.orc_predict6.argtypes = [i64, P, P, P, P, P, P, P, d, P, P, P]
+        lib.orc_predict6.restype = None
+        lib.orc_hermite6_correct.argtypes = [P, P, P, P, P, P, P, P, d, P, P, P, P, P]
+        lib.orc_hermite6_correct.restype = None
+        lib.orc_aarseth6_dt.argtypes = [d, P, P, P, P, P, P]
+        lib.orc_aarseth6_dt.restype = d
+        lib.orc_init6.argtypes = [i64, P, P, P, P, P, P, P, P, P, d, d, d, d, d, d, i32]
+        lib.orc_init6.restype = i32
+        lib.orc_run6.argtypes = [i64, P, P, P, P, P, P, P, P, P, d, d, d, d, d, d, i32,
+                                 i64, P, P]
+        lib.orc_run6.restype = i32
         _lib = lib
         return lib
 
@@ -184,6 +197,88 @@ def energy(m, r, v, eps, G=1.0, nthreads=1):
     _load().orc_energy(n, _ptr(m), _ptr(r), _ptr(v), float(eps), float(G),
                        _ptr(K), _ptr(W), int(nthreads))
     return float(K[0]), float(W[0])
+
+
+def force_snap(m, r, v, a, eps, G=1.0, idx=None, nthreads=1):
+    """Acceleration, jerk, snap and potential on ``idx`` (default: all), the
+    snap from the particles' predicted accelerations ``a`` (sixth-order
+    variant)."""
+    lib = _load()
+    m = _f64(m)
+    n = m.shape[0]
+    r, v, a = _f64(r, (n, 3)), _f64(v, (n, 3)), _f64(a, (n, 3))
+    if idx is None:
+        idx = np.arange(n, dtype=np.int64)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    k = idx.shape[0]
+    acc, jerk, snap, pot = np.empty((k, 3)), np.empty((k, 3)), np.empty((k, 3)), np.empty(k)
+    lib.orc_force_snap(n, _ptr(m), _ptr(r), _ptr(v), _ptr(a), float(eps), float(G), k,
+                       _ptr(idx), _ptr(acc), _ptr(jerk), _ptr(snap), _ptr(pot), int(nthreads))
+    return acc, jerk, snap, pot
+
+
+def predict6(r0, v0, a0, j0, s0, c0, t0, t):
+    """Sixth-order predictor of r, v, a to time ``t``."""
+    lib = _load()
+    t0 = _f64(t0)
+    n = t0.shape[0]
+    r0, v0, a0, j0, s0, c0 = (_f64(x, (n, 3)) for x in (r0, v0, a0, j0, s0, c0))
+    rp, vp, ap = np.empty((n, 3)), np.empty((n, 3)), np.empty((n, 3))
+    lib.orc_predict6(n, _ptr(r0), _ptr(v0), _ptr(a0), _ptr(j0), _ptr(s0), _ptr(c0),
+                     _ptr(t0), float(t), _ptr(rp), _ptr(vp), _ptr(ap))
+    return rp, vp, ap
+
+
+def hermite6_correct(r0, v0, a0, j0, s0, a1, j1, s1, h):
+    """Sixth-order corrector for one particle: (r1, v1, crackle, pop, fifth
+    derivative) at the end of a step ``h``."""
+    lib = _load()
+    args = [_f64(x, (3,)) for x in (r0, v0, a0, j0, s0, a1, j1, s1)]
+    out = [np.empty(3) for _ in range(5)]
+    lib.orc_hermite6_correct(*[_ptr(x) for x in args], float(h), *[_ptr(x) for x in out])
+    return tuple(out)
+
+
+def aarseth6_dt(eta, a, j, s, c, d, x):
+    """The sixth-order timestep criterion (reading H2)."""
+    vs = [_f64(q, (3,)) for q in (a, j, s, c, d, x)]
+    return _load().orc_aarseth6_dt(float(eta), *[_ptr(q) for q in vs])
+
+
+class State6:
+    """Full state of one system under the sixth-order scheme (the oracle's copy)."""
+
+    def __init__(self, m, r, v, eps, eta, G=1.0, eta_start=0.01, dt_max=1.0 / 16,
+                 dt_min=2.0 ** -40, nthreads=1):
+        self.m = _f64(m).copy()
+        n = self.n = self.m.shape[0]
+        self.r, self.v = _f64(r, (n, 3)).copy(), _f64(v, (n, 3)).copy()
+        self.a, self.j, self.s, self.c = (np.empty((n, 3)) for _ in range(4))
+        self.t, self.dt = np.empty(n), np.empty(n)
+        self.eps, self.eta, self.G = float(eps), float(eta), float(G)
+        self.dt_max, self.dt_min, self.nthreads = float(dt_max), float(dt_min), int(nthreads)
+        self.n_steps, self.n_inter = 0, 0.0
+        st = _load().orc_init6(n, _ptr(self.m), _ptr(self.r), _ptr(self.v), _ptr(self.a),
+                               _ptr(self.j), _ptr(self.s), _ptr(self.c), _ptr(self.t),
+                               _ptr(self.dt), 0.0, self.eps, self.G, float(eta_start),
+                               self.dt_max, self.dt_min, self.nthreads)
+        if st != OK:
+            raise RuntimeError(f"oracle init failed with status {st}")
+
+    def run(self, t_end, max_steps=0):
+        steps, inter = np.zeros(1, dtype=np.int64), np.zeros(1)
+        st = _load().orc_run6(self.n, _ptr(self.m), _ptr(self.r), _ptr(self.v), _ptr(self.a),
+                              _ptr(self.j), _ptr(self.s), _ptr(self.c), _ptr(self.t),
+                              _ptr(self.dt), float(t_end), self.eps, self.G, self.eta,
+                              self.dt_max, self.dt_min, self.nthreads, int(max_steps),
+                              _ptr(steps), _ptr(inter))
+        self.n_steps += int(steps[0])
+        self.n_inter += float(inter[0])
+        return st
+
+    def energy(self):
+        K, W = energy(self.m, self.r, self.v, self.eps, self.G, self.nthreads)
+        return K + W
 
 
 class State:
