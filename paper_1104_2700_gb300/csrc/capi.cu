@@ -51,6 +51,7 @@ struct nb_ctx {
     double* acc1 = nullptr;
     double* jerk1 = nullptr;
     double* pot1 = nullptr;
+    double* snap1 = nullptr;  // sixth-order variant: the block's new snap
     double* scratch = nullptr;
     uint32_t* counters = nullptr;
     int64_t counter_stride = 0;
@@ -166,6 +167,7 @@ void free_buffers(nb_ctx* c)
     dfree(c->sd.tmin_bits), dfree(c->sd.idx), dfree(c->sd.n_act);
     dfree(c->sd.block_counts), dfree(c->sd.block_offsets), dfree(c->sd.ticket);
     dfree(c->idx_user), dfree(c->n_act_user), dfree(c->acc1), dfree(c->jerk1), dfree(c->pot1);
+    dfree(c->snap1), dfree(c->st.s), dfree(c->st.c);
     dfree(c->scratch), dfree(c->counters), dfree(c->staging);
     dfree(c->energy_partials), dfree(c->energy_out), dfree(c->energy_ticket);
     dfree(c->cl.off), dfree(c->cl.joff), dfree(c->cl.eps2), dfree(c->cl.cluster_of);
@@ -269,6 +271,11 @@ nb_status ensure_capacity(nb_ctx* c, int64_t n, int64_t n_pad, int64_t k)
     NB_CK(c, cudaMalloc(&c->acc1, 3 * n * d));
     NB_CK(c, cudaMalloc(&c->jerk1, 3 * n * d));
     NB_CK(c, cudaMalloc(&c->pot1, n * d));
+    if (c->prec == Prec::FP64_H6) {
+        NB_CK(c, cudaMalloc(&c->snap1, 3 * n * d));
+        NB_CK(c, cudaMalloc(&c->st.s, 3 * n * d));
+        NB_CK(c, cudaMalloc(&c->st.c, 3 * n * d));
+    }
     NB_CK(c, cudaMalloc(&c->staging, 3 * n * d));
     c->scratch_cap = 0;
     c->counter_cap = 0;
@@ -402,6 +409,7 @@ nb::ForceArgs force_args(nb_ctx* c, Prec p, const nb::JLayout& jl, const int32_t
     f.acc = c->acc1;
     f.jerk = c->jerk1;
     f.pot = c->pot1;
+    f.snap = c->snap1;
     f.scratch = c->scratch;
     f.st_a = c->st.a;
     f.st_j = c->st.j;
@@ -651,7 +659,10 @@ nb_status block_step(nb_ctx* c, double t_end)
     ca.status = c->status_dev;
     ca.step_counter = c->ctr64;
     ca.inter_counter = c->ctr64 + 1;
-    NB_CK(c, nb::correct_launch(c->st, ca, c->stream));
+    if (c->prec == Prec::FP64_H6)
+        NB_CK(c, nb::correct6_launch(c->st, ca, c->snap1, c->stream));
+    else
+        NB_CK(c, nb::correct_launch(c->st, ca, c->stream));
     c->last_force_n_act = -1;
     c->order_fresh = false;  // the positions move
     return NB_OK;
@@ -711,6 +722,22 @@ nb_status hybrid_noise_pass(nb_ctx* c, bool ensemble)
     return run_force(c, c->prec, c->jl, c->idx_user, c->n_act_user, static_cast<int32_t>(c->n));
 }
 
+// Sixth-order variant, at a load: every particle at time t with a, j in
+// the state; its snap from a force pass with those accelerations (reading
+// H3 of its oracle), crackle zero.
+nb_status h6_start(nb_ctx* c, double t)
+{
+    NB_CK(c, cudaMemsetAsync(c->st.s, 0, 3 * c->n * sizeof(double), c->stream));
+    NB_CK(c, cudaMemsetAsync(c->st.c, 0, 3 * c->n * sizeof(double), c->stream));
+    NB_CK(c, nb::predict_launch(c->st, c->prec, c->jl, c->cfg.G, nullptr, t, nullptr, c->stream));
+    NB_CK(c, nb::iota_launch(c->idx_user, c->n, c->n_act_user, c->stream));
+    nb_status s = run_force(c, c->prec, c->jl, c->idx_user, c->n_act_user,
+                            static_cast<int32_t>(c->n));
+    if (s != NB_OK) return s;
+    NB_CK(c, nb::init_snap_launch(c->st, c->snap1, c->stream));
+    return NB_OK;
+}
+
 // Set-up shared by nb_set_particles / nb_set_state.
 nb_status begin_load(nb_ctx* c, int64_t n, double eps, double eta)
 {
@@ -762,7 +789,7 @@ nb_status nb_create(const nb_config* cfg, nb_ctx** out)
 {
     if (!cfg || !out) return NB_EINVAL;
     *out = nullptr;
-    if (cfg->precision < NB_FP64 || cfg->precision > NB_HYBRID_SPJ) return NB_EINVAL;
+    if (cfg->precision < NB_FP64 || cfg->precision > NB_FP64_HERMITE6) return NB_EINVAL;
     if (cfg->j_split != 0 && cfg->j_split != 1 && cfg->j_split != 2 && cfg->j_split != 4 &&
         cfg->j_split != 8)
         return NB_EINVAL;
@@ -855,6 +882,10 @@ nb_status nb_set_particles(nb_ctx* c, int64_t n, const double* m, const double* 
     NB_CK(c, cudaMemsetAsync(c->st.a, 0, 3 * n * sizeof(double), c->stream));
     NB_CK(c, cudaMemsetAsync(c->st.j, 0, 3 * n * sizeof(double), c->stream));
     NB_CK(c, cudaMemsetAsync(c->st.t, 0, n * sizeof(double), c->stream));
+    if (c->prec == Prec::FP64_H6) {
+        NB_CK(c, cudaMemsetAsync(c->st.s, 0, 3 * n * sizeof(double), c->stream));
+        NB_CK(c, cudaMemsetAsync(c->st.c, 0, 3 * n * sizeof(double), c->stream));
+    }
     if ((s = refresh_bounds(c)) != NB_OK) return s;
     // Forces on every particle at t = 0, then the first timesteps.
     NB_CK(c, nb::predict_launch(c->st, c->prec, c->jl, c->cfg.G, nullptr, 0.0, nullptr, c->stream));
@@ -864,6 +895,7 @@ nb_status nb_set_particles(nb_ctx* c, int64_t n, const double* m, const double* 
         return s;
     NB_CK(c, nb::init_dt_launch(c->st, c->acc1, c->jerk1, c->cfg.eta_start, c->cfg.dt_max,
                                 c->cfg.dt_min, 0.0, c->status_dev, c->stream));
+    if (c->prec == Prec::FP64_H6 && (s = h6_start(c, 0.0)) != NB_OK) return s;
     if ((s = hybrid_noise_pass(c, false)) != NB_OK) return s;
     if ((s = check_status(c)) != NB_OK) return s;
     c->loaded = true;
@@ -897,6 +929,18 @@ nb_status nb_set_state(nb_ctx* c, int64_t n, const double* m, const double* r, c
     if ((s = upload_perm(c, t, c->st.t, 1, on_device)) != NB_OK) return s;
     if ((s = upload_perm(c, dt, c->st.dt, 1, on_device)) != NB_OK) return s;
     if ((s = refresh_bounds(c)) != NB_OK) return s;
+    if (c->prec == Prec::FP64_H6) {
+        // the snap needs every particle at one time
+        std::vector<double> ht(n);
+        NB_CK(c, cudaMemcpyAsync(ht.data(), c->st.t, n * sizeof(double), cudaMemcpyDeviceToHost,
+                                 c->stream));
+        NB_CK(c, cudaStreamSynchronize(c->stream));
+        for (int64_t q = 1; q < n; ++q)
+            if (ht[q] != ht[0])
+                return fail(c, NB_EINVAL, "the sixth-order variant loads synchronised states only");
+        if ((s = h6_start(c, ht[0])) != NB_OK) return s;
+        if ((s = check_status(c)) != NB_OK) return s;
+    }
     if (!on_device) NB_CK(c, cudaStreamSynchronize(c->stream));
     c->loaded = true;
     return NB_OK;
@@ -913,6 +957,9 @@ nb_status nb_snapshot(nb_ctx* c, void* buf)
 {
     nb_status s = enter(c, true);
     if (s != NB_OK) return s;
+    if (c->prec == Prec::FP64_H6)
+        return fail(c, NB_ESTATE, "no snapshots of the sixth-order variant (its snap and "
+                                  "crackle are not in the snapshot layout)");
     if (!buf || (reinterpret_cast<uintptr_t>(buf) & 15u)) return fail(c, NB_EINVAL, "buf NULL or not 16-byte aligned");
     double* b = static_cast<double*>(buf);
     NB_CK(c, nb::snapshot_launch(c->st, b, true, c->stream));
@@ -928,6 +975,9 @@ nb_status nb_restore(nb_ctx* c, const void* buf)
 {
     nb_status s = enter(c, true);
     if (s != NB_OK) return s;
+    if (c->prec == Prec::FP64_H6)
+        return fail(c, NB_ESTATE, "no snapshots of the sixth-order variant (its snap and "
+                                  "crackle are not in the snapshot layout)");
     if (!buf || (reinterpret_cast<uintptr_t>(buf) & 15u)) return fail(c, NB_EINVAL, "buf NULL or not 16-byte aligned");
     double* b = static_cast<double*>(const_cast<void*>(buf));
     NB_CK(c, nb::snapshot_launch(c->st, b, false, c->stream));
@@ -940,6 +990,21 @@ nb_status nb_restore(nb_ctx* c, const void* buf)
     c->host_order_stale = true;
     c->order_pos.clear();
     c->order_fresh = false;
+    return NB_OK;
+}
+
+nb_status nb_get_snap(nb_ctx* c, double* sn, double* cr, int32_t on_device)
+{
+    nb_status s = enter(c, true);
+    if (s != NB_OK) return s;
+    if (c->prec != Prec::FP64_H6) return fail(c, NB_ESTATE, "no snap in this precision");
+    double* src[2] = {c->st.s, c->st.c};
+    double* dst[2] = {sn, cr};
+    for (int q = 0; q < 2; ++q) {
+        if (!dst[q]) continue;
+        if ((s = download_perm(c, src[q], dst[q], 3, on_device)) != NB_OK) return s;
+        if (!on_device) NB_CK(c, cudaStreamSynchronize(c->stream));
+    }
     return NB_OK;
 }
 
@@ -1069,6 +1134,9 @@ nb_status nb_correct(nb_ctx* c, double t, int32_t n_act, const int32_t* idx, con
     if (!std::isfinite(t)) return fail(c, NB_EINVAL, "t not finite");
     if (n_act > 0 && !idx) return fail(c, NB_EINVAL, "NULL idx");
     if ((acc == nullptr) != (jerk == nullptr)) return fail(c, NB_EINVAL, "give both acc and jerk or neither");
+    if (acc && c->prec == Prec::FP64_H6)
+        return fail(c, NB_EINVAL, "the sixth-order variant corrects with the last nb_force "
+                                  "results (acc = jerk = NULL), which hold the snap");
     if (!acc && n_act != c->last_force_n_act)
         return fail(c, NB_ESTATE, "no nb_force result for a block of %d particles", n_act);
     if (n_act == 0) return NB_OK;
@@ -1111,7 +1179,10 @@ nb_status nb_correct(nb_ctx* c, double t, int32_t n_act, const int32_t* idx, con
     ca.dt_max = c->cfg.dt_max;
     ca.dt_min = c->cfg.dt_min;
     ca.status = c->status_dev;
-    NB_CK(c, nb::correct_launch(c->st, ca, c->stream));
+    if (c->prec == Prec::FP64_H6)
+        NB_CK(c, nb::correct6_launch(c->st, ca, c->snap1, c->stream));
+    else
+        NB_CK(c, nb::correct_launch(c->st, ca, c->stream));
     c->last_force_n_act = -1;
     c->order_fresh = false;  // the positions move
     if (!on_device) return check_status(c);  // (also keeps list alive until the copy ran)
@@ -1206,6 +1277,8 @@ nb_status nb_set_ensemble(nb_ctx* c, int32_t k, const int64_t* offsets, const do
     if (!c) return NB_EINVAL;
     if (k < 1 || !offsets || !m || !r || !v || !eps)
         return fail(c, NB_EINVAL, "need k >= 1 and non-NULL arrays");
+    if (c->prec == Prec::FP64_H6)
+        return fail(c, NB_EINVAL, "the sixth-order variant integrates one system");
     if (offsets[0] != 0) return fail(c, NB_EINVAL, "offsets[0] must be 0");
     for (int32_t q = 0; q < k; ++q) {
         if (offsets[q + 1] <= offsets[q])

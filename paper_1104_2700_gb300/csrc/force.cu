@@ -38,6 +38,7 @@ struct ForceParams {
     double* acc;
     double* jerk;
     double* pot;
+    double* snap;  // sixth-order variant: [n_act][3]
     double* scratch;
     uint32_t* counters;      // RLEVELS arrays of counter_stride entries
     int64_t counter_stride;  // >= warps + groups
@@ -154,6 +155,111 @@ struct PolicyFP64 {
         v[0] = a.ax, v[1] = a.ay, v[2] = a.az;
         v[3] = a.jx, v[4] = a.jy, v[5] = a.jz;
         v[6] = -a.ph;
+    }
+};
+
+// FP64 with snap, for the sixth-order Hermite variant (adjacent to the
+// paper): the j layout also carries each particle's predicted acceleration,
+// and each pair adds the second time derivative of its acceleration term
+// along the predicted trajectories,
+//   S = G m a / r^3 - 6 alpha J - 3 beta A,
+// alpha = (r.v) / r^2, beta = (v.v + r.a) / r^2 + alpha^2, with A and J
+// the pair's acceleration and jerk terms (r, v, a relative, r softened).
+template <int IT>
+struct PolicyFP64Snap {
+    static constexpr bool GUARDED = false;
+    static constexpr int MIN_CTAS = 1;
+    static constexpr int CHUNKS = 1;
+    static constexpr int NARR = 3;
+    __host__ __device__ static constexpr int elem(int a) { return a < 3 ? 32 : 0; }
+    static constexpr int TILE_BYTES = TJ * 96;
+    static constexpr int STAGES = 2;
+
+    struct I {
+        double x, y, z, vx, vy, vz, ax, ay, az;
+        int p;
+    };
+    struct Acc {
+        double ax, ay, az, jx, jy, jz, sx, sy, sz, ph;
+        __device__ void zero() { ax = ay = az = jx = jy = jz = sx = sy = sz = ph = 0.0; }
+    };
+
+    __device__ static void load_i(const ForceParams& f, int p, int, I& s)
+    {
+        s.p = p;
+        if (p < 0) {
+            s.x = s.y = s.z = s.vx = s.vy = s.vz = s.ax = s.ay = s.az = 0.0;
+            return;
+        }
+        const double2* P = static_cast<const double2*>(f.jl0) + 2 * (int64_t)p;
+        const double2* V = static_cast<const double2*>(f.jl1) + 2 * (int64_t)p;
+        const double2* A = static_cast<const double2*>(f.jl2) + 2 * (int64_t)p;
+        const double2 p0 = __ldg(P), p1 = __ldg(P + 1);
+        const double2 v0 = __ldg(V), v1 = __ldg(V + 1);
+        const double2 a0 = __ldg(A), a1 = __ldg(A + 1);
+        s.x = p0.x, s.y = p0.y, s.z = p1.x;
+        s.vx = v0.x, s.vy = v0.y, s.vz = v1.x;
+        s.ax = a0.x, s.ay = a0.y, s.az = a1.x;
+    }
+
+    template <bool MASK, int S>
+    __device__ static void tile(const unsigned char* buf, int64_t j0, const double eps2,
+                                I (&is)[IT], Acc (&ac)[IT], int sl)
+    {
+        const double2* sP = reinterpret_cast<const double2*>(buf);
+        const double2* sV = reinterpret_cast<const double2*>(buf + TJ * 32);
+        const double2* sA = reinterpret_cast<const double2*>(buf + TJ * 64);
+#pragma unroll 1
+        for (int u = 0; u < TJ / S; ++u) {
+            const int k = sl + S * u;
+            const double2 p0 = sP[2 * k], p1 = sP[2 * k + 1];
+            const double2 v0 = sV[2 * k], v1 = sV[2 * k + 1];
+            const double2 a0 = sA[2 * k], a1 = sA[2 * k + 1];
+#pragma unroll
+            for (int q = 0; q < IT; ++q) {
+                const double dx = p0.x - is[q].x, dy = p0.y - is[q].y, dz = p1.x - is[q].z;
+                const double vx = v0.x - is[q].vx, vy = v0.y - is[q].vy, vz = v1.x - is[q].vz;
+                const double wx = a0.x - is[q].ax, wy = a0.y - is[q].ay, wz = a1.x - is[q].az;
+                const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
+                double ri = rsqrt(r2);
+                if (MASK) ri = (j0 + k == is[q].p) ? 0.0 : ri;
+                const double mr = p1.y * ri;
+                const double ri2 = ri * ri;
+                const double g = mr * ri2;  // G m / r^3
+                const double alpha = fma(dx, vx, fma(dy, vy, dz * vz)) * ri2;
+                const double beta =
+                    fma(fma(vx, vx, fma(vy, vy, vz * vz)) + fma(dx, wx, fma(dy, wy, dz * wz)), ri2,
+                        alpha * alpha);
+                const double Ax = g * dx, Ay = g * dy, Az = g * dz;
+                const double Jx = fma(g, vx, -3.0 * alpha * Ax);
+                const double Jy = fma(g, vy, -3.0 * alpha * Ay);
+                const double Jz = fma(g, vz, -3.0 * alpha * Az);
+                ac[q].ax += Ax, ac[q].ay += Ay, ac[q].az += Az;
+                ac[q].jx += Jx, ac[q].jy += Jy, ac[q].jz += Jz;
+                ac[q].sx += fma(g, wx, fma(-6.0 * alpha, Jx, -3.0 * beta * Ax));
+                ac[q].sy += fma(g, wy, fma(-6.0 * alpha, Jy, -3.0 * beta * Ay));
+                ac[q].sz += fma(g, wz, fma(-6.0 * alpha, Jz, -3.0 * beta * Az));
+                ac[q].ph += mr;
+            }
+        }
+    }
+
+    static constexpr int NV = 10;  // acc (3), jerk (3), pot, snap (3)
+    using TV = double;
+    __device__ static void values(const Acc& a, TV (&v)[NV])
+    {
+        v[0] = a.ax, v[1] = a.ay, v[2] = a.az;
+        v[3] = a.jx, v[4] = a.jy, v[5] = a.jz;
+        v[6] = -a.ph;
+        v[7] = a.sx, v[8] = a.sy, v[9] = a.sz;
+    }
+
+    __device__ static void finish(const ForceParams& f, const I&, int64_t row,
+                                  const double (&v)[NV])
+    {
+        f.snap[3 * row + 0] = v[7];
+        f.snap[3 * row + 1] = v[8];
+        f.snap[3 * row + 2] = v[9];
     }
 };
 
@@ -609,7 +715,8 @@ struct PolicyHybrid {
         v[7].h = a.q, v[7].l = 0.f;
     }
 
-    __device__ static void finish(const ForceParams& f, const I& s, const double (&v)[NV])
+    __device__ static void finish(const ForceParams& f, const I& s, int64_t,
+                                  const double (&v)[NV])
     {
         // a guarded evaluation stores its estimate negated (the guard state)
         if (s.particle >= 0) f.st_hq[s.particle] = s.all_near ? -v[7] : v[7];
@@ -858,7 +965,7 @@ __device__ __forceinline__ void issue_tile(const ForceParams& f, unsigned char* 
 // Radix of the deterministic reduction tree over the warps sharing a group.
 constexpr int RB = 16;
 constexpr int RLEVELS = 4;  // RB^RLEVELS >= any warp count
-constexpr int MAX_NV = 8;   // values a policy reduces (scratch is sized for the most)
+constexpr int MAX_NV = 10;  // values a policy reduces (scratch is sized for the most)
 
 // Chunk that holds flattened tile x when T tiles are cut into Pu ranges.
 __device__ __forceinline__ int64_t owner_warp(int64_t x, int64_t T, int64_t Pu)
@@ -1238,7 +1345,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
                         f.jerk[3 * a + 1] = o[4];
                         f.jerk[3 * a + 2] = o[5];
                         f.pot[a] = o[6];
-                        if constexpr (K::NV > 7) K::finish(f, is[q], o);
+                        if constexpr (K::NV > 7) K::finish(f, is[q], a, o);
                     }
                 }
             }
@@ -1288,6 +1395,7 @@ const void* kernel_ptr(Prec p, int it, int split, bool ens = false)
     case Prec::HYBRID: return kfn_split<PolicyHybrid<1>, PolicyHybrid<2>>(it, split, ens);
     case Prec::HYBRID_SPJ:
         return kfn_split<PolicyHybrid<1, true>, PolicyHybrid<2, true>>(it, split, ens);
+    case Prec::FP64_H6: return kfn_split<PolicyFP64Snap<1>, void>(it, split, ens);
     }
     return nullptr;
 }
@@ -1303,6 +1411,7 @@ int jlayout_narr(Prec p)
     case Prec::DS: return 4;
     case Prec::HYBRID:
     case Prec::HYBRID_SPJ: return 4;
+    case Prec::FP64_H6: return 3;
     }
     return 0;
 }
@@ -1316,6 +1425,7 @@ int jlayout_elem_bytes(Prec p, int k)
     case Prec::DS: return k < 4 ? 16 : 0;
     case Prec::HYBRID:
     case Prec::HYBRID_SPJ: return k < 4 ? 16 : 0;
+    case Prec::FP64_H6: return k < 3 ? 32 : 0;
     }
     return 0;
 }
@@ -1329,6 +1439,7 @@ size_t force_smem_bytes(Prec p)
     case Prec::DS: return (size_t)FORCE_WARPS * WarpSmem<PolicyDS<1>>::BYTES;
     case Prec::HYBRID:
     case Prec::HYBRID_SPJ: return (size_t)FORCE_WARPS * WarpSmem<PolicyHybrid<1>>::BYTES;
+    case Prec::FP64_H6: return (size_t)FORCE_WARPS * WarpSmem<PolicyFP64Snap<1>>::BYTES;
     }
     return 0;
 }
@@ -1393,6 +1504,7 @@ cudaError_t force_launch(const ForceArgs& a, cudaStream_t s)
     f.acc = a.acc;
     f.jerk = a.jerk;
     f.pot = a.pot;
+    f.snap = a.snap;
     f.scratch = a.scratch;
     f.counters = a.counters;
     f.counter_stride = a.counter_stride;
@@ -1421,6 +1533,7 @@ cudaError_t force_launch(const ForceArgs& a, cudaStream_t s)
     if (f.jt_hi > 0 && (a.plan.grp_tile0 || f.jt_lo < 0 || f.jt_hi <= f.jt_lo ||
                         f.jt_hi > f.n_pad / TJ))
         return cudaErrorInvalidValue;
+    if (a.prec == Prec::FP64_H6 && !f.snap) return cudaErrorInvalidValue;
     if (is_hybrid(a.prec) &&
         (!f.st_a || !f.st_j || !f.bound_v || !f.st_dt || !f.st_hq || !f.tile_box))
         return cudaErrorInvalidValue;

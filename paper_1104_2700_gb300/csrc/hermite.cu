@@ -67,6 +67,48 @@ __global__ void predict_fp64_kernel(const StateDev st, const JLayout jl, const d
     V[1] = make_double2(vp[2], 0.0);
 }
 
+// The sixth-order variant's predictor (reading H1 of its oracle): x, v and
+// a carried to time t with a, j, s and the crackle c, in FP64 Horner form,
+// into the layout of the snap force kernel.
+__global__ void predict_h6_kernel(const StateDev st, const JLayout jl, const double G,
+                                  const unsigned long long* t_bits, const double t_host,
+                                  const int32_t* n_act_dev)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // j-layout slot
+    if (q >= st.n_pad) return;
+    const int64_t n = st.n;
+    const int64_t i = q < n ? q : -1;
+    double xp[3], vp[3], ap[3], gm;
+    if (i >= 0) {
+        const double t = t_bits ? dkey_decode(t_bits[0]) : t_host;
+        const double h = t - st.t[i];
+        gm = G * st.m[i];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double x = st.x[c * n + i], v = st.v[c * n + i], a = st.a[c * n + i];
+            const double jj = st.j[c * n + i], sn = st.s[c * n + i], cr = st.c[c * n + i];
+            xp[c] = fma(h, fma(h, fma(h, fma(h, fma(h, cr * (1.0 / 120.0), sn * (1.0 / 24.0)),
+                                             jj * (1.0 / 6.0)), a * 0.5), v), x);
+            vp[c] = fma(h, fma(h, fma(h, fma(h, cr * (1.0 / 24.0), sn * (1.0 / 6.0)), jj * 0.5), a), v);
+            ap[c] = fma(h, fma(h, fma(h, cr * (1.0 / 6.0), sn * 0.5), jj), a);
+        }
+    } else {
+        xp[0] = xp[1] = xp[2] = GHOST_POS;
+        vp[0] = vp[1] = vp[2] = ap[0] = ap[1] = ap[2] = 0.0;
+        gm = 0.0;
+    }
+    if (n_act_dev && *n_act_dev == 0) return;
+    double2* P = static_cast<double2*>(jl.arr[0]) + 2 * q;
+    double2* V = static_cast<double2*>(jl.arr[1]) + 2 * q;
+    double2* A = static_cast<double2*>(jl.arr[2]) + 2 * q;
+    P[0] = make_double2(xp[0], xp[1]);
+    P[1] = make_double2(xp[2], gm);
+    V[0] = make_double2(vp[0], vp[1]);
+    V[1] = make_double2(vp[2], 0.0);
+    A[0] = make_double2(ap[0], ap[1]);
+    A[1] = make_double2(ap[2], 0.0);
+}
+
 // ---------------------------------------------------------------------------
 // Steps 2-3 for the precisions whose j layout holds double-single values
 // (MIXED, DS, HYBRID): the prediction in double-single arithmetic on the
@@ -362,6 +404,10 @@ cudaError_t predict_launch(const StateDev& st, Prec p, const JLayout& jl, double
     case Prec::DS:
         predict_ds_kernel<static_cast<int>(Prec::DS)>
             <<<blocks, threads, 0, s>>>(st, jl, G, t_bits, t_host, n_act_dev, jsrc, cof);
+        break;
+    case Prec::FP64_H6:
+        if (cl || !st.s || !st.c) return cudaErrorInvalidValue;
+        predict_h6_kernel<<<blocks, threads, 0, s>>>(st, jl, G, t_bits, t_host, n_act_dev);
         break;
     case Prec::HYBRID:
     case Prec::HYBRID_SPJ:  // same j layout
@@ -1086,6 +1132,140 @@ cudaError_t correct_launch(const StateDev& st, const CorrectArgs& c, cudaStream_
     const int64_t want = (st.n + CORR_P - 1) / CORR_P;
     const unsigned blocks = static_cast<unsigned>(want < 2432 ? want : 2432);
     correct_kernel<<<blocks, 3 * CORR_P, 0, s>>>(st, c);
+    return cudaGetLastError();
+}
+
+// The sixth-order variant's steps 5-8 for one active particle per thread,
+// written operation by operation in the order of its oracle (the quintic
+// Hermite interpolant of a(t); readings H1-H2), so that identical inputs
+// give the oracle's r, v, a, j, s and crackle.  The timestep uses the FP64
+// pow of the criterion, whose last bit may differ from the host's: the
+// power-of-two rule only looks at the candidate's interval.
+__global__ void correct6_kernel(const StateDev st, const CorrectArgs c, const double* snap1)
+{
+    const int n_act = *c.n_act_dev;
+    const int64_t n = st.n;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && n_act > 0) {
+        if (c.step_counter) atomicAdd(c.step_counter, 1ull);
+        if (c.inter_counter)
+            atomicAdd(c.inter_counter, static_cast<unsigned long long>(n_act) *
+                                           static_cast<unsigned long long>(n));
+    }
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_act;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = c.idx[k];
+        if (i < 0 || i >= n) {
+            atomicOr(c.status, ST_BADINDEX);
+            continue;
+        }
+        const double tn = dkey_decode(c.t_bits[0]);
+        const double h = st.dt[i];
+        if (DADD(st.t[i], h) != tn) {
+            atomicOr(c.status, ST_NOTDUE);
+            continue;
+        }
+        double a1[3], j1[3], s1[3];
+        bool finite = true;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            a1[d] = c.acc1[3 * k + d];
+            j1[d] = c.jerk1[3 * k + d];
+            s1[d] = snap1[3 * k + d];
+            finite = finite && isfinite(a1[d]) && isfinite(j1[d]) && isfinite(s1[d]);
+        }
+        if (!finite) {
+            atomicOr(c.status, ST_NONFINITE);
+            continue;
+        }
+        const double h2 = DMUL(h, h), h3 = DMUL(h2, h), h4 = DMUL(h3, h), h5 = DMUL(h4, h);
+        double c1[3], d1[3], x1[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int64_t q = d * n + i;
+            const double r0 = st.x[q], v0 = st.v[q], a0 = st.a[q], j0 = st.j[q], s0 = st.s[q];
+            const double Da = DSUB(DSUB(DSUB(a1[d], a0), DMUL(j0, h)), DMUL(DDIV(s0, 2.0), h2));
+            const double Dj = DSUB(DSUB(j1[d], j0), DMUL(s0, h));
+            const double Ds = DSUB(s1[d], s0);
+            const double c3 = DDIV(DMUL(3.0, DADD(DSUB(DMUL(20.0, Da), DMUL(DMUL(8.0, Dj), h)),
+                                                  DMUL(Ds, h2))), h3);
+            const double c4 = DDIV(DMUL(-24.0, DADD(DSUB(DMUL(15.0, Da), DMUL(DMUL(7.0, Dj), h)),
+                                                    DMUL(Ds, h2))), h4);
+            const double c5 = DDIV(DMUL(60.0, DADD(DSUB(DMUL(12.0, Da), DMUL(DMUL(6.0, Dj), h)),
+                                                   DMUL(Ds, h2))), h5);
+            const double v1 = DADD(DSUB(DADD(v0, DMUL(DDIV(h, 2.0), DADD(a0, a1[d]))),
+                                        DMUL(DDIV(h2, 10.0), DSUB(j1[d], j0))),
+                                   DMUL(DDIV(h3, 120.0), DADD(s0, s1[d])));
+            const double r1 = DADD(DSUB(DADD(r0, DMUL(DDIV(h, 2.0), DADD(v0, v1))),
+                                        DMUL(DDIV(h2, 10.0), DSUB(a1[d], a0))),
+                                   DMUL(DDIV(h3, 120.0), DADD(j0, j1[d])));
+            c1[d] = DADD(DADD(c3, DMUL(c4, h)), DMUL(DDIV(c5, 2.0), h2));
+            d1[d] = DADD(c4, DMUL(c5, h));
+            x1[d] = c5;
+            st.x[q] = r1;
+            st.v[q] = v1;
+            st.a[q] = a1[d];
+            st.j[q] = j1[d];
+            st.s[q] = s1[d];
+            st.c[q] = c1[d];
+            const uint32_t xb = __float_as_uint(__double2float_ru(fabs(r1)));
+            const uint32_t vb = __float_as_uint(__double2float_ru(fabs(v1)));
+            if (xb > st.bound[0]) atomicMax(&st.bound[0], xb);
+            if (vb > st.bound[1]) atomicMax(&st.bound[1], vb);
+        }
+        st.t[i] = tn;
+        // reading H2: the sixth-order criterion at the new time, then R2
+        const double A = norm3_rn(a1[0], a1[1], a1[2]), J = norm3_rn(j1[0], j1[1], j1[2]);
+        const double S = norm3_rn(s1[0], s1[1], s1[2]), C = norm3_rn(c1[0], c1[1], c1[2]);
+        const double D = norm3_rn(d1[0], d1[1], d1[2]), X = norm3_rn(x1[0], x1[1], x1[2]);
+        const double den = DADD(DMUL(C, X), DMUL(D, D));
+        const double dta = den == 0.0
+                               ? CUDART_INF
+                               : DMUL(c.eta, pow(DDIV(DADD(DMUL(A, S), DMUL(J, J)), den), 1.0 / 6.0));
+        if (isnan(dta)) {
+            atomicOr(c.status, ST_NONFINITE);
+            continue;
+        }
+        const double cand = dta < c.dt_max ? dta : c.dt_max;
+        double dt_new = h;
+        const double k2h = DMUL(tn, recip_pow2(DMUL(2.0, h)));
+        if (cand >= DMUL(2.0, h) && k2h == rint(k2h)) {
+            dt_new = DMUL(2.0, h);
+        } else if (cand >= h) {
+            dt_new = h;
+        } else {
+            while (dt_new > cand && dt_new >= c.dt_min) dt_new = DMUL(dt_new, 0.5);
+        }
+        st.dt[i] = dt_new;
+        st.nkey[i] = dkey(DADD(tn, dt_new));
+        if (dt_new < c.dt_min) atomicOr(c.status, ST_DTMIN);
+    }
+}
+
+cudaError_t correct6_launch(const StateDev& st, const CorrectArgs& c, const double* snap1,
+                            cudaStream_t s)
+{
+    if (st.n <= 0) return cudaSuccess;
+    if (!st.s || !st.c || !snap1 || c.cluster_of) return cudaErrorInvalidValue;
+    const int threads = 64;  // FP64 bound: spread the particles over many SMs
+    const int64_t want = (st.n + threads - 1) / threads;
+    correct6_kernel<<<static_cast<unsigned>(want < 4096 ? want : 4096), threads, 0, s>>>(st, c,
+                                                                                          snap1);
+    return cudaGetLastError();
+}
+
+__global__ void init_snap_kernel(const StateDev st, const double* snap_rows)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 3 * st.n) return;
+    const int64_t d = e / st.n, i = e - d * st.n;
+    st.s[e] = snap_rows[3 * i + d];
+    st.c[e] = 0.0;  // reading H1: no crackle yet
+}
+
+cudaError_t init_snap_launch(const StateDev& st, const double* snap_rows, cudaStream_t s)
+{
+    if (st.n <= 0) return cudaSuccess;
+    init_snap_kernel<<<static_cast<unsigned>((3 * st.n + 255) / 256), 256, 0, s>>>(st, snap_rows);
     return cudaGetLastError();
 }
 

@@ -19,7 +19,11 @@ namespace nb {
 //           the paper's own kernel uses (Sec. 4, Fig. err_snp_djerk).
 //   HYBRID_SPJ - HYBRID with the far-field jerk summed in plain FP32 (the
 //           same study on the precision that integrates).
-enum class Prec : int { FP64 = 0, MIXED = 1, DS = 2, HYBRID = 3, MIXED_SPJ = 4, HYBRID_SPJ = 5 };
+//   FP64_H6 - FP64 with snap: the sixth-order Hermite variant (adjacent to
+//           the paper, which integrates with the fourth-order scheme).
+enum class Prec : int {
+    FP64 = 0, MIXED = 1, DS = 2, HYBRID = 3, MIXED_SPJ = 4, HYBRID_SPJ = 5, FP64_H6 = 6
+};
 
 inline bool is_mixed(Prec p) { return p == Prec::MIXED || p == Prec::MIXED_SPJ; }
 inline bool is_hybrid(Prec p) { return p == Prec::HYBRID || p == Prec::HYBRID_SPJ; }
@@ -45,6 +49,10 @@ struct StateDev {
     // last force evaluation, negative when that evaluation was guarded
     // (all double-single); 0 = none yet.
     double* hq = nullptr;
+    // Sixth-order variant only: snap s and crackle c at each particle's
+    // time (3 n each, SoA like a and j).
+    double* s = nullptr;
+    double* c = nullptr;
     // Per particle, the order-preserving key of its next time t_i + dt_i,
     // kept by every writer of t and dt so that step 1 compares integers.
     unsigned long long* nkey = nullptr;
@@ -63,6 +71,8 @@ cudaError_t next_key_launch(const StateDev& st, cudaStream_t s);
 
 // Predicted j particles in the layout a force kernel streams.
 //   FP64 : arr[0] = double4 (x, y, z, G m), arr[1] = double4 (vx, vy, vz, 0)
+//   FP64_H6: as FP64 plus arr[2] = double4 (ax, ay, az, 0), the predicted
+//          accelerations
 //   MIXED: arr[0] = float4 (x_hi, y_hi, z_hi, G m), arr[1] = float4 (x_lo,
 //          y_lo, z_lo, vx), arr[2] = float2 (vy, vz)
 //   Position (and DS velocity) hi/lo pairs are grid-aligned splits
@@ -141,6 +151,7 @@ struct ForceArgs {
     double* acc = nullptr;   // [n_act][3]
     double* jerk = nullptr;  // [n_act][3]
     double* pot = nullptr;   // [n_act]
+    double* snap = nullptr;  // [n_act][3], FP64_H6 only
     double* scratch = nullptr;
     uint32_t* counters = nullptr;   // force_counter_entries() zeroed words
     int64_t counter_stride = 0;     // entries per reduction level
@@ -224,6 +235,12 @@ struct CorrectArgs {
     const int64_t* cl_off = nullptr;
 };
 cudaError_t correct_launch(const StateDev& st, const CorrectArgs& c, cudaStream_t s);
+// The sixth-order variant's steps 5-8 (snap1: the block's new snap rows).
+cudaError_t correct6_launch(const StateDev& st, const CorrectArgs& c, const double* snap1,
+                            cudaStream_t s);
+// Its start: the snap rows of a full evaluation (in particle order) into
+// the state, crackle zero.
+cudaError_t init_snap_launch(const StateDev& st, const double* snap_rows, cudaStream_t s);
 
 // Initial timesteps from a, j (reading R3), t = t0.
 cudaError_t init_dt_launch(const StateDev& st, const double* acc, const double* jerk,

@@ -18,9 +18,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libnbody.so")
 
 NB_OK, NB_EINVAL, NB_ECUDA, NB_ENOMEM, NB_ENONFINITE, NB_EDTMIN, NB_ETIMEOUT, NB_ESTATE = range(8)
-NB_FP64, NB_MIXED, NB_DS, NB_HYBRID, NB_MIXED_SPJ, NB_HYBRID_SPJ = 0, 1, 2, 3, 4, 5
+NB_FP64, NB_MIXED, NB_DS, NB_HYBRID, NB_MIXED_SPJ, NB_HYBRID_SPJ, NB_FP64_HERMITE6 = \
+    0, 1, 2, 3, 4, 5, 6
 PRECISIONS = {"fp64": NB_FP64, "mixed": NB_MIXED, "ds": NB_DS, "hybrid": NB_HYBRID,
-              "mixed_spj": NB_MIXED_SPJ, "hybrid_spj": NB_HYBRID_SPJ}
+              "mixed_spj": NB_MIXED_SPJ, "hybrid_spj": NB_HYBRID_SPJ,
+              "fp64_hermite6": NB_FP64_HERMITE6}
 
 
 class NbConfig(ctypes.Structure):
@@ -105,6 +107,7 @@ def load(path: str = LIB_PATH):
         "nb_restore": (c_int32, [P, P]),
         "nb_spatial_order": (c_int32, [P, P]),
         "nb_set_j_part": (c_int32, [P, c_int32, c_int32]),
+        "nb_get_snap": (c_int32, [P, P, P, c_int32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -246,6 +249,10 @@ def nb_set_j_part(ctx, part, parts):
     return load().nb_set_j_part(ctx, part, parts)
 
 
+def nb_get_snap(ctx, s, c, on_device):
+    return load().nb_get_snap(ctx, s, c, on_device)
+
+
 def nb_measure_peaks(device, fp32_ref, fp64_ref):
     return load().nb_measure_peaks(device, fp32_ref, fp64_ref)
 
@@ -351,6 +358,13 @@ class Context:
         p = {k: out[k].ctypes.data_as(c_void_p) for k in out}
         self._ck(nb_get_state(self.handle, p["r"], p["v"], p["a"], p["j"], p["t"], p["dt"], 0))
         return out
+
+    def get_snap(self):
+        """Snap and crackle of every particle (sixth-order variant)."""
+        n = self.n
+        s, c = np.empty((n, 3)), np.empty((n, 3))
+        self._ck(nb_get_snap(self.handle, s.ctypes.data_as(c_void_p), c.ctypes.data_as(c_void_p), 0))
+        return s, c
 
     def set_ensemble(self, offsets, m, r, v, eps, eta):
         """k independent systems: system q is [offsets[q], offsets[q+1])."""

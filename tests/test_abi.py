@@ -43,7 +43,7 @@ def test_config_defaults(nbody_lib):
 
 
 @pytest.mark.parametrize("field,value", [("dt_max", 0.1), ("dt_max", -1.0),
-                                         ("precision", 6), ("precision", -1),
+                                         ("precision", 7), ("precision", -1),
                                          ("eta_start", 0.0), ("j_split", 3), ("j_split", 16)])
 def test_create_rejects_bad_config_before_touching_the_gpu(nbody_lib, field, value):
     cfg = nbody_lib.nb_config_init()
