@@ -355,9 +355,12 @@ nb::ForceArgs force_args(nb_ctx* c, Prec p, const nb::JLayout& jl, const int32_t
                          const int32_t* n_act_dev);
 
 nb_status run_force(nb_ctx* c, Prec p, const nb::JLayout& jl, const int32_t* idx,
-                    const int32_t* n_act_dev, int32_t n_act_host = -1)
+                    const int32_t* n_act_dev, int32_t n_act_host = -1,
+                    const int32_t* idx_map = nullptr)
 {
     nb::ForceArgs f = force_args(c, p, jl, idx, n_act_dev);
+    f.n_act_host = n_act_host;  // known here: the kernel need not read it
+    f.idx_map = idx_map;
     if (p == c->prec && c->j_parts > 1) {
         const int64_t nt = c->n_pad / nb::TJ;
         f.jt_lo = nt * c->j_part / c->j_parts;
@@ -422,6 +425,7 @@ nb::ForceArgs force_args(nb_ctx* c, Prec p, const nb::JLayout& jl, const int32_t
     f.status = c->status_dev;
     f.eps2 = c->eps * c->eps;
     f.wait_limit = c->cfg.wait_limit_cycles;
+    f.cta_mode = c->ens ? 0 : 1;
     if (c->ens) {
         // the plan for this active list must have been written by plan_launch
         f.plan.grp_cluster = c->cl.grp_cluster;
@@ -1087,13 +1091,22 @@ nb_status nb_force(nb_ctx* c, int32_t n_act, const int32_t* idx, double* acc, do
         NB_CK(c, cudaMemcpyAsync(c->idx_user, sorted.data(), (size_t)n_act * sizeof(int32_t),
                                  cudaMemcpyHostToDevice, c->stream));
         NB_CK(c, cudaStreamSynchronize(c->stream));  // sorted is a copy source
-    } else if (n_act > 0) {
+    } else if (n_act > 0 && c->ens) {
         NB_CK(c, nb::map_index_launch(idx, c->idx_user, n_act, c->n, c->inv_dev, c->stream));
     }
-    NB_CK(c, nb::set_scalars_launch(c->n_act_user, n_act, nullptr, 0.0, c->stream));
-    if (n_act > 0 &&
-        (s = run_force_list(c, c->prec, c->jl, c->idx_user, c->n_act_user, n_act)) != NB_OK)
-        return s;
+    if (c->ens) {
+        // the ensemble plan reads the block size on the device
+        NB_CK(c, nb::set_scalars_launch(c->n_act_user, n_act, nullptr, 0.0, c->stream));
+        if (n_act > 0 &&
+            (s = run_force_list(c, c->prec, c->jl, c->idx_user, c->n_act_user, n_act)) != NB_OK)
+            return s;
+    } else if (n_act > 0) {
+        // one launch: n_act as a parameter, and a device list in the caller's
+        // numbering mapped to layout slots by the kernel itself
+        if ((s = run_force(c, c->prec, c->jl, on_device ? idx : c->idx_user, c->n_act_user,
+                           n_act, on_device ? c->inv_dev : nullptr)) != NB_OK)
+            return s;
+    }
     c->last_force_n_act = n_act;
     if (n_act > 0 && on_device) {
         const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;

@@ -70,7 +70,30 @@ struct ForceParams {
     // One system: the j tiles [jt_lo, jt_hi) this launch sums over (its part
     // of a j-partitioned force); jt_hi = 0 means every tile.
     int64_t jt_lo, jt_hi;
+    // One system: sum small blocks CTA by CTA (see force_kernel)
+    int32_t cta_mode;
+    // n_act given at launch (>= 0; else read from n_act_dev), and an
+    // optional map of the listed indices (caller numbering -> layout slot)
+    int32_t n_act_host;
+    const int32_t* idx_map;
+    float guard_eta;  // HYBRID: the guard's coefficient times eta
 };
+
+// A double narrowed to FP32 with integer operations only: the top 23
+// mantissa bits (truncated), zero below FP32's normal range, infinity above
+// it (and for NaN).  Within an FP32 ulp of the value, which suffices for the
+// thresholds it feeds.
+__device__ __forceinline__ float f32_trunc(double x)
+{
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const uint32_t hi = static_cast<uint32_t>(b >> 32);
+    const uint32_t sign = hi & 0x80000000u;
+    const int e = static_cast<int>((hi >> 20) & 0x7ffu) - 1023 + 127;
+    if (e <= 0) return __uint_as_float(sign);
+    if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+    const uint32_t mant = ((hi & 0xfffffu) << 3) | (static_cast<uint32_t>(b) >> 29);
+    return __uint_as_float(sign | (static_cast<uint32_t>(e) << 23) | mant);
+}
 
 // ---------------------------------------------------------------------------
 // Precision policies.  Each provides: the j-layout arrays it stages, the
@@ -81,7 +104,7 @@ struct ForceParams {
 template <int IT>
 struct PolicyFP64 {
     static constexpr bool GUARDED = false;
-    static constexpr int MIN_CTAS = 1;
+    static constexpr int MIN_CTAS = 3;  // registers capped for three CTAs per SM
     static constexpr int CHUNKS = 1;
     static constexpr int NARR = 2;
     __host__ __device__ static constexpr int elem(int a) { return a < 2 ? 32 : 0; }
@@ -273,7 +296,7 @@ struct PolicyFP64Snap {
 template <int IT, bool SPJ = false>
 struct PolicyMixed {
     static constexpr bool GUARDED = false;
-    static constexpr int MIN_CTAS = 1;
+    static constexpr int MIN_CTAS = IT > 1 ? 2 : 3;  // registers capped: 2 or 3 CTAs per SM
     static constexpr int CHUNKS = 1;
     static constexpr int NARR = 3;
     __host__ __device__ static constexpr int elem(int a) { return a < 2 ? 16 : (a == 2 ? 8 : 0); }
@@ -663,7 +686,9 @@ struct PolicyHybrid {
     static constexpr int CHUNKS = 4;  // tiles of unequal cost
     static constexpr int NARR = 4;
     __host__ __device__ static constexpr int elem(int a) { return a < 4 ? 16 : 0; }
-    static constexpr int TILE_BYTES = TJ * 64;
+    // the four j arrays of the tile, then its box (two float4, staged with it)
+    static constexpr int BOX_BYTES = 32;
+    static constexpr int TILE_BYTES = TJ * 64 + BOX_BYTES;
     static constexpr int STAGES = 3;
     static constexpr int NV = 8;  // acc, jerk, pot and the noise estimate
 
@@ -678,13 +703,15 @@ struct PolicyHybrid {
         s.particle = particle;
         if (p < 0) return;
         // The near radius and the guard are thresholds, not results: FP32
-        // is ample, and it keeps this per-group set-up off the FP64 pipe.
+        // is ample, and the state's doubles are narrowed with integer
+        // operations (f32_trunc), so this per-group set-up stays off GB300's
+        // narrow FP64 pipe, which every warp of a launch would queue on.
         const int64_t n = f.n;
         float a2 = 0.f, j2 = 0.f;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const float a = static_cast<float>(f.st_a[c * n + particle]);
-            const float jj = static_cast<float>(f.st_j[c * n + particle]);
+            const float a = f32_trunc(f.st_a[c * n + particle]);
+            const float jj = f32_trunc(f.st_j[c * n + particle]);
             a2 = fmaf(a, a, a2);
             j2 = fmaf(jj, jj, j2);
         }
@@ -696,10 +723,9 @@ struct PolicyHybrid {
         const float x = 4.f * V / (HY_THETA * J);
         const float cb = cbrtf(x);
         s.cj = cb * cb;
-        const float hq = static_cast<float>(f.st_hq[particle]);
+        const float hq = f32_trunc(f.st_hq[particle]);
         const float noise = 2.f * static_cast<float>(HY_U) * sqrtf(fabsf(hq));
-        const float scale = static_cast<float>(HY_GUARD * f.eta) * J *
-                            static_cast<float>(f.st_dt[particle]);
+        const float scale = f.guard_eta * J * f32_trunc(f.st_dt[particle]);
         // ratio = 12 noise / scale, compared without a division
         s.all_near = hq < 0.f ? 12.f * noise > static_cast<float>(HY_GUARD_OFF) * scale
                               : 12.f * noise > scale;
@@ -724,14 +750,16 @@ struct PolicyHybrid {
 
     __device__ static bool guarded(const I& s) { return s.all_near; }
 
-    // The far-tile test of one i particle against tile T's box: true when
-    // no pair of the tile can be near.  The box holds the tiles' grid-rounded
-    // positions; the 0.999 keeps the test on the safe side of that rounding.
-    __device__ static bool tile_far(const ForceParams& f, const I& s, int64_t T, float e2h)
+    // The far-tile test of one i particle against the tile's box (staged
+    // after its j arrays): true when no pair of the tile can be near.  The
+    // box holds the tiles' grid-rounded positions; the 0.999 keeps the test
+    // on the safe side of that rounding.
+    __device__ static bool tile_far(const unsigned char* buf, const I& s, float e2h)
     {
         if (s.p < 0) return true;  // an empty lane
-        const float4 lo = __ldg(f.tile_box + 2 * T);
-        const float4 hi = __ldg(f.tile_box + 2 * T + 1);
+        const float4* box = reinterpret_cast<const float4*>(buf + TJ * 64);
+        const float4 lo = box[0];
+        const float4 hi = box[1];
         const float dx = fmaxf(fmaxf(lo.x - s.xh, s.xh - hi.x), 0.f);
         const float dy = fmaxf(fmaxf(lo.y - s.yh, s.yh - hi.y), 0.f);
         const float dz = fmaxf(fmaxf(lo.z - s.zh, s.zh - hi.z), 0.f);
@@ -940,6 +968,22 @@ struct PolicyHybrid {
 
 };
 
+// Bytes of the tile's box staged after its j arrays (policies that test
+// tiles for distance declare BOX_BYTES).
+template <class K, class = void>
+struct BoxBytes {
+    static constexpr int value = 0;
+};
+template <class K>
+struct BoxBytes<K, std::void_t<decltype(K::BOX_BYTES)>> {
+    static constexpr int value = K::BOX_BYTES;
+};
+template <class K>
+__host__ __device__ constexpr int box_bytes()
+{
+    return BoxBytes<K>::value;
+}
+
 template <class K>
 struct WarpSmem {
     static constexpr int BAR_BYTES = 128;  // STAGES mbarriers, padded
@@ -960,6 +1004,7 @@ __device__ __forceinline__ void issue_tile(const ForceParams& f, unsigned char* 
                  bytes, bar);
         dst += bytes;
     }
+    if constexpr (box_bytes<K>() > 0) bulk_g2s(dst, f.tile_box + 2 * jtile, box_bytes<K>(), bar);
 }
 
 // Radix of the deterministic reduction tree over the warps sharing a group.
@@ -1010,6 +1055,9 @@ __device__ __forceinline__ int64_t tile_stride(int64_t nt)
 // The j tile of rank k (0 <= k < ntiles) of a group.
 __device__ __forceinline__ int64_t tile_at(const GroupInfo& g, int64_t k)
 {
+    if (g.ntiles < 65536)  // the product fits 32 bits: a much shorter division
+        return static_cast<int64_t>((static_cast<uint32_t>(k) * static_cast<uint32_t>(g.jstride)) %
+                                    static_cast<uint32_t>(g.ntiles));
     return static_cast<int64_t>((static_cast<uint64_t>(k) * static_cast<uint64_t>(g.jstride)) %
                                 static_cast<uint64_t>(g.ntiles));
 }
@@ -1020,11 +1068,12 @@ struct UniformPlan {
     int64_t n_act, G, NT, T, jstride, J0;
     double eps2;
     int GI;
-    __device__ void init(const ForceParams& f, int gi)
+    template <int GI_>
+    __device__ void init(const ForceParams& f)
     {
-        GI = gi;
-        n_act = *f.n_act_dev;
-        G = (n_act + GI - 1) / GI;
+        GI = GI_;
+        n_act = f.n_act_host >= 0 ? f.n_act_host : *f.n_act_dev;
+        G = (n_act + GI_ - 1) / GI_;
         J0 = f.jt_hi > 0 ? f.jt_lo : 0;
         NT = f.jt_hi > 0 ? f.jt_hi - f.jt_lo : f.n_pad / TJ;
         T = G * NT;
@@ -1054,7 +1103,8 @@ struct ClusterPlan {
     static constexpr bool CHUNKED = false;
     const ForceParams* f;
     int64_t G, T;
-    __device__ void init(const ForceParams& fp, int)
+    template <int GI_>
+    __device__ void init(const ForceParams& fp)
     {
         f = &fp;
         G = fp.plan_scalars[0];
@@ -1106,13 +1156,33 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
         // Launch variants tuned for different block sizes share one stream:
         // each works only inside its n_act window (read on the device, so
         // the host need not know the block size).
-        const int na = *f.n_act_dev;
+        const int na = f.n_act_host >= 0 ? f.n_act_host : *f.n_act_dev;
         if (na < f.nact_lo || na >= f.nact_hi) return;
     }
     Plan plan;
-    plan.init(f, GI);
+    plan.template init<GI>(f);
     const int64_t T = plan.T;
     if (T <= 0) return;
+    // CTA mode (one system, few groups: at least four CTAs per group).  Group
+    // g gets R consecutive CTAs, each a contiguous stretch of its tile walk,
+    // cut in four for the CTA's warps.  The warps' sums meet in shared
+    // memory, in warp order, and each CTA stores one entry; the last CTA of
+    // the group to arrive adds the R entries with all its threads and
+    // writes the results.  For small blocks that replaces the levels of the
+    // warp tree below, each a chain of global-memory round trips, with one.
+    bool cta = false;
+    int64_t cg = 0, cR = 1, crank = 0;
+    if constexpr (Plan::CHUNKED) {
+        if (f.cta_mode && 4 * plan.G <= (int64_t)gridDim.x) {
+            cta = true;
+            const int64_t rmax = (plan.NT + FORCE_WARPS - 1) / FORCE_WARPS;
+            cR = (int64_t)gridDim.x / plan.G;
+            if (cR > rmax) cR = rmax;
+            cg = blockIdx.x / static_cast<uint32_t>(cR);
+            crank = blockIdx.x - static_cast<uint32_t>(cg * cR);
+            if (cg >= plan.G) return;  // the whole CTA: no group left for it
+        }
+    }
     // The flattened (group, tile) space is cut into NCH equal chunks (the
     // stream-K split) and warp w takes chunks w, w + P, ...: KC chunks from
     // KC stretches of the space, so that regions of dearer tiles (the near
@@ -1120,8 +1190,8 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
     // by all warps.  Chunks keep at least CHUNK_MIN_TILES tiles.
     int64_t KC = Plan::CHUNKED ? K::CHUNKS : 1;
     while (KC > 1 && T < P * KC * CHUNK_MIN_TILES) --KC;
-    const int64_t NCH = P * KC < T ? P * KC : T;
-    if (w >= NCH) return;
+    const int64_t NCH = cta ? 1 : (P * KC < T ? P * KC : T);
+    if (!cta && w >= NCH) return;
 
     unsigned char* wsm = smem + (size_t)wib * WarpSmem<K>::BYTES;
     uint64_t* bars = reinterpret_cast<uint64_t*>(wsm);
@@ -1138,13 +1208,56 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
     typename K::Acc ac[IT];
     int64_t used = 0;    // tiles this warp has consumed: ring slot used % STAGES
     int64_t issued = 0;  // tiles this warp has staged
+    bool loaded = false;   // is[] and ac[] set up for a group
+    bool aborted = false;  // a tile wait ran out (CTA mode: the CTA still meets)
 
-    for (int64_t ch = w; ch < NCH; ch += P) {
-    const int64_t t0 = T * ch / NCH;
-    const int64_t t1 = T * (ch + 1) / NCH;
+    // i state of group gi's lanes, accumulators zeroed
+    auto load_group = [&](const GroupInfo& gi) {
+#pragma unroll
+        for (int q = 0; q < IT; ++q) {
+            const int64_t a = gi.act_begin + q * IW + ir;
+            int p = -1, particle = -1;
+            if (a < gi.act_begin + gi.act_count) {
+                particle = f.idx[a];
+                if (particle < 0 || particle >= f.n) {
+                    atomicOr(f.status, ST_BADINDEX);
+                    particle = -1;
+                } else {
+                    if (f.idx_map) particle = f.idx_map[particle];
+                    p = static_cast<int>(particle + gi.pj_shift);
+                }
+            }
+            K::load_i(f, p, particle, is[q]);
+            ac[q].zero();
+        }
+        loaded = true;
+    };
+
+    for (int64_t ch = cta ? 0 : w; ch < NCH; ch += cta ? 1 : P) {
+    int64_t t0, t1;
+    if (!cta) {
+        t0 = T * ch / NCH;
+        t1 = T * (ch + 1) / NCH;
+    }
+    if constexpr (Plan::CHUNKED) {
+        if (cta) {
+            int64_t c0, c1;
+            if (plan.NT * cR < 0x7fffffff) {  // 32-bit divisions: much shorter
+                const uint32_t nt = static_cast<uint32_t>(plan.NT), r = static_cast<uint32_t>(cR);
+                c0 = nt * static_cast<uint32_t>(crank) / r;
+                c1 = nt * static_cast<uint32_t>(crank + 1) / r;
+            } else {
+                c0 = plan.NT * crank / cR;
+                c1 = plan.NT * (crank + 1) / cR;
+            }
+            const int64_t len = c1 - c0;
+            t0 = cg * plan.NT + c0 + len * wib / FORCE_WARPS;
+            t1 = cg * plan.NT + c0 + len * (wib + 1) / FORCE_WARPS;
+        }
+    }
     // Compute cursor (g, gi) and load cursor (lg, lgi): both start at the
     // group of tile t0; the load cursor runs STAGES tiles ahead.
-    int64_t g = plan.find(t0);
+    int64_t g = cta ? cg : plan.find(t0);
     GroupInfo gi = plan.group(g);
     int64_t lg = g;
     GroupInfo lgi = gi;
@@ -1183,22 +1296,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
         if (fresh) {
             fresh = false;
             cpos = tile_at(gi, t - gi.tile0);
-#pragma unroll
-            for (int q = 0; q < IT; ++q) {
-                const int64_t a = gi.act_begin + q * IW + ir;
-                int p = -1, particle = -1;
-                if (a < gi.act_begin + gi.act_count) {
-                    particle = f.idx[a];
-                    if (particle < 0 || particle >= f.n) {
-                        atomicOr(f.status, ST_BADINDEX);
-                        particle = -1;
-                    } else {
-                        p = static_cast<int>(particle + gi.pj_shift);
-                    }
-                }
-                K::load_i(f, p, particle, is[q]);
-                ac[q].zero();
-            }
+            load_group(gi);
             if constexpr (K::GUARDED) {
                 bool gq = false;
 #pragma unroll
@@ -1217,7 +1315,9 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
                 mbar_wait_bounded(&bars[kk % K::STAGES],
                                   static_cast<uint32_t>((kk / K::STAGES) & 1));
             }
-            return;
+            if (!cta) return;
+            aborted = true;  // no tile left in flight; meet the CTA below
+            break;
         }
         ++used;
         const int64_t jt = t - gi.tile0;  // rank of the tile in the group's walk
@@ -1237,7 +1337,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
             if (far) {
                 const float e2h = static_cast<float>(gi.eps2);
 #pragma unroll
-                for (int q = 0; q < IT; ++q) far &= K::tile_far(f, is[q], j0 / TJ, e2h);
+                for (int q = 0; q < IT; ++q) far &= K::tile_far(buf, is[q], e2h);
                 far = __all_sync(0xffffffffu, far);
             }
             if (far) K::template far_tile<S>(buf, gi.eps2, is, ac, sl);
@@ -1258,7 +1358,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
             issue_next();
         }
 
-        if (jt == gi.ntiles - 1 || t == t1 - 1) {
+        if (!cta && (jt == gi.ntiles - 1 || t == t1 - 1)) {
             // This warp's share of group g is complete.  The warps that
             // share the group are summed by a radix-RB tree: within each
             // chunk of RB consecutive contributors the last to arrive adds
@@ -1352,6 +1452,123 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
         }
     }
     }  // chunks
+
+    if (cta) {
+        // CTA mode: this warp's sums (zeros if it had no tile) into its own
+        // ring, which no copy uses any more; the four warps added in warp
+        // order as the CTA's entry; the last CTA of the group adds the
+        // group's R entries in CTA order.
+        constexpr int NV = K::NV;
+        using TV = typename K::TV;
+        constexpr int VALS = NV * GI;
+        constexpr int NTH = FORCE_WARPS * 32;
+        constexpr int PARTS = VALS >= NTH ? 1 : NTH / VALS;
+        static_assert(VALS * sizeof(TV) <= (size_t)K::STAGES * K::TILE_BYTES &&
+                          PARTS * VALS <= (VALS > NTH ? VALS : NTH),
+                      "a warp's ring holds the CTA-mode sums");
+        auto ring_of = [&](int ww) {
+            return reinterpret_cast<TV*>(smem + (size_t)ww * WarpSmem<K>::BYTES +
+                                         WarpSmem<K>::BAR_BYTES);
+        };
+        const GroupInfo cgi = plan.group(cg);
+        (void)aborted;
+        if (!loaded) load_group(cgi);
+        TV v[IT][NV];
+#pragma unroll
+        for (int q = 0; q < IT; ++q) K::values(ac[q], v[q]);
+#pragma unroll
+        for (int o = IW; o < 32; o <<= 1)
+#pragma unroll
+            for (int q = 0; q < IT; ++q)
+#pragma unroll
+                for (int c = 0; c < NV; ++c) tree_xor(v[q][c], o);
+        TV* mine = ring_of(wib);
+        if (sl == 0) {
+#pragma unroll
+            for (int q = 0; q < IT; ++q)
+#pragma unroll
+                for (int c = 0; c < NV; ++c) mine[c * GI + q * IW + ir] = v[q][c];
+        }
+        __syncthreads();
+        uint32_t* last_flag = reinterpret_cast<uint32_t*>(smem + 64);  // warp 0's barrier block
+        if (wib == 0) {
+            for (int vi = lane; vi < VALS; vi += 32) {
+                TV x;
+                tree_zero(x);
+#pragma unroll
+                for (int ww = 0; ww < FORCE_WARPS; ++ww) tree_add(x, ring_of(ww)[vi]);
+                tree_store(f.scratch, (size_t)blockIdx.x * VALS + vi, x);
+            }
+            __syncwarp();
+            // one acquire-release add: publishes this CTA's entry (the warp's
+            // stores precede it through the warp barrier) and, in the last
+            // CTA, makes every other entry visible
+            uint32_t prev = 0;
+            if (lane == 0) prev = atomic_add_acq_rel_gpu(f.counters + cg, 1u);
+            if (lane == 0) *last_flag = prev == static_cast<uint32_t>(cR - 1) ? 1u : 0u;
+        }
+        __syncthreads();
+        if (*last_flag == 0u) return;  // the whole CTA: another one finishes the group
+        __threadfence();
+        const int tid = threadIdx.x;
+        const size_t e0 = (size_t)(cg * cR) * VALS;  // the group's first entry
+        TV* part = ring_of(1);
+        if (PARTS == 1) {
+            for (int vi = tid; vi < VALS; vi += NTH) {
+                TV x;
+                tree_zero(x);
+                for (int64_t u = 0; u < cR; ++u) {
+                    TV y;
+                    tree_load(f.scratch, e0 + (size_t)u * VALS + vi, y);
+                    tree_add(x, y);
+                }
+                part[vi] = x;
+            }
+        } else if (tid < PARTS * VALS) {
+            const int vi = tid % VALS, pp = tid / VALS;
+            const int64_t u0 = cR * pp / PARTS, u1 = cR * (pp + 1) / PARTS;
+            TV x;
+            tree_zero(x);
+            for (int64_t u = u0; u < u1; ++u) {
+                TV y;
+                tree_load(f.scratch, e0 + (size_t)u * VALS + vi, y);
+                tree_add(x, y);
+            }
+            part[pp * VALS + vi] = x;
+        }
+        __syncthreads();
+        TV* fin = part;
+        if (PARTS > 1) {
+            fin = ring_of(2);
+            for (int vi = tid; vi < VALS; vi += NTH) {
+                TV x;
+                tree_zero(x);
+                for (int pp = 0; pp < PARTS; ++pp) tree_add(x, part[pp * VALS + vi]);
+                fin[vi] = x;
+            }
+            __syncthreads();
+        }
+        if (tid == 0) f.counters[cg] = 0u;  // every entry is in: ready for the next launch
+        if (wib == 0 && sl == 0) {
+#pragma unroll
+            for (int q = 0; q < IT; ++q) {
+                const int64_t a = cgi.act_begin + q * IW + ir;
+                if (a < cgi.act_begin + cgi.act_count) {
+                    double o[NV];
+#pragma unroll
+                    for (int c = 0; c < NV; ++c) o[c] = tree_value(fin[c * GI + q * IW + ir]);
+                    f.acc[3 * a + 0] = o[0];
+                    f.acc[3 * a + 1] = o[1];
+                    f.acc[3 * a + 2] = o[2];
+                    f.jerk[3 * a + 0] = o[3];
+                    f.jerk[3 * a + 1] = o[4];
+                    f.jerk[3 * a + 2] = o[5];
+                    f.pot[a] = o[6];
+                    if constexpr (K::NV > 7) K::finish(f, is[q], a, o);
+                }
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1530,6 +1747,10 @@ cudaError_t force_launch(const ForceArgs& a, cudaStream_t s)
     f.eta = a.eta;
     f.jt_lo = a.jt_lo;
     f.jt_hi = a.jt_hi;
+    f.cta_mode = a.cta_mode && !a.plan.grp_tile0;
+    f.n_act_host = a.n_act_host;
+    f.idx_map = a.idx_map;
+    f.guard_eta = static_cast<float>(HY_GUARD * a.eta);
     if (f.jt_hi > 0 && (a.plan.grp_tile0 || f.jt_lo < 0 || f.jt_hi <= f.jt_lo ||
                         f.jt_hi > f.n_pad / TJ))
         return cudaErrorInvalidValue;

@@ -86,6 +86,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
     return ok != 0;
 }
 
+// atomicAdd with acquire-release semantics at GPU scope: the caller's
+// earlier writes are visible to whoever observes the add, and the writes
+// released by earlier adds to the same word are visible to the caller.
+__device__ __forceinline__ uint32_t atomic_add_acq_rel_gpu(uint32_t* p, uint32_t v)
+{
+    uint32_t old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;"
+                 : "=r"(old)
+                 : "l"(p), "r"(v)
+                 : "memory");
+    return old;
+}
+
 // Bounded wait for phase `parity` of `bar`; false after `limit` cycles.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
                                                   long long limit = WAIT_LIMIT_CYCLES)

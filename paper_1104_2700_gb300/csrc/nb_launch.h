@@ -173,6 +173,14 @@ struct ForceArgs {
     // One system only: sum over the j tiles [jt_lo, jt_hi) of the layout
     // (a part of a j-partitioned force); jt_hi = 0: every tile.
     int64_t jt_lo = 0, jt_hi = 0;
+    // One system: blocks of at most a quarter as many i-groups as CTAs are summed
+    // CTA by CTA (shared memory, then one global level) instead of by the
+    // warp tree.
+    int32_t cta_mode = 0;
+    // n_act known at launch (>= 0): the kernel does not read n_act_dev.
+    int32_t n_act_host = -1;
+    // Optional: idx holds caller indices, idx_map[i] is the layout slot of i.
+    const int32_t* idx_map = nullptr;
 };
 
 cudaError_t force_setup(Prec p, int it, int split);  // one-time attribute setup
