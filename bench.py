@@ -416,10 +416,16 @@ def run_ours(args):
 
     def breakdown(ctx, dstates, reps=50):
         """Per block size, warm CUDA-event times (us) of: the state roll-back
-        alone (nb_restore, bench scaffolding), roll-back + one block step, and
-        the force launch alone on that block's active list."""
+        alone (nb_restore, bench scaffolding), roll-back + one block step,
+        roll-back + the force call on that block's active list (all three as
+        replayed CUDA graphs, as the timed step runs), and the force call
+        issued eagerly from Python (host overhead included)."""
         out = {}
         for k, buf in zip(NACTS, ctx.snaps):
+            ctx.restore(buf)
+            ctx.predict(0.0)
+            idx_k = spatial_list(ctx, perm[:k])
+
             def restore():
                 ctx.restore(buf)
 
@@ -427,8 +433,13 @@ def run_ours(args):
                 restore()
                 ctx.block_step(1.0)
 
+            def force():
+                restore()
+                ctx.force(idx_k)
+
             row = {}
-            for name, fn in (("restore_us", restore), ("restore_and_block_step_us", step)):
+            for name, fn in (("restore_us", restore), ("restore_and_block_step_us", step),
+                             ("restore_and_force_us", force)):
                 fn()
                 ctx.synchronize()
                 g = torch.cuda.CUDAGraph()
@@ -445,10 +456,8 @@ def run_ours(args):
                 e1.synchronize()
                 row[name] = e0.elapsed_time(e1) * 1e3 / reps
                 del g
-            restore()
-            ctx.predict(0.0)
-            idx_k = spatial_list(ctx, perm[:k])
-            row["force_us"] = timed_forces(ctx, buf, idx_k, reps) * 1e6
+            row["force_us"] = row["restore_and_force_us"] - row["restore_us"]
+            row["force_us_eager"] = timed_forces(ctx, buf, idx_k, reps) * 1e6
             row["block_step_us"] = row["restore_and_block_step_us"] - row["restore_us"]
             row["non_force_us"] = row["block_step_us"] - row["force_us"]
             out[str(k)] = row

@@ -155,7 +155,7 @@ void free_buffers(nb_ctx* c)
 {
     dfree(c->st.m), dfree(c->st.x), dfree(c->st.v), dfree(c->st.a), dfree(c->st.j);
     dfree(c->st.t), dfree(c->st.dt), dfree(c->st.hq), dfree(c->st.nkey);
-    dfree(c->st.tile_box), dfree(c->perm_dev), dfree(c->inv_dev), dfree(c->order_buf);
+    dfree(c->perm_dev), dfree(c->inv_dev), dfree(c->order_buf);
     c->order_pos.clear();
     c->order_fresh = false;
     c->host_order_stale = false;
@@ -247,8 +247,6 @@ nb_status ensure_capacity(nb_ctx* c, int64_t n, int64_t n_pad, int64_t k)
     NB_CK(c, cudaMalloc(&c->st.nkey, n * sizeof(unsigned long long)));
     NB_CK(c, cudaMalloc(&c->perm_dev, n * sizeof(int32_t)));
     NB_CK(c, cudaMalloc(&c->inv_dev, n * sizeof(int32_t)));
-    if (nb::is_hybrid(c->prec))
-        NB_CK(c, cudaMalloc(&c->st.tile_box, 2 * (n_pad / nb::TJ) * sizeof(float4)));
     // i-groups never mix systems: at most n / 32 + k of them
     const int64_t groups_bound = n + 32 * k;
     nb_status s = alloc_layout(c, c->prec, c->jl, n_pad);
@@ -408,7 +406,6 @@ nb::ForceArgs force_args(nb_ctx* c, Prec p, const nb::JLayout& jl, const int32_t
     f.n_pad = c->n_pad;
     f.idx = idx;
     f.n_act_dev = n_act_dev;
-    f.tile_box = c->st.tile_box;
     f.acc = c->acc1;
     f.jerk = c->jerk1;
     f.pot = c->pot1;

@@ -34,7 +34,6 @@ struct ForceParams {
     int64_t n_pad;
     const int32_t* idx;
     const int32_t* n_act_dev;
-    const float4* tile_box;   // HYBRID: per-tile bounds (two float4 per tile)
     double* acc;
     double* jerk;
     double* pot;
@@ -686,9 +685,7 @@ struct PolicyHybrid {
     static constexpr int CHUNKS = 4;  // tiles of unequal cost
     static constexpr int NARR = 4;
     __host__ __device__ static constexpr int elem(int a) { return a < 4 ? 16 : 0; }
-    // the four j arrays of the tile, then its box (two float4, staged with it)
-    static constexpr int BOX_BYTES = 32;
-    static constexpr int TILE_BYTES = TJ * 64 + BOX_BYTES;
+    static constexpr int TILE_BYTES = TJ * 64;
     static constexpr int STAGES = 3;
     static constexpr int NV = 8;  // acc, jerk, pot and the noise estimate
 
@@ -750,16 +747,18 @@ struct PolicyHybrid {
 
     __device__ static bool guarded(const I& s) { return s.all_near; }
 
-    // The far-tile test of one i particle against the tile's box (staged
-    // after its j arrays): true when no pair of the tile can be near.  The
-    // box holds the tiles' grid-rounded positions; the 0.999 keeps the test
-    // on the safe side of that rounding.
+    // The far-tile test of one i particle against the tile's box: true when
+    // no pair of the tile can be near.  The predictor leaves the box in the
+    // fourth component of the tile's first eight D records (lo_x, lo_y,
+    // lo_z, max G m, hi_x, hi_y, hi_z, max (G m)^(2/3)), so it comes with
+    // the staged tile.  It holds the tile's grid-rounded positions; the
+    // 0.999 keeps the test on the safe side of that rounding.
     __device__ static bool tile_far(const unsigned char* buf, const I& s, float e2h)
     {
         if (s.p < 0) return true;  // an empty lane
-        const float4* box = reinterpret_cast<const float4*>(buf + TJ * 64);
-        const float4 lo = box[0];
-        const float4 hi = box[1];
+        const float4* sD = reinterpret_cast<const float4*>(buf + TJ * 48);
+        const float4 lo = make_float4(sD[0].w, sD[1].w, sD[2].w, sD[3].w);
+        const float4 hi = make_float4(sD[4].w, sD[5].w, sD[6].w, sD[7].w);
         const float dx = fmaxf(fmaxf(lo.x - s.xh, s.xh - hi.x), 0.f);
         const float dy = fmaxf(fmaxf(lo.y - s.yh, s.yh - hi.y), 0.f);
         const float dz = fmaxf(fmaxf(lo.z - s.zh, s.zh - hi.z), 0.f);
@@ -968,22 +967,6 @@ struct PolicyHybrid {
 
 };
 
-// Bytes of the tile's box staged after its j arrays (policies that test
-// tiles for distance declare BOX_BYTES).
-template <class K, class = void>
-struct BoxBytes {
-    static constexpr int value = 0;
-};
-template <class K>
-struct BoxBytes<K, std::void_t<decltype(K::BOX_BYTES)>> {
-    static constexpr int value = K::BOX_BYTES;
-};
-template <class K>
-__host__ __device__ constexpr int box_bytes()
-{
-    return BoxBytes<K>::value;
-}
-
 template <class K>
 struct WarpSmem {
     static constexpr int BAR_BYTES = 128;  // STAGES mbarriers, padded
@@ -1004,7 +987,6 @@ __device__ __forceinline__ void issue_tile(const ForceParams& f, unsigned char* 
                  bytes, bar);
         dst += bytes;
     }
-    if constexpr (box_bytes<K>() > 0) bulk_g2s(dst, f.tile_box + 2 * jtile, box_bytes<K>(), bar);
 }
 
 // Radix of the deterministic reduction tree over the warps sharing a group.
@@ -1017,6 +999,9 @@ __device__ __forceinline__ int64_t owner_warp(int64_t x, int64_t T, int64_t Pu)
 {
     return ((x + 1) * Pu - 1) / T;
 }
+
+// CTA mode: the most tiles per warp it takes on (see force_kernel).
+constexpr int64_t CTA_MAX_TILES = 4;
 
 // Stream-K chunks per warp (largest; policies choose theirs) and the
 // fewest tiles a chunk is cut down to.
@@ -1170,14 +1155,18 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
     // the group to arrive adds the R entries with all its threads and
     // writes the results.  For small blocks that replaces the levels of the
     // warp tree below, each a chain of global-memory round trips, with one.
+    // It is used while it leaves each warp at most CTA_MAX_TILES tiles: past
+    // that the latency it saves is small against the stream-K balance.
     bool cta = false;
     int64_t cg = 0, cR = 1, crank = 0;
     if constexpr (Plan::CHUNKED) {
         if (f.cta_mode && 4 * plan.G <= (int64_t)gridDim.x) {
-            cta = true;
             const int64_t rmax = (plan.NT + FORCE_WARPS - 1) / FORCE_WARPS;
-            cR = (int64_t)gridDim.x / plan.G;
+            cR = gridDim.x / static_cast<uint32_t>(plan.G);  // G < gridDim.x / 4
             if (cR > rmax) cR = rmax;
+            cta = plan.NT <= cR * FORCE_WARPS * CTA_MAX_TILES;
+        }
+        if (cta) {
             cg = blockIdx.x / static_cast<uint32_t>(cR);
             crank = blockIdx.x - static_cast<uint32_t>(cg * cR);
             if (cg >= plan.G) return;  // the whole CTA: no group left for it
@@ -1509,7 +1498,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
         }
         __syncthreads();
         if (*last_flag == 0u) return;  // the whole CTA: another one finishes the group
-        __threadfence();
+        // (thread 0's acquire, passed on by the barrier, orders the loads below)
         const int tid = threadIdx.x;
         const size_t e0 = (size_t)(cg * cR) * VALS;  // the group's first entry
         TV* part = ring_of(1);
@@ -1717,7 +1706,6 @@ cudaError_t force_launch(const ForceArgs& a, cudaStream_t s)
     f.n_pad = a.n_pad;
     f.idx = a.idx;
     f.n_act_dev = a.n_act_dev;
-    f.tile_box = a.tile_box;
     f.acc = a.acc;
     f.jerk = a.jerk;
     f.pot = a.pot;
@@ -1756,7 +1744,7 @@ cudaError_t force_launch(const ForceArgs& a, cudaStream_t s)
         return cudaErrorInvalidValue;
     if (a.prec == Prec::FP64_H6 && !f.snap) return cudaErrorInvalidValue;
     if (is_hybrid(a.prec) &&
-        (!f.st_a || !f.st_j || !f.bound_v || !f.st_dt || !f.st_hq || !f.tile_box))
+        (!f.st_a || !f.st_j || !f.bound_v || !f.st_dt || !f.st_hq))
         return cudaErrorInvalidValue;
     void* args[] = {&f};
     return cudaLaunchKernel(fn, dim3(a.grid), dim3(FORCE_WARPS * 32), args,

@@ -306,11 +306,14 @@ __global__ void predict_ds_kernel(const StateDev st, const JLayout jl, const dou
         // (G m)^(2/3): the hybrid precision's near-pair test
         const float g23 = cbrtf(gm.hi);
         static_cast<float4*>(jl.arr[2])[q] = make_float4(vh[0], vh[1], vh[2], g23 * g23);
-        static_cast<float4*>(jl.arr[3])[q] = make_float4(vl[0], vl[1], vl[2], 0.f);
+        float box = 0.f;
         if (HYB) {
             // the tile's box (hi parts; a ghost adds nothing) and its
             // largest G m and (G m)^(2/3), for the force kernel's test of
-            // whether a whole tile is far from an i particle
+            // whether a whole tile is far from an i particle.  It rides in
+            // the spare fourth component of the tile's first eight D
+            // records (lo_x, lo_y, lo_z, max G m, hi_x, hi_y, hi_z,
+            // max (G m)^(2/3)), so it arrives with the tile at no extra copy.
             TileExtent e;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -320,12 +323,19 @@ __global__ void predict_ds_kernel(const StateDev st, const JLayout jl, const dou
             e.gm = gm.hi;
             e.g23 = g23 * g23;
             tile_extent_reduce(e);
-            if (threadIdx.x == 0) {
-                const int64_t T = q / TJ;
-                st.tile_box[2 * T] = make_float4(e.lo[0], e.lo[1], e.lo[2], e.gm);
-                st.tile_box[2 * T + 1] = make_float4(e.hi[0], e.hi[1], e.hi[2], e.g23);
+            switch (threadIdx.x) {
+            case 0: box = e.lo[0]; break;
+            case 1: box = e.lo[1]; break;
+            case 2: box = e.lo[2]; break;
+            case 3: box = e.gm; break;
+            case 4: box = e.hi[0]; break;
+            case 5: box = e.hi[1]; break;
+            case 6: box = e.hi[2]; break;
+            case 7: box = e.g23; break;
+            default: break;
             }
         }
+        static_cast<float4*>(jl.arr[3])[q] = make_float4(vl[0], vl[1], vl[2], box);
     }
 }
 
@@ -411,7 +421,6 @@ cudaError_t predict_launch(const StateDev& st, Prec p, const JLayout& jl, double
         break;
     case Prec::HYBRID:
     case Prec::HYBRID_SPJ:  // same j layout
-        if (!st.tile_box) return cudaErrorInvalidValue;
         predict_ds_kernel<static_cast<int>(Prec::HYBRID)>
             <<<blocks, threads, 0, s>>>(st, jl, G, t_bits, t_host, n_act_dev, jsrc, cof);
         break;

@@ -56,10 +56,6 @@ struct StateDev {
     // Per particle, the order-preserving key of its next time t_i + dt_i,
     // kept by every writer of t and dt so that step 1 compares integers.
     unsigned long long* nkey = nullptr;
-    // HYBRID only: per j tile, a box around its predicted positions and its
-    // largest masses (written by the predictor): tile_box[2T] = (lo_x, lo_y,
-    // lo_z, max G m), tile_box[2T + 1] = (hi_x, hi_y, hi_z, max (G m)^(2/3)).
-    float4* tile_box = nullptr;
 };
 
 // bound[0] = max |a_k|, bound[1] = max |b_k| over k < count (float bits,
@@ -147,7 +143,6 @@ struct ForceArgs {
     int64_t n_pad = 0;   // j count incl. ghosts, multiple of TJ
     const int32_t* idx = nullptr;
     const int32_t* n_act_dev = nullptr;
-    const float4* tile_box = nullptr;  // HYBRID: per-tile bounds (StateDev::tile_box)
     double* acc = nullptr;   // [n_act][3]
     double* jerk = nullptr;  // [n_act][3]
     double* pot = nullptr;   // [n_act]
