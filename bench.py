@@ -71,6 +71,10 @@ def parse_args():
     p.add_argument("--profile", choices=["mixed", "hybrid", "ds", "fp64"], default=None,
                    help="only run --launches force launches (for ncu), no timing")
     p.add_argument("--profile-nact", type=int, default=16384)
+    p.add_argument("--profile-n", type=int, choices=[16384, 65536], default=16384,
+                   help="the profiled workload: the N = 16384 sweep (a random active "
+                        "list) or the N = 65536 roofline workload (every particle, in the "
+                        "context's spatial order, no noise history)")
     p.add_argument("--profile-steps", choices=["sweep", "ensemble"], default=None,
                    help="only run a few eager HYBRID block steps of the N = 16384 "
                         "workload or the 256-system ensemble (for ncu), no timing")
@@ -163,24 +167,34 @@ def run_profile_steps(args):
 
 
 def run_profile(args):
-    """A few force launches of one precision on the sweep workload (for ncu)."""
+    """A few force launches of one precision on the sweep workload or the
+    N = 65536 roofline workload (for ncu)."""
     import torch
     from paper_1104_2700_gb300 import build as nb_build
     from paper_1104_2700_gb300 import nbody
     nb_build.build()
-    n, eps = WL.n, WL.eps
-    m, r, v = WL.particles()
-    idx = torch.from_numpy(ics.permutation(n, WL.seed)[:args.profile_nact].astype(np.int32)).cuda()
+    wl = WL if args.profile_n == 16384 else ics.MIXED_N64K
+    n, eps = wl.n, wl.eps
+    m, r, v = wl.particles()
     it, split, cps = (int(x) for x in args.profile_shape.split(","))
     with nbody.Context(args.profile, i_per_thread=it, j_split=split, ctas_per_sm=cps) as ctx:
         # loading evaluates every force once (the launch ncu skips with -s 1)
         # and leaves a, j in the state for the hybrid near-pair test
-        ctx.set_particles(m, r, v, eps, WL.eta)
+        ctx.set_particles(m, r, v, eps, wl.eta)
+        if args.profile_n == 16384:
+            members = ics.permutation(n, WL.seed)[:args.profile_nact]
+        else:
+            # as the bench's roofline: every particle in the spatial order,
+            # the state reloaded so that no noise history arms the guard
+            st = ctx.get_state()
+            ctx.set_state(m, st["r"], st["v"], st["a"], st["j"], st["t"], st["dt"], eps, wl.eta)
+            members = ctx.spatial_order()
+        idx = torch.from_numpy(np.asarray(members).astype(np.int32)).cuda()
         ctx.predict(0.0)
         for _ in range(args.launches):
             ctx.force(idx)
         ctx.synchronize()
-    print(json.dumps({"profile": args.profile, "n": n, "n_act": args.profile_nact,
+    print(json.dumps({"profile": args.profile, "n": n, "n_act": len(members),
                       "launches": args.launches, "shape": [it, split, cps]}))
 
 

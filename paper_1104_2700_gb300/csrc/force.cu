@@ -94,6 +94,21 @@ __device__ __forceinline__ float f32_trunc(double x)
     return __uint_as_float(sign | (static_cast<uint32_t>(e) << 23) | mant);
 }
 
+// eps^2 of a group's system, as the FP64 value and its FP32 hi + lo split
+// (made once per group, so the tile loops do no FP64 conversion).
+struct Eps2 {
+    double d;
+    float h, l;
+};
+__device__ __forceinline__ Eps2 make_eps2(double e2)
+{
+    Eps2 r;
+    r.d = e2;
+    r.h = static_cast<float>(e2);
+    r.l = static_cast<float>(e2 - static_cast<double>(r.h));
+    return r;
+}
+
 // ---------------------------------------------------------------------------
 // Precision policies.  Each provides: the j-layout arrays it stages, the
 // i state it keeps in registers, the per-tile pair loop and the final values.
@@ -136,9 +151,10 @@ struct PolicyFP64 {
 
     // S lanes share each i; lane slice sl takes records sl, sl + S, ...
     template <bool MASK, int S>
-    __device__ static void tile(const unsigned char* buf, int64_t j0, const double eps2,
+    __device__ static void tile(const unsigned char* buf, int64_t j0, const Eps2& e2s,
                                 I (&is)[IT], Acc (&ac)[IT], int sl)
     {
+        const double eps2 = e2s.d;
         const double2* sP = reinterpret_cast<const double2*>(buf);
         const double2* sV = reinterpret_cast<const double2*>(buf + TJ * 32);
 #pragma unroll 2
@@ -225,9 +241,10 @@ struct PolicyFP64Snap {
     }
 
     template <bool MASK, int S>
-    __device__ static void tile(const unsigned char* buf, int64_t j0, const double eps2,
+    __device__ static void tile(const unsigned char* buf, int64_t j0, const Eps2& e2s,
                                 I (&is)[IT], Acc (&ac)[IT], int sl)
     {
+        const double eps2 = e2s.d;
         const double2* sP = reinterpret_cast<const double2*>(buf);
         const double2* sV = reinterpret_cast<const double2*>(buf + TJ * 32);
         const double2* sA = reinterpret_cast<const double2*>(buf + TJ * 64);
@@ -330,13 +347,13 @@ struct PolicyMixed {
     }
 
     template <bool MASK, int S>
-    __device__ static void tile(const unsigned char* buf, int64_t j0, const double eps2d,
+    __device__ static void tile(const unsigned char* buf, int64_t j0, const Eps2& e2s,
                                 I (&is)[IT], Acc (&ac)[IT], int sl)
     {
         const float4* sA = reinterpret_cast<const float4*>(buf);
         const float4* sB = reinterpret_cast<const float4*>(buf + TJ * 16);
         const float2* sC = reinterpret_cast<const float2*>(buf + TJ * 32);
-        const float eps2 = static_cast<float>(eps2d);
+        const float eps2 = e2s.h;
         float ax[IT], ay[IT], az[IT], jx[IT], jy[IT], jz[IT], ph[IT];
 #pragma unroll
         for (int q = 0; q < IT; ++q) {
@@ -579,15 +596,15 @@ struct PolicyDS {
     __device__ static void load_i(const ForceParams& f, int p, int, I& s) { ds_load_i(f, p, s); }
 
     template <bool MASK, int S>
-    __device__ static void tile(const unsigned char* buf, int64_t j0, const double eps2d,
+    __device__ static void tile(const unsigned char* buf, int64_t j0, const Eps2& e2s,
                                 I (&is)[IT], Acc (&ac)[IT], int sl)
     {
         const float4* sA = reinterpret_cast<const float4*>(buf);
         const float4* sB = reinterpret_cast<const float4*>(buf + TJ * 16);
         const float4* sC = reinterpret_cast<const float4*>(buf + TJ * 32);
         const float4* sD = reinterpret_cast<const float4*>(buf + TJ * 48);
-        const float e2h = static_cast<float>(eps2d);
-        const float e2l = static_cast<float>(eps2d - static_cast<double>(e2h));
+        const float e2h = e2s.h;
+        const float e2l = e2s.l;
 #pragma unroll 1
         for (int u = 0; u < TJ / S; ++u) {
             const int k = sl + S * u;
@@ -769,7 +786,7 @@ struct PolicyHybrid {
     // Far path: no pair of the tile is near for any lane of the warp, and no
     // lane's own particle is in it.  Lane slice sl takes records sl + S u.
     template <int S>
-    __device__ static void far_tile(const unsigned char* buf, const double eps2d, I (&is)[IT],
+    __device__ static void far_tile(const unsigned char* buf, const Eps2& e2s, I (&is)[IT],
                                     Acc (&ac)[IT], int sl)
     {
         constexpr int R = TJ / S;
@@ -777,7 +794,7 @@ struct PolicyHybrid {
         const float4* sA = reinterpret_cast<const float4*>(buf);
         const float4* sB = reinterpret_cast<const float4*>(buf + TJ * 16);
         const float4* sC = reinterpret_cast<const float4*>(buf + TJ * 32);
-        const float e2h = static_cast<float>(eps2d);
+        const float e2h = e2s.h;
 #pragma unroll 1
         for (int u0 = 0; u0 < R; u0 += RUN) {
             float ax[IT], ay[IT], az[IT], jx[IT], jy[IT], jz[IT], ph[IT], bs[IT];
@@ -842,7 +859,7 @@ struct PolicyHybrid {
     // (rare); the other instantiation assumes none has, so near is the
     // natural test and the noise estimate reuses the far-pair factor m / r.
     template <bool MASK, bool GUARD, int S>
-    __device__ static void tile(const unsigned char* buf, int64_t j0, const double eps2d,
+    __device__ static void tile(const unsigned char* buf, int64_t j0, const Eps2& e2s,
                                 I (&is)[IT], Acc (&ac)[IT], int sl)
     {
         static_assert(TJ == 64, "one 64-bit near mask per lane and tile");
@@ -853,8 +870,8 @@ struct PolicyHybrid {
         const float4* sB = reinterpret_cast<const float4*>(buf + TJ * 16);
         const float4* sC = reinterpret_cast<const float4*>(buf + TJ * 32);
         const float4* sD = reinterpret_cast<const float4*>(buf + TJ * 48);
-        const float e2h = static_cast<float>(eps2d);
-        const float e2l = static_cast<float>(eps2d - static_cast<double>(e2h));
+        const float e2h = e2s.h;
+        const float e2l = e2s.l;
         // Pass 1: every pair in FP32; near pairs add nothing here and are
         // marked in a per-lane 64-bit mask (bit u = slot sl + S u).
         uint32_t nlo[IT], nhi[IT];
@@ -1016,7 +1033,7 @@ struct GroupInfo {
     int64_t jtile0;                // first j tile of its system in the j layout
     int64_t jstride;               // tile walk: rank k -> j tile k * jstride mod ntiles
     int64_t pj_shift;              // j-layout slot of particle p = p + pj_shift
-    double eps2;
+    Eps2 e2;
 };
 
 // A group walks its system's j tiles in the order k -> k * stride mod
@@ -1051,7 +1068,7 @@ __device__ __forceinline__ int64_t tile_at(const GroupInfo& g, int64_t k)
 struct UniformPlan {
     static constexpr bool CHUNKED = true;
     int64_t n_act, G, NT, T, jstride, J0;
-    double eps2;
+    Eps2 e2;
     int GI;
     template <int GI_>
     __device__ void init(const ForceParams& f)
@@ -1063,7 +1080,7 @@ struct UniformPlan {
         NT = f.jt_hi > 0 ? f.jt_hi - f.jt_lo : f.n_pad / TJ;
         T = G * NT;
         jstride = tile_stride(NT);
-        eps2 = f.eps2;
+        e2 = make_eps2(f.eps2);
     }
     __device__ int64_t find(int64_t t) const { return t / NT; }
     __device__ GroupInfo group(int64_t g) const
@@ -1076,7 +1093,7 @@ struct UniformPlan {
         gi.jtile0 = J0;
         gi.jstride = jstride;
         gi.pj_shift = 0;
-        gi.eps2 = eps2;
+        gi.e2 = e2;
         return gi;
     }
 };
@@ -1115,7 +1132,7 @@ struct ClusterPlan {
         gi.jtile0 = f->cl_joff[c] / TJ;
         gi.jstride = tile_stride(gi.ntiles);
         gi.pj_shift = f->cl_joff[c] - f->cl_off[c];
-        gi.eps2 = f->cl_eps2[c];
+        gi.e2 = make_eps2(f->cl_eps2[c]);
         return gi;
     }
 };
@@ -1324,22 +1341,22 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
             // has the guard on and the tile is far from every lane's i
             bool far = !mask_self && !guard_any;
             if (far) {
-                const float e2h = static_cast<float>(gi.eps2);
+                const float e2h = gi.e2.h;
 #pragma unroll
                 for (int q = 0; q < IT; ++q) far &= K::tile_far(buf, is[q], e2h);
                 far = __all_sync(0xffffffffu, far);
             }
-            if (far) K::template far_tile<S>(buf, gi.eps2, is, ac, sl);
+            if (far) K::template far_tile<S>(buf, gi.e2, is, ac, sl);
             else if (guard_any) {
-                if (mask_self) K::template tile<true, true, S>(buf, j0, gi.eps2, is, ac, sl);
-                else K::template tile<false, true, S>(buf, j0, gi.eps2, is, ac, sl);
+                if (mask_self) K::template tile<true, true, S>(buf, j0, gi.e2, is, ac, sl);
+                else K::template tile<false, true, S>(buf, j0, gi.e2, is, ac, sl);
             } else {
-                if (mask_self) K::template tile<true, false, S>(buf, j0, gi.eps2, is, ac, sl);
-                else K::template tile<false, false, S>(buf, j0, gi.eps2, is, ac, sl);
+                if (mask_self) K::template tile<true, false, S>(buf, j0, gi.e2, is, ac, sl);
+                else K::template tile<false, false, S>(buf, j0, gi.e2, is, ac, sl);
             }
         } else {
-            if (mask_self) K::template tile<true, S>(buf, j0, gi.eps2, is, ac, sl);
-            else K::template tile<false, S>(buf, j0, gi.eps2, is, ac, sl);
+            if (mask_self) K::template tile<true, S>(buf, j0, gi.e2, is, ac, sl);
+            else K::template tile<false, S>(buf, j0, gi.e2, is, ac, sl);
         }
         __syncwarp();
         if (t + K::STAGES < t1) {
