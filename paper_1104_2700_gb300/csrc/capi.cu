@@ -78,11 +78,11 @@ struct nb_ctx {
     cudaGraphExec_t step_graph = nullptr;
     double graph_t_end = 0.0;
     // The particles are stored in a spatial order: internal index k holds the
-    // caller's particle perm[k] (inv is the inverse).  Within each system the
-    // order follows a Morton curve through the system's bounding box, so the
-    // j tiles and the i-groups cut from the (ascending) active lists are each
-    // close together in space, which the hybrid precision's far-tile test
-    // needs.  The order is a pure function of the caller-order positions it
+    // caller's particle perm[k] (inv is the inverse).  For one system the
+    // order follows a Morton curve through its bounding box, so the j tiles
+    // and the i-groups cut from the (ascending) active lists are each close
+    // together in space, which the hybrid precision's far-tile test needs;
+    // an ensemble keeps the order it was given (see order_of).  The order is a pure function of the caller-order positions it
     // was computed from (kept in order_pos, with the systems' offsets in
     // order_off): it is recomputed at every load and at the start of every
     // nb_step_until, so a run resumed from a checkpoint gets the order the

@@ -1017,8 +1017,10 @@ __device__ __forceinline__ int64_t owner_warp(int64_t x, int64_t T, int64_t Pu)
     return ((x + 1) * Pu - 1) / T;
 }
 
-// CTA mode: the most tiles per warp it takes on (see force_kernel).
+// CTA mode: the most tiles per warp it takes on, and the most entries a
+// thread loads in one batch when CTAs' entries are added (see force_kernel).
 constexpr int64_t CTA_MAX_TILES = 4;
+constexpr int CTA_BATCH = 16;
 
 // Stream-K chunks per warp (largest; policies choose theirs) and the
 // fewest tiles a chunk is cut down to.
@@ -1497,64 +1499,80 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
         }
         __syncthreads();
         uint32_t* last_flag = reinterpret_cast<uint32_t*>(smem + 64);  // warp 0's barrier block
+        const int tid = threadIdx.x;
+        const int64_t key = cg * cR;  // slot of the group's first entry
+        // Level 0: this CTA's entry, its warps' sums added in warp order.
         if (wib == 0) {
             for (int vi = lane; vi < VALS; vi += 32) {
                 TV x;
                 tree_zero(x);
 #pragma unroll
                 for (int ww = 0; ww < FORCE_WARPS; ++ww) tree_add(x, ring_of(ww)[vi]);
-                tree_store(f.scratch, (size_t)blockIdx.x * VALS + vi, x);
+                tree_store(f.scratch, (size_t)(key + crank) * VALS + vi, x);
             }
-            __syncwarp();
-            // one acquire-release add: publishes this CTA's entry (the warp's
-            // stores precede it through the warp barrier) and, in the last
-            // CTA, makes every other entry visible
-            uint32_t prev = 0;
-            if (lane == 0) prev = atomic_add_acq_rel_gpu(f.counters + cg, 1u);
-            if (lane == 0) *last_flag = prev == static_cast<uint32_t>(cR - 1) ? 1u : 0u;
         }
-        __syncthreads();
-        if (*last_flag == 0u) return;  // the whole CTA: another one finishes the group
-        // (thread 0's acquire, passed on by the barrier, orders the loads below)
-        const int tid = threadIdx.x;
-        const size_t e0 = (size_t)(cg * cR) * VALS;  // the group's first entry
+        // The entries meet in a tree, as the warps' sums do in warp mode, but
+        // each chunk is added by all the threads of its last CTA, each thread
+        // loading at most CTA_BATCH entries of one value in one batch: the
+        // radix is CTA_BATCH times the parts the CTA's threads split a value
+        // into.  Level L entry r sits in slot key + r * RADIX^L, and a chunk's
+        // sum takes its first entry's slot.
+        constexpr int RADIX = CTA_BATCH * PARTS;
         TV* part = ring_of(1);
-        if (PARTS == 1) {
-            for (int vi = tid; vi < VALS; vi += NTH) {
-                TV x;
-                tree_zero(x);
-                for (int64_t u = 0; u < cR; ++u) {
-                    TV y;
-                    tree_load(f.scratch, e0 + (size_t)u * VALS + vi, y);
-                    tree_add(x, y);
-                }
-                part[vi] = x;
-            }
-        } else if (tid < PARTS * VALS) {
-            const int vi = tid % VALS, pp = tid / VALS;
-            const int64_t u0 = cR * pp / PARTS, u1 = cR * (pp + 1) / PARTS;
-            TV x;
-            tree_zero(x);
-            for (int64_t u = u0; u < u1; ++u) {
-                TV y;
-                tree_load(f.scratch, e0 + (size_t)u * VALS + vi, y);
-                tree_add(x, y);
-            }
-            part[pp * VALS + vi] = x;
-        }
-        __syncthreads();
-        TV* fin = part;
-        if (PARTS > 1) {
-            fin = ring_of(2);
-            for (int vi = tid; vi < VALS; vi += NTH) {
-                TV x;
-                tree_zero(x);
-                for (int pp = 0; pp < PARTS; ++pp) tree_add(x, part[pp * VALS + vi]);
-                fin[vi] = x;
+        TV* fin = ring_of(2);
+        int64_t kk = cR, r = crank, stride = 1;
+        for (int level = 0;; ++level) {
+            // every store of this CTA's entry precedes thread 0's release
+            __syncthreads();
+            const int64_t chunk = r / RADIX, first = chunk * RADIX;
+            const int cs = static_cast<int>(kk - first < RADIX ? kk - first : RADIX);
+            if (tid == 0) {
+                uint32_t* cnt = f.counters + (size_t)level * f.counter_stride + key + chunk;
+                const uint32_t prev = atomic_add_acq_rel_gpu(cnt, 1u);
+                const bool last = prev == static_cast<uint32_t>(cs - 1);
+                if (last) *cnt = 0u;  // the whole chunk is in: ready for the next launch
+                *last_flag = last ? 1u : 0u;
             }
             __syncthreads();
+            if (*last_flag == 0u) return;  // the whole CTA: another one carries the chunk on
+            // (thread 0's acquire, passed on by the barrier, orders the loads below)
+            const size_t e0 = (size_t)(key + first * stride) * VALS;
+            const size_t es = (size_t)stride * VALS;
+            auto sum_entries = [&](int vi, int u0, int u1) {  // u1 - u0 <= CTA_BATCH
+                TV y[CTA_BATCH];
+#pragma unroll
+                for (int k = 0; k < CTA_BATCH; ++k)
+                    if (u0 + k < u1) tree_load(f.scratch, e0 + (size_t)(u0 + k) * es + vi, y[k]);
+                TV x;
+                tree_zero(x);
+#pragma unroll
+                for (int k = 0; k < CTA_BATCH; ++k)
+                    if (u0 + k < u1) tree_add(x, y[k]);
+                return x;
+            };
+            if (PARTS == 1) {
+                for (int vi = tid; vi < VALS; vi += NTH) fin[vi] = sum_entries(vi, 0, cs);
+            } else {
+                if (tid < PARTS * VALS) {
+                    const int vi = tid % VALS, pp = tid / VALS;
+                    part[pp * VALS + vi] = sum_entries(vi, cs * pp / PARTS, cs * (pp + 1) / PARTS);
+                }
+                __syncthreads();
+                for (int vi = tid; vi < VALS; vi += NTH) {
+                    TV x;
+                    tree_zero(x);
+                    for (int pp = 0; pp < PARTS; ++pp) tree_add(x, part[pp * VALS + vi]);
+                    fin[vi] = x;
+                }
+            }
+            __syncthreads();
+            r = chunk;
+            kk = (kk + RADIX - 1) / RADIX;
+            stride *= RADIX;
+            if (kk == 1) break;  // fin holds the group's sums
+            for (int vi = tid; vi < VALS; vi += NTH)
+                tree_store(f.scratch, (size_t)(key + r * stride) * VALS + vi, fin[vi]);
         }
-        if (tid == 0) f.counters[cg] = 0u;  // every entry is in: ready for the next launch
         if (wib == 0 && sl == 0) {
 #pragma unroll
             for (int q = 0; q < IT; ++q) {
