@@ -383,6 +383,7 @@ nb_status run_force(nb_ctx* c, Prec p, const nb::JLayout& jl, const int32_t* idx
         f.it = c->var[v].it;
         f.split = c->var[v].split;
         f.grid = c->var[v].grid;
+        f.cta_mode = !c->ens && v == 0;  // small blocks: CTA-level sums
         f.nact_lo = v == 0 ? 0 : c->nact_split;
         f.nact_hi = v == 0 ? c->nact_split : 0x7fffffff;
         if (n_act_host >= 0 && (n_act_host < f.nact_lo || n_act_host >= f.nact_hi)) continue;
@@ -422,7 +423,7 @@ nb::ForceArgs force_args(nb_ctx* c, Prec p, const nb::JLayout& jl, const int32_t
     f.status = c->status_dev;
     f.eps2 = c->eps * c->eps;
     f.wait_limit = c->cfg.wait_limit_cycles;
-    f.cta_mode = c->ens ? 0 : 1;
+    f.cta_mode = 0;  // the small-block build: run_force and the autotuner choose it
     if (c->ens) {
         // the plan for this active list must have been written by plan_launch
         f.plan.grp_cluster = c->cl.grp_cluster;
@@ -1433,7 +1434,8 @@ nb_status nb_autotune(nb_ctx* c, nb_tuning* out)
     if ((nb::is_mixed(c->prec) || nb::is_hybrid(c->prec)) && !c->ens) shapes.push_back({2, 1});
     struct Cand {
         int it, split, cps;
-        double us[4];
+        double us[4];   // with the small-block build (probes 0-2)
+        double usl[4];  // with the large-block build (probes 2-3)
     };
     std::vector<Cand> cands;
     int max_grid = 0;
@@ -1443,7 +1445,7 @@ nb_status nb_autotune(nb_ctx* c, nb_tuning* out)
         const int occ = nb::force_ctas_per_sm(c->prec, sh.first, sh.second);
         for (int cps : {1, 2, 3, 4, 5, 6, 8})
             if (cps <= occ) {
-                cands.push_back({sh.first, sh.second, cps, {0, 0, 0, 0}});
+                cands.push_back({sh.first, sh.second, cps, {0, 0, 0, 0}, {0, 0, 0, 0}});
                 max_grid = std::max(max_grid, cps * c->num_sms);
             }
     }
@@ -1493,16 +1495,23 @@ nb_status nb_autotune(nb_ctx* c, nb_tuning* out)
             f.it = cd.it;
             f.split = cd.split;
             f.grid = cd.cps * c->num_sms;
-            const int reps = 3;
-            cudaError_t e = nb::force_launch(f, c->stream);  // warm-up
-            if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
-            for (int k = 0; k < reps && e == cudaSuccess; ++k) e = nb::force_launch(f, c->stream);
-            if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            float ms = 0.f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            if (e != cudaSuccess) st = fail(c, NB_ECUDA, "autotune: %s", cudaGetErrorString(e));
-            cd.us[q] = 1e3 * ms / reps;
+            // the small bucket's probes (0-2) with the build its variant runs
+            // (CTA-level sums), the large bucket's (2-3) with the plain one
+            for (int build = 0; build < 2 && st == NB_OK; ++build) {
+                const bool small = build == 0;
+                if ((small && q > 2) || (!small && q < 2)) continue;
+                f.cta_mode = small && !c->ens;
+                const int reps = 3;
+                cudaError_t e = nb::force_launch(f, c->stream);  // warm-up
+                if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+                for (int k = 0; k < reps && e == cudaSuccess; ++k) e = nb::force_launch(f, c->stream);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e != cudaSuccess) st = fail(c, NB_ECUDA, "autotune: %s", cudaGetErrorString(e));
+                (small ? cd.us : cd.usl)[q] = 1e3 * ms / reps;
+            }
         }
     }
     cudaEventDestroy(e0);
@@ -1519,7 +1528,7 @@ nb_status nb_autotune(nb_ctx* c, nb_tuning* out)
     // (i per thread, j split) with the least total time.
     auto bucket_us = [](const Cand& cd, int lo, int hi) {
         double t = 0.0;
-        for (int q = lo; q < hi; ++q) t += cd.us[q];
+        for (int q = lo; q < hi; ++q) t += lo == 0 ? cd.us[q] : cd.usl[q];
         return t;
     };
     auto best_of = [&](int lo, int hi, int it, int split) {

@@ -1139,10 +1139,152 @@ struct ClusterPlan {
     }
 };
 
+// CTA mode, after the tiles: this warp's sums (zeros if it had no tile) into
+// its own ring, which no copy uses any more; the four warps added in warp
+// order as the CTA's entry; the CTAs' entries of group cg added in a tree
+// whose last CTA writes the results.  Kept out of line: inlined, it changed
+// the register allocation of the tile loops and cost ~3 % on large blocks.
+template <class K, int IT, int S>
+__device__ __noinline__ void cta_finish(const ForceParams& f, unsigned char* smem,
+                                        const typename K::I (&is)[IT],
+                                        const typename K::Acc (&ac)[IT], const GroupInfo& cgi,
+                                        int64_t cg, int64_t cR, int64_t crank)
+{
+    constexpr int IW = 32 / S;
+    constexpr int GI = IW * IT;
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int ir = lane % IW, sl = lane / IW;
+    constexpr int NV = K::NV;
+    using TV = typename K::TV;
+    constexpr int VALS = NV * GI;
+    constexpr int NTH = FORCE_WARPS * 32;
+    constexpr int PARTS = VALS >= NTH ? 1 : NTH / VALS;
+    static_assert(VALS * sizeof(TV) <= (size_t)K::STAGES * K::TILE_BYTES &&
+                      PARTS * VALS <= (VALS > NTH ? VALS : NTH),
+                  "a warp's ring holds the CTA-mode sums");
+    auto ring_of = [&](int ww) {
+        return reinterpret_cast<TV*>(smem + (size_t)ww * WarpSmem<K>::BYTES +
+                                     WarpSmem<K>::BAR_BYTES);
+    };
+    TV v[IT][NV];
+#pragma unroll
+    for (int q = 0; q < IT; ++q) K::values(ac[q], v[q]);
+#pragma unroll
+    for (int o = IW; o < 32; o <<= 1)
+#pragma unroll
+        for (int q = 0; q < IT; ++q)
+#pragma unroll
+            for (int c = 0; c < NV; ++c) tree_xor(v[q][c], o);
+    TV* mine = ring_of(wib);
+    if (sl == 0) {
+#pragma unroll
+        for (int q = 0; q < IT; ++q)
+#pragma unroll
+            for (int c = 0; c < NV; ++c) mine[c * GI + q * IW + ir] = v[q][c];
+    }
+    __syncthreads();
+    uint32_t* last_flag = reinterpret_cast<uint32_t*>(smem + 64);  // warp 0's barrier block
+    const int tid = threadIdx.x;
+    const int64_t key = cg * cR;  // slot of the group's first entry
+    // Level 0: this CTA's entry, its warps' sums added in warp order.
+    if (wib == 0) {
+        for (int vi = lane; vi < VALS; vi += 32) {
+            TV x;
+            tree_zero(x);
+#pragma unroll
+            for (int ww = 0; ww < FORCE_WARPS; ++ww) tree_add(x, ring_of(ww)[vi]);
+            tree_store(f.scratch, (size_t)(key + crank) * VALS + vi, x);
+        }
+    }
+    // The entries meet in a tree, as the warps' sums do in warp mode, but
+    // each chunk is added by all the threads of its last CTA, each thread
+    // loading at most CTA_BATCH entries of one value in one batch: the
+    // radix is CTA_BATCH times the parts the CTA's threads split a value
+    // into.  Level L entry r sits in slot key + r * RADIX^L, and a chunk's
+    // sum takes its first entry's slot.
+    constexpr int RADIX = CTA_BATCH * PARTS;
+    TV* part = ring_of(1);
+    TV* fin = ring_of(2);
+    int64_t kk = cR, r = crank, stride = 1;
+    for (int level = 0;; ++level) {
+        // every store of this CTA's entry precedes thread 0's release
+        __syncthreads();
+        const int64_t chunk = r / RADIX, first = chunk * RADIX;
+        const int cs = static_cast<int>(kk - first < RADIX ? kk - first : RADIX);
+        if (tid == 0) {
+            uint32_t* cnt = f.counters + (size_t)level * f.counter_stride + key + chunk;
+            const uint32_t prev = atomic_add_acq_rel_gpu(cnt, 1u);
+            const bool last = prev == static_cast<uint32_t>(cs - 1);
+            if (last) *cnt = 0u;  // the whole chunk is in: ready for the next launch
+            *last_flag = last ? 1u : 0u;
+        }
+        __syncthreads();
+        if (*last_flag == 0u) return;  // the whole CTA: another one carries the chunk on
+        // (thread 0's acquire, passed on by the barrier, orders the loads below)
+        const size_t e0 = (size_t)(key + first * stride) * VALS;
+        const size_t es = (size_t)stride * VALS;
+        auto sum_entries = [&](int vi, int u0, int u1) {  // u1 - u0 <= CTA_BATCH
+            TV y[CTA_BATCH];
+#pragma unroll
+            for (int k = 0; k < CTA_BATCH; ++k)
+                if (u0 + k < u1) tree_load(f.scratch, e0 + (size_t)(u0 + k) * es + vi, y[k]);
+            TV x;
+            tree_zero(x);
+#pragma unroll
+            for (int k = 0; k < CTA_BATCH; ++k)
+                if (u0 + k < u1) tree_add(x, y[k]);
+            return x;
+        };
+        if (PARTS == 1) {
+            for (int vi = tid; vi < VALS; vi += NTH) fin[vi] = sum_entries(vi, 0, cs);
+        } else {
+            if (tid < PARTS * VALS) {
+                const int vi = tid % VALS, pp = tid / VALS;
+                part[pp * VALS + vi] = sum_entries(vi, cs * pp / PARTS, cs * (pp + 1) / PARTS);
+            }
+            __syncthreads();
+            for (int vi = tid; vi < VALS; vi += NTH) {
+                TV x;
+                tree_zero(x);
+                for (int pp = 0; pp < PARTS; ++pp) tree_add(x, part[pp * VALS + vi]);
+                fin[vi] = x;
+            }
+        }
+        __syncthreads();
+        r = chunk;
+        kk = (kk + RADIX - 1) / RADIX;
+        stride *= RADIX;
+        if (kk == 1) break;  // fin holds the group's sums
+        for (int vi = tid; vi < VALS; vi += NTH)
+            tree_store(f.scratch, (size_t)(key + r * stride) * VALS + vi, fin[vi]);
+    }
+    if (wib == 0 && sl == 0) {
+#pragma unroll
+        for (int q = 0; q < IT; ++q) {
+            const int64_t a = cgi.act_begin + q * IW + ir;
+            if (a < cgi.act_begin + cgi.act_count) {
+                double o[NV];
+#pragma unroll
+                for (int c = 0; c < NV; ++c) o[c] = tree_value(fin[c * GI + q * IW + ir]);
+                f.acc[3 * a + 0] = o[0];
+                f.acc[3 * a + 1] = o[1];
+                f.acc[3 * a + 2] = o[2];
+                f.jerk[3 * a + 0] = o[3];
+                f.jerk[3 * a + 1] = o[4];
+                f.jerk[3 * a + 2] = o[5];
+                f.pot[a] = o[6];
+                if constexpr (K::NV > 7) K::finish(f, is[q], a, o);
+            }
+        }
+    }
+}
+
+
 // S: lanes per i (the j split inside a warp).  Lane = ir + IW sl: i slot ir
 // of the warp's IW = 32 / S, j slice sl; the S slices of an i are summed with
 // shuffles before the split-group tree.
-template <class K, int IT, int S, class Plan>
+template <class K, int IT, int S, class Plan, bool CTA>
 __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
     force_kernel(const ForceParams f)
 {
@@ -1176,9 +1318,12 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
     // warp tree below, each a chain of global-memory round trips, with one.
     // It is used while it leaves each warp at most CTA_MAX_TILES tiles: past
     // that the latency it saves is small against the stream-K balance.
+    // (Only the CTA = true build carries it, the small-block launch variant:
+    // the code of its reduction, present in the large-block build, cost that
+    // build ~2 % through the register allocation of its tile loops.)
     bool cta = false;
     int64_t cg = 0, cR = 1, crank = 0;
-    if constexpr (Plan::CHUNKED) {
+    if constexpr (Plan::CHUNKED && CTA) {
         if (f.cta_mode && 4 * plan.G <= (int64_t)gridDim.x) {
             const int64_t rmax = (plan.NT + FORCE_WARPS - 1) / FORCE_WARPS;
             cR = gridDim.x / static_cast<uint32_t>(plan.G);  // G < gridDim.x / 4
@@ -1214,8 +1359,9 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
 
     typename K::I is[IT];
     typename K::Acc ac[IT];
-    int64_t used = 0;    // tiles this warp has consumed: ring slot used % STAGES
-    int64_t issued = 0;  // tiles this warp has staged
+    // (32-bit: a warp's tiles and a system's j tiles stay below 2^31)
+    uint32_t used = 0;    // tiles this warp has consumed: ring slot used % STAGES
+    uint32_t issued = 0;  // tiles this warp has staged
     bool loaded = false;   // is[] and ac[] set up for a group
     bool aborted = false;  // a tile wait ran out (CTA mode: the CTA still meets)
 
@@ -1270,11 +1416,11 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
     int64_t lg = g;
     GroupInfo lgi = gi;
     int64_t tl = t0;
-    int64_t lpos = tile_at(lgi, tl - lgi.tile0);  // j tile of the next load
+    int32_t lpos = static_cast<int32_t>(tile_at(lgi, tl - lgi.tile0));  // j tile of the next load
     auto issue_next = [&]() {
         if (tl >= lgi.tile0 + lgi.ntiles) {
             while (tl >= lgi.tile0 + lgi.ntiles) lgi = plan.group(++lg);
-            lpos = tile_at(lgi, tl - lgi.tile0);
+            lpos = static_cast<int32_t>(tile_at(lgi, tl - lgi.tile0));
         }
         const int s = static_cast<int>(issued % K::STAGES);
         // (self-test: with unfed_first_tile the warp's first tile is never
@@ -1291,10 +1437,10 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
 
     bool fresh = true;
     bool guard_any = false;  // some lane of this group has the hybrid guard on
-    int64_t cpos = 0;        // j tile of the tile being computed (rank in the walk)
+    int32_t cpos = 0;        // j tile of the tile being computed (rank in the walk)
 
     for (int64_t t = t0; t < t1; ++t) {
-        const int64_t k = used;
+        const uint32_t k = used;
         const int s = static_cast<int>(k % K::STAGES);
         const uint32_t parity = static_cast<uint32_t>((k / K::STAGES) & 1);
         while (t >= gi.tile0 + gi.ntiles) {
@@ -1303,7 +1449,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
         }
         if (fresh) {
             fresh = false;
-            cpos = tile_at(gi, t - gi.tile0);
+            cpos = static_cast<int32_t>(tile_at(gi, t - gi.tile0));
             load_group(gi);
             if constexpr (K::GUARDED) {
                 bool gq = false;
@@ -1318,7 +1464,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
             // Give up on this launch, but first let every bulk copy this warp
             // still has in flight (ring positions k .. issued - 1) land, each
             // wait bounded again, so no copy outlives the CTA.
-            for (int64_t kk = k; kk < issued; ++kk) {
+            for (uint32_t kk = k; kk < issued; ++kk) {
                 if (f.unfed_first_tile && kk == 0) continue;  // never issued
                 mbar_wait_bounded(&bars[kk % K::STAGES],
                                   static_cast<uint32_t>((kk / K::STAGES) & 1));
@@ -1461,138 +1607,15 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
     }
     }  // chunks
 
-    if (cta) {
-        // CTA mode: this warp's sums (zeros if it had no tile) into its own
-        // ring, which no copy uses any more; the four warps added in warp
-        // order as the CTA's entry; the last CTA of the group adds the
-        // group's R entries in CTA order.
-        constexpr int NV = K::NV;
-        using TV = typename K::TV;
-        constexpr int VALS = NV * GI;
-        constexpr int NTH = FORCE_WARPS * 32;
-        constexpr int PARTS = VALS >= NTH ? 1 : NTH / VALS;
-        static_assert(VALS * sizeof(TV) <= (size_t)K::STAGES * K::TILE_BYTES &&
-                          PARTS * VALS <= (VALS > NTH ? VALS : NTH),
-                      "a warp's ring holds the CTA-mode sums");
-        auto ring_of = [&](int ww) {
-            return reinterpret_cast<TV*>(smem + (size_t)ww * WarpSmem<K>::BYTES +
-                                         WarpSmem<K>::BAR_BYTES);
-        };
-        const GroupInfo cgi = plan.group(cg);
-        (void)aborted;
-        if (!loaded) load_group(cgi);
-        TV v[IT][NV];
-#pragma unroll
-        for (int q = 0; q < IT; ++q) K::values(ac[q], v[q]);
-#pragma unroll
-        for (int o = IW; o < 32; o <<= 1)
-#pragma unroll
-            for (int q = 0; q < IT; ++q)
-#pragma unroll
-                for (int c = 0; c < NV; ++c) tree_xor(v[q][c], o);
-        TV* mine = ring_of(wib);
-        if (sl == 0) {
-#pragma unroll
-            for (int q = 0; q < IT; ++q)
-#pragma unroll
-                for (int c = 0; c < NV; ++c) mine[c * GI + q * IW + ir] = v[q][c];
-        }
-        __syncthreads();
-        uint32_t* last_flag = reinterpret_cast<uint32_t*>(smem + 64);  // warp 0's barrier block
-        const int tid = threadIdx.x;
-        const int64_t key = cg * cR;  // slot of the group's first entry
-        // Level 0: this CTA's entry, its warps' sums added in warp order.
-        if (wib == 0) {
-            for (int vi = lane; vi < VALS; vi += 32) {
-                TV x;
-                tree_zero(x);
-#pragma unroll
-                for (int ww = 0; ww < FORCE_WARPS; ++ww) tree_add(x, ring_of(ww)[vi]);
-                tree_store(f.scratch, (size_t)(key + crank) * VALS + vi, x);
-            }
-        }
-        // The entries meet in a tree, as the warps' sums do in warp mode, but
-        // each chunk is added by all the threads of its last CTA, each thread
-        // loading at most CTA_BATCH entries of one value in one batch: the
-        // radix is CTA_BATCH times the parts the CTA's threads split a value
-        // into.  Level L entry r sits in slot key + r * RADIX^L, and a chunk's
-        // sum takes its first entry's slot.
-        constexpr int RADIX = CTA_BATCH * PARTS;
-        TV* part = ring_of(1);
-        TV* fin = ring_of(2);
-        int64_t kk = cR, r = crank, stride = 1;
-        for (int level = 0;; ++level) {
-            // every store of this CTA's entry precedes thread 0's release
-            __syncthreads();
-            const int64_t chunk = r / RADIX, first = chunk * RADIX;
-            const int cs = static_cast<int>(kk - first < RADIX ? kk - first : RADIX);
-            if (tid == 0) {
-                uint32_t* cnt = f.counters + (size_t)level * f.counter_stride + key + chunk;
-                const uint32_t prev = atomic_add_acq_rel_gpu(cnt, 1u);
-                const bool last = prev == static_cast<uint32_t>(cs - 1);
-                if (last) *cnt = 0u;  // the whole chunk is in: ready for the next launch
-                *last_flag = last ? 1u : 0u;
-            }
-            __syncthreads();
-            if (*last_flag == 0u) return;  // the whole CTA: another one carries the chunk on
-            // (thread 0's acquire, passed on by the barrier, orders the loads below)
-            const size_t e0 = (size_t)(key + first * stride) * VALS;
-            const size_t es = (size_t)stride * VALS;
-            auto sum_entries = [&](int vi, int u0, int u1) {  // u1 - u0 <= CTA_BATCH
-                TV y[CTA_BATCH];
-#pragma unroll
-                for (int k = 0; k < CTA_BATCH; ++k)
-                    if (u0 + k < u1) tree_load(f.scratch, e0 + (size_t)(u0 + k) * es + vi, y[k]);
-                TV x;
-                tree_zero(x);
-#pragma unroll
-                for (int k = 0; k < CTA_BATCH; ++k)
-                    if (u0 + k < u1) tree_add(x, y[k]);
-                return x;
-            };
-            if (PARTS == 1) {
-                for (int vi = tid; vi < VALS; vi += NTH) fin[vi] = sum_entries(vi, 0, cs);
-            } else {
-                if (tid < PARTS * VALS) {
-                    const int vi = tid % VALS, pp = tid / VALS;
-                    part[pp * VALS + vi] = sum_entries(vi, cs * pp / PARTS, cs * (pp + 1) / PARTS);
-                }
-                __syncthreads();
-                for (int vi = tid; vi < VALS; vi += NTH) {
-                    TV x;
-                    tree_zero(x);
-                    for (int pp = 0; pp < PARTS; ++pp) tree_add(x, part[pp * VALS + vi]);
-                    fin[vi] = x;
-                }
-            }
-            __syncthreads();
-            r = chunk;
-            kk = (kk + RADIX - 1) / RADIX;
-            stride *= RADIX;
-            if (kk == 1) break;  // fin holds the group's sums
-            for (int vi = tid; vi < VALS; vi += NTH)
-                tree_store(f.scratch, (size_t)(key + r * stride) * VALS + vi, fin[vi]);
-        }
-        if (wib == 0 && sl == 0) {
-#pragma unroll
-            for (int q = 0; q < IT; ++q) {
-                const int64_t a = cgi.act_begin + q * IW + ir;
-                if (a < cgi.act_begin + cgi.act_count) {
-                    double o[NV];
-#pragma unroll
-                    for (int c = 0; c < NV; ++c) o[c] = tree_value(fin[c * GI + q * IW + ir]);
-                    f.acc[3 * a + 0] = o[0];
-                    f.acc[3 * a + 1] = o[1];
-                    f.acc[3 * a + 2] = o[2];
-                    f.jerk[3 * a + 0] = o[3];
-                    f.jerk[3 * a + 1] = o[4];
-                    f.jerk[3 * a + 2] = o[5];
-                    f.pot[a] = o[6];
-                    if constexpr (K::NV > 7) K::finish(f, is[q], a, o);
-                }
-            }
+    if constexpr (CTA) {
+        if (cta) {
+            const GroupInfo cgi = plan.group(cg);
+            if (!loaded) load_group(cgi);
+            cta_finish<K, IT, S>(f, smem, is, ac, cgi, cg, cR, crank);
         }
     }
+    (void)aborted;
+    (void)loaded;
 }
 
 // ---------------------------------------------------------------------------
@@ -1600,43 +1623,48 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
 // ---------------------------------------------------------------------------
 namespace {
 
+// The kernel of one launch: ensembles use the cluster plan; one system the
+// uniform plan, in its small-block build (CTA mode) when asked for and the
+// i-tile is one per lane (the small-block shapes), else its plain build.
 template <class K, int IT, int S>
-const void* kfn(bool ens)
+const void* kfn(bool ens, bool cta)
 {
-    return ens ? reinterpret_cast<const void*>(&force_kernel<K, IT, S, ClusterPlan>)
-               : reinterpret_cast<const void*>(&force_kernel<K, IT, S, UniformPlan>);
+    if (ens) return reinterpret_cast<const void*>(&force_kernel<K, IT, S, ClusterPlan, false>);
+    if constexpr (IT == 1)
+        if (cta) return reinterpret_cast<const void*>(&force_kernel<K, IT, S, UniformPlan, true>);
+    return reinterpret_cast<const void*>(&force_kernel<K, IT, S, UniformPlan, false>);
 }
 
 // One i per lane with any j split; two i per lane without one.
 template <class K1, class K2>
-const void* kfn_split(int it, int split, bool ens)
+const void* kfn_split(int it, int split, bool ens, bool cta)
 {
     if (it == 1) {
         switch (split) {
-        case 1: return kfn<K1, 1, 1>(ens);
-        case 2: return kfn<K1, 1, 2>(ens);
-        case 4: return kfn<K1, 1, 4>(ens);
-        case 8: return kfn<K1, 1, 8>(ens);
+        case 1: return kfn<K1, 1, 1>(ens, cta);
+        case 2: return kfn<K1, 1, 2>(ens, cta);
+        case 4: return kfn<K1, 1, 4>(ens, cta);
+        case 8: return kfn<K1, 1, 8>(ens, cta);
         }
         return nullptr;
     }
     if constexpr (!std::is_same<K2, void>::value)
-        if (it == 2 && split == 1) return kfn<K2, 2, 1>(ens);
+        if (it == 2 && split == 1) return kfn<K2, 2, 1>(ens, cta);
     return nullptr;
 }
 
-const void* kernel_ptr(Prec p, int it, int split, bool ens = false)
+const void* kernel_ptr(Prec p, int it, int split, bool ens = false, bool cta = false)
 {
     switch (p) {
-    case Prec::FP64: return kfn_split<PolicyFP64<1>, void>(it, split, ens);
-    case Prec::MIXED: return kfn_split<PolicyMixed<1>, PolicyMixed<2>>(it, split, ens);
+    case Prec::FP64: return kfn_split<PolicyFP64<1>, void>(it, split, ens, cta);
+    case Prec::MIXED: return kfn_split<PolicyMixed<1>, PolicyMixed<2>>(it, split, ens, cta);
     case Prec::MIXED_SPJ:
-        return kfn_split<PolicyMixed<1, true>, PolicyMixed<2, true>>(it, split, ens);
-    case Prec::DS: return kfn_split<PolicyDS<1>, void>(it, split, ens);
-    case Prec::HYBRID: return kfn_split<PolicyHybrid<1>, PolicyHybrid<2>>(it, split, ens);
+        return kfn_split<PolicyMixed<1, true>, PolicyMixed<2, true>>(it, split, ens, cta);
+    case Prec::DS: return kfn_split<PolicyDS<1>, void>(it, split, ens, cta);
+    case Prec::HYBRID: return kfn_split<PolicyHybrid<1>, PolicyHybrid<2>>(it, split, ens, cta);
     case Prec::HYBRID_SPJ:
-        return kfn_split<PolicyHybrid<1, true>, PolicyHybrid<2, true>>(it, split, ens);
-    case Prec::FP64_H6: return kfn_split<PolicyFP64Snap<1>, void>(it, split, ens);
+        return kfn_split<PolicyHybrid<1, true>, PolicyHybrid<2, true>>(it, split, ens, cta);
+    case Prec::FP64_H6: return kfn_split<PolicyFP64Snap<1>, void>(it, split, ens, cta);
     }
     return nullptr;
 }
@@ -1689,8 +1717,8 @@ bool force_variant_exists(Prec p, int it, int split) { return kernel_ptr(p, it, 
 
 cudaError_t force_setup(Prec p, int it, int split)
 {
-    for (int e = 0; e < 2; ++e) {
-        const void* fn = kernel_ptr(p, it, split, e == 1);
+    for (int e = 0; e < 3; ++e) {  // plain, ensemble, small-block builds
+        const void* fn = kernel_ptr(p, it, split, e == 1, e == 2);
         if (!fn) return cudaErrorInvalidValue;
         const cudaError_t r = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    static_cast<int>(force_smem_bytes(p)));
@@ -1730,7 +1758,8 @@ int64_t force_counter_entries(int64_t n_act_max, int warps)
 
 cudaError_t force_launch(const ForceArgs& a, cudaStream_t s)
 {
-    const void* fn = kernel_ptr(a.prec, a.it, a.split, a.plan.grp_tile0 != nullptr);
+    const bool ens = a.plan.grp_tile0 != nullptr;
+    const void* fn = kernel_ptr(a.prec, a.it, a.split, ens, a.cta_mode && !ens);
     if (!fn || a.grid <= 0) return cudaErrorInvalidValue;
     ForceParams f;
     f.jl0 = a.jl.arr[0];
