@@ -123,14 +123,15 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_metric(prec, key="traffic_bytes_per_launch", shape=None):
+def profiled_metric(prec, key="traffic_bytes_per_launch", shape=None, n=16384):
     """A figure of the force launch at n_act = N from the committed ncu summary
-    (DRAM bytes per launch, thread instructions per interaction), or None when
-    the kernel sources changed since it was captured or it was captured with
-    another kernel shape (i per thread, j split) than `shape`; the CTAs per SM
-    only change how far the j range splits over warps."""
+    of the N = n workload (DRAM bytes per launch, thread instructions per
+    interaction), or None when the kernel sources changed since it was
+    captured or it was captured with another kernel shape (i per thread, j
+    split) than `shape`; the CTAs per SM only change how far the j range
+    splits over warps."""
     import re
-    path = os.path.join(ROOT, "profiles", f"force_{prec}_n16384.md")
+    path = os.path.join(ROOT, "profiles", f"force_{prec}_n{n}.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
@@ -778,6 +779,14 @@ def extra_measurements(nbody, torch, dev, stream, world, peak32, refs):
                    "frac": ach / peak32, "launch_ms": t * 1e3,
                    "interactions_per_s": n * n / t, "autotuned_launch": tun,
                    "algorithmic_bytes_per_launch": algorithmic_bytes(prec, n, n)}
+            # the committed ncu summary of this launch, when its kernel source
+            # and shape are this run's (else null)
+            shape = (tun["large_i_per_thread"], tun["large_j_split"])
+            row["traffic"] = profiled_metric(prec, shape=shape, n=n)
+            row["thread_instructions_per_interaction"] = profiled_metric(
+                prec, "thread_instructions_per_interaction", shape, n=n)
+            if row["traffic"] is not None:
+                row["traffic_source"] = f"profiles/force_{prec}_n{n}.md"
             if t_guard is not None:
                 row["launch_ms_right_after_load"] = t_guard * 1e3
                 row["right_after_load_note"] = (
