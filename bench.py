@@ -105,14 +105,15 @@ def parse_args():
 
 def kernel_source_hash():
     """sha256 (first 16 hex) of what the force kernel is built from:
-    csrc/force.cu, csrc/nb_device.cuh and csrc/nb_launch.h with comments and
-    whitespace stripped (so that a comment edit does not orphan the ncu
-    summaries taken of the same code), plus force.cu's compiler flags."""
+    csrc/force_kernel.cuh, force.cu, force_cta.cu, nb_device.cuh and
+    nb_launch.h with comments and whitespace stripped (so that a comment edit
+    does not orphan the ncu summaries taken of the same code), plus the
+    force translation units' compiler flags."""
     import hashlib
     import re
     from paper_1104_2700_gb300 import build as nb_build
     h = hashlib.sha256()
-    for f in ("force.cu", "nb_device.cuh", "nb_launch.h"):
+    for f in ("force_kernel.cuh", "force.cu", "force_cta.cu", "nb_device.cuh", "nb_launch.h"):
         with open(os.path.join(ROOT, "paper_1104_2700_gb300", "csrc", f)) as fh:
             src = fh.read()
         src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)

@@ -26,8 +26,9 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2",
 # in them relies on gradual underflow.
 PER_FILE = {
     "force.cu": ["-ftz=true"],
+    "force_cta.cu": ["-ftz=true"],
 }
-SOURCES = ["capi.cu", "force.cu", "hermite.cu", "static_force.cu", "peak.cu"]
+SOURCES = ["capi.cu", "force.cu", "force_cta.cu", "hermite.cu", "static_force.cu", "peak.cu"]
 
 
 def nvcc() -> str:
