@@ -129,14 +129,20 @@ void nb_config_init(nb_config* cfg);
 
 /* Launch shapes of the force kernel (i-tile per lane, j-split inside a warp
  * and over warps): blocks of fewer than nact_split active particles use the
- * "small" shape, others the "large" one.  i_per_thread is the i-tile per
- * lane; j_split the lanes that share one i, each taking every j_split-th j
- * of a tile (an i-group is 32 * i_per_thread / j_split particles); ctas_per_sm
- * sets the persistent grid, which fixes how far each i-group's j range is
- * split across warps.  An ensemble context uses one i-tile and one j split
- * for both shapes (its force plan is cut once per block).  The *_us fields
- * give the force time the autotuner measured for the chosen shapes on its
- * probe blocks. */
+ * "small" shape, others the "large" one.  When tiny_split > 0, a force call
+ * whose block size the host knows (nb_force with n_act >= 0) on fewer than
+ * tiny_split particles uses a third, "tiny" shape; a block step, whose size
+ * is on the device, launches the small and the large shape as two parallel
+ * branches (one returns at once) and never the tiny one, since a third
+ * branch costs a block step more than the shape saves.  i_per_thread is the
+ * i-tile per lane; j_split the lanes that share one i, each taking every
+ * j_split-th j of a tile (an i-group is 32 * i_per_thread / j_split
+ * particles); ctas_per_sm sets the persistent grid, which fixes how far each
+ * i-group's j range is split across warps.  An ensemble context uses one
+ * i-tile and one j split for both shapes (its force plan is cut once per
+ * block) and no tiny shape.  The *_us fields give the force time the
+ * autotuner measured for the chosen shapes on their probe blocks (tiny_us 0
+ * without a tiny shape). */
 typedef struct nb_tuning {
     int32_t small_i_per_thread;
     int32_t small_ctas_per_sm;
@@ -147,20 +153,38 @@ typedef struct nb_tuning {
     int32_t large_j_split;
     double small_us;
     double large_us;
+    int32_t tiny_split;   /* 0: no tiny shape */
+    int32_t tiny_i_per_thread;
+    int32_t tiny_ctas_per_sm;
+    int32_t tiny_j_split;
+    double tiny_us;
 } nb_tuning;
 
 /* Autotuner: time every candidate launch shape of the force kernel on the
- * loaded system (probe blocks of 32, 256, 2048 and min(n, 65536) particles
- * spread evenly over the context's stored order, nb_spatial_order, like the
- * scattered members of a block step; for the hybrid precision with the
- * integration guard idle, as in a steady integration) and keep the fastest for each bucket, with the bucket
- * boundary nact_split at 1024 (probes 32 and 256 small) or 4096 (2048 small
- * too), whichever gives the least total.  Predicts all particles to the
- * time of particle 0 first, so call nb_predict again before nb_force.  *out
- * (may be NULL)
- * receives the choice.  Blocks.  Errors: NB_ESTATE (nothing loaded),
- * NB_ECUDA. */
+ * loaded system (probe blocks of 32, 96, 256, 2048 and min(n, 65536)
+ * particles spread evenly over the context's stored order, nb_spatial_order,
+ * like the scattered members of a block step; for the hybrid precision with
+ * the integration guard idle, as in a steady integration) and keep the
+ * fastest for each bucket, with the bucket boundary nact_split at 1024
+ * (probes up to 256 small) or 4096 (2048 small too), whichever gives the
+ * least total.  A single system then may take a tiny shape (tiny_split 64:
+ * probe 32; 160: probes 32 and 96), kept only when it beats the small shape
+ * on those probes by more than 0.5 us.  Predicts all particles to the time
+ * of particle 0 first, so call nb_predict again before nb_force.  *out (may
+ * be NULL) receives the choice.  Blocks.  Errors: NB_ESTATE (nothing
+ * loaded), NB_ECUDA. */
 nb_status nb_autotune(nb_ctx* ctx, nb_tuning* out);
+
+/* Set the force launch shapes by hand, e.g. ones an earlier nb_autotune
+ * returned for the same workload (its *_us fields are ignored).  Each shape
+ * used (the tiny one only when tiny_split > 0) must name a built kernel
+ * (i_per_thread 1 or 2, j_split 1, 2, 4 or 8; 2 i per thread only with j
+ * split 1) and 1 to its occupancy of CTAs per SM; 0 <= tiny_split <
+ * nact_split.  An ensemble context takes equal small and large i-tiles and
+ * j splits and tiny_split 0.  The shapes hold until the next nb_autotune (a
+ * context created with autotune = 1 retunes on every load).  Errors:
+ * NB_EINVAL (shape or boundary out of range; nothing changes), NB_ECUDA. */
+nb_status nb_set_tuning(nb_ctx* ctx, const nb_tuning* tuning);
 
 /* Self-test of failure detection (no counterpart in the paper): run one
  * force launch in which no warp stages its first j tile, so that tile's

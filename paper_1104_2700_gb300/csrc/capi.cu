@@ -30,13 +30,17 @@ struct nb_ctx {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int num_sms = 0;
     // Force launch variants of the context precision: [0] for blocks with
-    // n_act < nact_split, [1] for larger ones (i per thread, persistent CTAs).
+    // n_act < nact_split, [1] for larger ones, [2] for blocks of fewer than
+    // tiny_split particles whose size the host knows (none while tiny_split
+    // is 0).  A device-sized block never takes [2]: a third parallel branch
+    // costs each block step more than the shape saves.
     struct Variant {
         int it = 1;
         int grid = 0;
         int split = 1;  // lanes per i (j split inside a warp)
-    } var[2];
+    } var[3];
     int32_t nact_split = 1024;
+    int32_t tiny_split = 0;
     int grid64 = 0;      // persistent CTAs of the FP64 energy pass (1 i per thread)
     size_t scratch_cap = 0;    // doubles allocated for split-group partials
     int64_t counter_cap = 0;   // counter words allocated
@@ -186,21 +190,19 @@ nb_status alloc_layout(nb_ctx* c, Prec p, nb::JLayout& jl, int64_t n_pad)
 }
 
 // Scratch for the split-group partials and reduction counters, enough for
-// the launch variants with the given grids (and the FP64 energy pass) on up
+// the three launch variants (and the FP64 energy pass) on up
 // to cap particles in cap_k systems.  Grows only; drops the step graph when
 // the buffers move.
-nb_status ensure_force_scratch(nb_ctx* c, int grid0, int grid1)
+nb_status ensure_force_scratch(nb_ctx* c)
 {
     const int64_t n = c->cap, k = c->cap_k;
     const int64_t groups_bound = n + 32 * k;  // i-groups never mix systems
     size_t need = nb::force_scratch_doubles(1, groups_bound, c->grid64 * nb::FORCE_WARPS);
     int max_grid = c->grid64;
-    const int grids[2] = {grid0, grid1};
-    for (int v = 0; v < 2; ++v) {
-        const int it = c->var[v].it;
-        need = std::max(need, nb::force_scratch_doubles(it, groups_bound + 32 * it * k,
-                                                        grids[v] * nb::FORCE_WARPS));
-        max_grid = std::max(max_grid, grids[v]);
+    for (const auto& var : c->var) {
+        need = std::max(need, nb::force_scratch_doubles(var.it, groups_bound + 32 * var.it * k,
+                                                        var.grid * nb::FORCE_WARPS));
+        max_grid = std::max(max_grid, var.grid);
     }
     const int64_t stride = nb::force_counter_stride(groups_bound, max_grid * nb::FORCE_WARPS);
     const int64_t words = nb::force_counter_entries(groups_bound, max_grid * nb::FORCE_WARPS);
@@ -304,7 +306,7 @@ nb_status ensure_capacity(nb_ctx* c, int64_t n, int64_t n_pad, int64_t k)
     c->cap_pad = n_pad;
     c->cap_k = k;
     c->cap = n;
-    s = ensure_force_scratch(c, c->var[0].grid, c->var[1].grid);
+    s = ensure_force_scratch(c);
     if (s != NB_OK) return s;
     c->n = n;
     c->n_pad = n_pad;
@@ -371,14 +373,25 @@ nb_status run_force(nb_ctx* c, Prec p, const nb::JLayout& jl, const int32_t* idx
         NB_CK(c, nb::force_launch(f, c->stream));
         return NB_OK;
     }
-    // With the block size on the device both variants are launched, the
-    // small-block one on the aux stream; exactly one of them does any work,
-    // and neither touches memory the other uses before it has read n_act.
-    const bool fork = n_act_host < 0;
-    if (fork) {
-        NB_CK(c, cudaEventRecord(c->ev_fork, c->stream));
-        NB_CK(c, cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
+    // With the block size known here, one launch of the variant whose
+    // window holds it.
+    if (n_act_host >= 0) {
+        const int v = n_act_host < c->tiny_split ? 2 : n_act_host < c->nact_split ? 0 : 1;
+        f.it = c->var[v].it;
+        f.split = c->var[v].split;
+        f.grid = c->var[v].grid;
+        f.cta_mode = !c->ens && v != 1;  // small blocks: CTA-level sums
+        f.nact_lo = 0;
+        f.nact_hi = 0x7fffffff;
+        NB_CK(c, nb::force_launch(f, c->stream));
+        return NB_OK;
     }
+    // With the block size on the device both the small and the large variant
+    // are launched, the small one on the aux stream; exactly one of them does
+    // any work, and neither touches memory the other uses before it has read
+    // n_act.
+    NB_CK(c, cudaEventRecord(c->ev_fork, c->stream));
+    NB_CK(c, cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
     for (int v = 0; v < 2; ++v) {
         f.it = c->var[v].it;
         f.split = c->var[v].split;
@@ -386,13 +399,10 @@ nb_status run_force(nb_ctx* c, Prec p, const nb::JLayout& jl, const int32_t* idx
         f.cta_mode = !c->ens && v == 0;  // small blocks: CTA-level sums
         f.nact_lo = v == 0 ? 0 : c->nact_split;
         f.nact_hi = v == 0 ? c->nact_split : 0x7fffffff;
-        if (n_act_host >= 0 && (n_act_host < f.nact_lo || n_act_host >= f.nact_hi)) continue;
-        NB_CK(c, nb::force_launch(f, (fork && v == 0) ? c->aux : c->stream));
+        NB_CK(c, nb::force_launch(f, v == 0 ? c->aux : c->stream));
     }
-    if (fork) {
-        NB_CK(c, cudaEventRecord(c->ev_join, c->aux));
-        NB_CK(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0));
-    }
+    NB_CK(c, cudaEventRecord(c->ev_join, c->aux));
+    NB_CK(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0));
     return NB_OK;
 }
 
@@ -836,6 +846,7 @@ nb_status nb_create(const nb_config* cfg, nb_ctx** out)
         c->var[v].split = split;
         c->var[v].grid = per_sm * c->num_sms;
     }
+    c->var[2] = c->var[0];  // no tiny variant until the autotuner sets one
     if (nb::force_setup(Prec::FP64, 1, 1) != cudaSuccess) return bail(NB_ECUDA);
     const int per_sm64 = nb::force_ctas_per_sm(Prec::FP64, 1, 1);
     if (per_sm64 < 1) return bail(NB_ECUDA);
@@ -1324,11 +1335,14 @@ nb_status nb_set_ensemble(nb_ctx* c, int32_t k, const int64_t* offsets, const do
     c->j_parts = 1;
     nb_status s = ensure_capacity(c, n, n_pad, k);
     if (s != NB_OK) return s;
-    // the ensemble plan cuts i-groups of one width for both variants
+    // the ensemble plan cuts i-groups of one width for both variants, and
+    // there is no tiny one
+    c->tiny_split = 0;
+    c->var[2] = c->var[0];
     if (c->var[1].it != c->var[0].it || c->var[1].split != c->var[0].split) {
         c->var[1].it = c->var[0].it;
         c->var[1].split = c->var[0].split;
-        if ((s = ensure_force_scratch(c, c->var[0].grid, c->var[1].grid)) != NB_OK) return s;
+        if ((s = ensure_force_scratch(c)) != NB_OK) return s;
     }
     c->eps = 0.0;  // per system: cl.eps2
     c->eta = eta;
@@ -1424,18 +1438,21 @@ nb_status nb_autotune(nb_ctx* c, nb_tuning* out)
     nb_status s = enter(c, true);
     if (s != NB_OK) return s;
     const int64_t n = c->n;
-    const int32_t probes[4] = {static_cast<int32_t>(std::min<int64_t>(32, n)),
-                               static_cast<int32_t>(std::min<int64_t>(256, n)),
-                               static_cast<int32_t>(std::min<int64_t>(2048, n)),
-                               static_cast<int32_t>(std::min<int64_t>(65536, n))};
+    // probes 0-3 are timed with the small-block build, 3-4 with the large one
+    constexpr int NQ = 5;
+    const int32_t probes[NQ] = {static_cast<int32_t>(std::min<int64_t>(32, n)),
+                                static_cast<int32_t>(std::min<int64_t>(96, n)),
+                                static_cast<int32_t>(std::min<int64_t>(256, n)),
+                                static_cast<int32_t>(std::min<int64_t>(2048, n)),
+                                static_cast<int32_t>(std::min<int64_t>(65536, n))};
     // candidates: (i per thread, j split) x CTAs per SM; two i per thread
     // only for MIXED and HYBRID single systems, and only without a j split
     std::vector<std::pair<int, int>> shapes = {{1, 1}, {1, 2}, {1, 4}, {1, 8}};
     if ((nb::is_mixed(c->prec) || nb::is_hybrid(c->prec)) && !c->ens) shapes.push_back({2, 1});
     struct Cand {
         int it, split, cps;
-        double us[4];   // with the small-block build (probes 0-2)
-        double usl[4];  // with the large-block build (probes 2-3)
+        double us[NQ];   // with the small-block build (probes 0-3)
+        double usl[NQ];  // with the large-block build (probes 3-4)
     };
     std::vector<Cand> cands;
     int max_grid = 0;
@@ -1445,18 +1462,19 @@ nb_status nb_autotune(nb_ctx* c, nb_tuning* out)
         const int occ = nb::force_ctas_per_sm(c->prec, sh.first, sh.second);
         for (int cps : {1, 2, 3, 4, 5, 6, 8})
             if (cps <= occ) {
-                cands.push_back({sh.first, sh.second, cps, {0, 0, 0, 0}, {0, 0, 0, 0}});
+                cands.push_back({sh.first, sh.second, cps, {}, {}});
                 max_grid = std::max(max_grid, cps * c->num_sms);
             }
     }
     if (cands.empty()) return fail(c, NB_ECUDA, "no force launch shape fits on this device");
     // scratch for the largest candidate grid with either i per thread
-    const nb_ctx::Variant keep0 = c->var[0], keep1 = c->var[1];
-    c->var[0] = {1, max_grid};
+    const nb_ctx::Variant keep0 = c->var[0], keep1 = c->var[1], keep2 = c->var[2];
+    c->var[0] = c->var[2] = {1, max_grid};
     c->var[1] = {shapes.back().first, max_grid};
-    s = ensure_force_scratch(c, max_grid, max_grid);
+    s = ensure_force_scratch(c);
     c->var[0] = keep0;
     c->var[1] = keep1;
+    c->var[2] = keep2;
     if (s != NB_OK) return s;
     double* ht = reinterpret_cast<double*>(c->pinned + 48);
     NB_CK(c, cudaMemcpyAsync(ht, c->st.t, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -1480,7 +1498,7 @@ nb_status nb_autotune(nb_ctx* c, nb_tuning* out)
     NB_CK(c, cudaEventCreate(&e0));
     NB_CK(c, cudaEventCreate(&e1));
     nb_status st = NB_OK;
-    for (int q = 0; q < 4 && st == NB_OK; ++q) {
+    for (int q = 0; q < NQ && st == NB_OK; ++q) {
         // a probe block: particles spread evenly over the stored order, like
         // the scattered members of a real block step
         if (cudaSuccess != nb::strided_list_launch(c->idx_user, probes[q], n, c->n_act_user,
@@ -1495,11 +1513,11 @@ nb_status nb_autotune(nb_ctx* c, nb_tuning* out)
             f.it = cd.it;
             f.split = cd.split;
             f.grid = cd.cps * c->num_sms;
-            // the small bucket's probes (0-2) with the build its variant runs
-            // (CTA-level sums), the large bucket's (2-3) with the plain one
+            // the small buckets' probes (0-3) with the build their variants
+            // run (CTA-level sums), the large bucket's (3-4) with the plain one
             for (int build = 0; build < 2 && st == NB_OK; ++build) {
                 const bool small = build == 0;
-                if ((small && q > 2) || (!small && q < 2)) continue;
+                if ((small && q > 3) || (!small && q < 3)) continue;
                 f.cta_mode = small && !c->ens;
                 const int reps = 3;
                 cudaError_t e = nb::force_launch(f, c->stream);  // warm-up
@@ -1522,13 +1540,20 @@ nb_status nb_autotune(nb_ctx* c, nb_tuning* out)
     if (st != NB_OK) return st;
     if ((s = check_status(c)) != NB_OK) return s;
     // Best shape per bucket; ties go to the smaller grid (listed first).  The
-    // small bucket holds the probes below the split (two or three of them:
+    // small bucket holds the probes below the split (three or four of them:
     // nact_split 1024 or 4096), the large one the rest.  An ensemble's plan
     // is cut once per block for both variants, so there the two share the
-    // (i per thread, j split) with the least total time.
+    // (i per thread, j split) with the least total time.  A single system
+    // then may take a tiny shape for its first one or two probes, used only
+    // by force calls whose block size the host knows (a device-sized block
+    // step keeps two launch branches); it must beat the small shape there by
+    // more than TINY_MARGIN_US, well above the timing noise.
+    constexpr double TINY_MARGIN_US = 0.5;
+    // lo == 0 or hi < NQ: a small or tiny bucket, timed with the small build
     auto bucket_us = [](const Cand& cd, int lo, int hi) {
+        const bool small = lo == 0 || hi < NQ;
         double t = 0.0;
-        for (int q = lo; q < hi; ++q) t += lo == 0 ? cd.us[q] : cd.usl[q];
+        for (int q = lo; q < hi; ++q) t += small ? cd.us[q] : cd.usl[q];
         return t;
     };
     auto best_of = [&](int lo, int hi, int it, int split) {
@@ -1539,31 +1564,43 @@ nb_status nb_autotune(nb_ctx* c, nb_tuning* out)
         }
         return bc;
     };
-    const Cand* best[2] = {nullptr, nullptr};
-    int split_probe = 2;
+    const Cand* best[3] = {nullptr, nullptr, nullptr};
+    int split_probe = 3, tiny_probe = 0;
     double tbest = -1.0;
-    for (int sp : {2, 3}) {  // probes [0, sp) are "small"
-        const Cand* b[2] = {best_of(0, sp, 0, 0), best_of(sp, 4, 0, 0)};
+    for (int sp : {3, 4}) {  // probes [0, sp) are small
+        const Cand* b[2] = {best_of(0, sp, 0, 0), best_of(sp, NQ, 0, 0)};
         if (c->ens) {
             b[0] = b[1] = nullptr;
             double tsh = -1.0;
             for (const auto& sh : shapes) {
                 const Cand* b0 = best_of(0, sp, sh.first, sh.second);
-                const Cand* b1 = best_of(sp, 4, sh.first, sh.second);
+                const Cand* b1 = best_of(sp, NQ, sh.first, sh.second);
                 if (!b0 || !b1) continue;
-                const double tot = bucket_us(*b0, 0, sp) + bucket_us(*b1, sp, 4);
+                const double tot = bucket_us(*b0, 0, sp) + bucket_us(*b1, sp, NQ);
                 if (tsh < 0.0 || tot < tsh) b[0] = b0, b[1] = b1, tsh = tot;
             }
         }
-        const double tot = bucket_us(*b[0], 0, sp) + bucket_us(*b[1], sp, 4);
+        const double tot = bucket_us(*b[0], 0, sp) + bucket_us(*b[1], sp, NQ);
         if (tbest < 0.0 || tot < tbest) best[0] = b[0], best[1] = b[1], split_probe = sp, tbest = tot;
+    }
+    if (!c->ens) {
+        double gain = TINY_MARGIN_US;
+        for (int tp : {1, 2}) {  // probes [0, tp) are tiny
+            const Cand* bt = best_of(0, tp, 0, 0);
+            const double g = bucket_us(*best[0], 0, tp) - bucket_us(*bt, 0, tp);
+            if (g > gain) best[2] = bt, tiny_probe = tp, gain = g;
+        }
     }
     c->var[0] = {best[0]->it, best[0]->cps * c->num_sms, best[0]->split};
     c->var[1] = {best[1]->it, best[1]->cps * c->num_sms, best[1]->split};
-    c->nact_split = split_probe == 2 ? 1024 : 4096;
+    c->var[2] = best[2] ? nb_ctx::Variant{best[2]->it, best[2]->cps * c->num_sms, best[2]->split}
+                        : c->var[0];
+    c->nact_split = split_probe == 3 ? 1024 : 4096;
+    c->tiny_split = tiny_probe == 0 ? 0 : tiny_probe == 1 ? 64 : 160;
     drop_graph(c);
     c->last_force_n_act = -1;
     if (out) {
+        *out = nb_tuning{};
         out->small_i_per_thread = best[0]->it;
         out->small_ctas_per_sm = best[0]->cps;
         out->large_i_per_thread = best[1]->it;
@@ -1572,8 +1609,56 @@ nb_status nb_autotune(nb_ctx* c, nb_tuning* out)
         out->small_j_split = best[0]->split;
         out->large_j_split = best[1]->split;
         out->small_us = bucket_us(*best[0], 0, split_probe);
-        out->large_us = bucket_us(*best[1], split_probe, 4);
+        out->large_us = bucket_us(*best[1], split_probe, NQ);
+        if (best[2]) {
+            out->tiny_split = c->tiny_split;
+            out->tiny_i_per_thread = best[2]->it;
+            out->tiny_ctas_per_sm = best[2]->cps;
+            out->tiny_j_split = best[2]->split;
+            out->tiny_us = bucket_us(*best[2], 0, tiny_probe);
+        }
     }
+    return NB_OK;
+}
+
+nb_status nb_set_tuning(nb_ctx* c, const nb_tuning* t)
+{
+    nb_status s = enter(c, false);
+    if (s != NB_OK) return s;
+    if (!t) return fail(c, NB_EINVAL, "no tuning given");
+    struct Shape {
+        const char* name;
+        int it, split, cps;
+    };
+    const Shape sh[3] = {{"small", t->small_i_per_thread, t->small_j_split, t->small_ctas_per_sm},
+                         {"large", t->large_i_per_thread, t->large_j_split, t->large_ctas_per_sm},
+                         {"tiny", t->tiny_i_per_thread, t->tiny_j_split, t->tiny_ctas_per_sm}};
+    if (t->nact_split < 1 || t->tiny_split < 0 || t->tiny_split >= t->nact_split)
+        return fail(c, NB_EINVAL, "block-size boundaries tiny %d, small %d", t->tiny_split,
+                    t->nact_split);
+    if (c->ens && (t->tiny_split != 0 || sh[0].it != sh[1].it || sh[0].split != sh[1].split))
+        return fail(c, NB_EINVAL, "an ensemble takes one i-tile and j split and no tiny shape");
+    for (int v = 0; v < 3; ++v) {
+        if (v == 2 && t->tiny_split == 0) continue;
+        const Shape& q = sh[v];
+        if (!nb::force_variant_exists(c->prec, q.it, q.split))
+            return fail(c, NB_EINVAL, "%s shape: no kernel with %d i per thread, j split %d",
+                        q.name, q.it, q.split);
+        if (nb::force_setup(c->prec, q.it, q.split) != cudaSuccess)
+            return fail(c, NB_ECUDA, "kernel attributes");
+        const int occ = nb::force_ctas_per_sm(c->prec, q.it, q.split);
+        if (q.cps < 1 || q.cps > occ)
+            return fail(c, NB_EINVAL, "%s shape: %d CTAs per SM (1 to %d fit)", q.name, q.cps, occ);
+    }
+    for (int v = 0; v < 3; ++v) {
+        const Shape& q = sh[v == 2 && t->tiny_split == 0 ? 0 : v];
+        c->var[v] = {q.it, q.cps * c->num_sms, q.split};
+    }
+    c->nact_split = t->nact_split;
+    c->tiny_split = t->tiny_split;
+    if ((s = ensure_force_scratch(c)) != NB_OK) return s;
+    drop_graph(c);
+    c->last_force_n_act = -1;
     return NB_OK;
 }
 

@@ -53,6 +53,11 @@ class NbTuning(ctypes.Structure):
         ("large_j_split", c_int32),
         ("small_us", c_double),
         ("large_us", c_double),
+        ("tiny_split", c_int32),
+        ("tiny_i_per_thread", c_int32),
+        ("tiny_ctas_per_sm", c_int32),
+        ("tiny_j_split", c_int32),
+        ("tiny_us", c_double),
     ]
 
 
@@ -100,6 +105,7 @@ def load(path: str = LIB_PATH):
         "nb_energy_systems": (c_int32, [P, c_int32, P, P]),
         "nb_num_systems": (c_int32, [P]),
         "nb_autotune": (c_int32, [P, POINTER(NbTuning)]),
+        "nb_set_tuning": (c_int32, [P, POINTER(NbTuning)]),
         "nb_selftest_timeout": (c_int32, [P]),
         "nb_measure_peaks": (c_int32, [c_int32, POINTER(c_double), POINTER(c_double)]),
         "nb_snapshot_bytes": (c_int64, [P]),
@@ -218,6 +224,10 @@ def nb_num_systems(ctx) -> int:
 
 def nb_autotune(ctx, out_ref):
     return load().nb_autotune(ctx, out_ref)
+
+
+def nb_set_tuning(ctx, tuning_ref):
+    return load().nb_set_tuning(ctx, tuning_ref)
 
 
 def nb_selftest_timeout(ctx):
@@ -393,6 +403,12 @@ class Context:
         tun = NbTuning()
         self._ck(nb_autotune(self.handle, ctypes.byref(tun)))
         return {name: getattr(tun, name) for name, _ in NbTuning._fields_}
+
+    def set_tuning(self, **shapes):
+        """Set the force launch shapes (the fields of ``nb_tuning``; those not
+        given are 0, i.e. no tiny shape)."""
+        tun = NbTuning(**shapes)
+        self._ck(nb_set_tuning(self.handle, ctypes.byref(tun)))
 
     def spatial_order(self):
         """The particles in the context's spatial (j-layout slot) order."""

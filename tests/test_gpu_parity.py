@@ -387,7 +387,7 @@ def test_autotune_picks_valid_shapes_and_keeps_results(gpu, orc, prec):
             assert tun[f"{b}_us"] > 0
         ctx.set_state(**_state_at_rest(n, m, r, v), eps=eps, eta=0.02)
         ctx.predict(0.0)
-        for k in (17, n):  # one block in each bucket
+        for k in (17, 100, n):  # one block in each bucket
             acc, jerk, pot = ctx.force(idx[:k])
             if prec == "mixed":
                 sa, sj, _ = _magnitude_sums(m, r, v, eps, idx[:k])
