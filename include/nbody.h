@@ -140,9 +140,13 @@ void nb_config_init(nb_config* cfg);
  * particles); ctas_per_sm sets the persistent grid, which fixes how far each
  * i-group's j range is split across warps.  An ensemble context uses one
  * i-tile and one j split for both shapes (its force plan is cut once per
- * block) and no tiny shape.  The *_us fields give the force time the
- * autotuner measured for the chosen shapes on their probe blocks (tiny_us 0
- * without a tiny shape). */
+ * block) and no tiny shape.  An ensemble's force launch cuts its (i-group,
+ * j tile) pairs into ens_chunks chunks per warp: with 1 each warp takes one
+ * contiguous range; with more (by default 4 for the hybrid precisions, whose
+ * tiles differ several-fold in cost), each warp's first chunk is its own
+ * and the rest go to warps in the order they come free.  The *_us fields give the force time the autotuner
+ * measured for the chosen shapes on their probe blocks (tiny_us 0 without a
+ * tiny shape). */
 typedef struct nb_tuning {
     int32_t small_i_per_thread;
     int32_t small_ctas_per_sm;
@@ -158,6 +162,8 @@ typedef struct nb_tuning {
     int32_t tiny_ctas_per_sm;
     int32_t tiny_j_split;
     double tiny_us;
+    int32_t ens_chunks;   /* ensembles: stream-K chunks per warp, 1-4 (0: the
+                           * default, 4 for the hybrid precisions, else 1) */
 } nb_tuning;
 
 /* Autotuner: time every candidate launch shape of the force kernel on the
@@ -180,8 +186,8 @@ nb_status nb_autotune(nb_ctx* ctx, nb_tuning* out);
  * used (the tiny one only when tiny_split > 0) must name a built kernel
  * (i_per_thread 1 or 2, j_split 1, 2, 4 or 8; 2 i per thread only with j
  * split 1) and 1 to its occupancy of CTAs per SM; 0 <= tiny_split <
- * nact_split.  An ensemble context takes equal small and large i-tiles and
- * j splits and tiny_split 0.  The shapes hold until the next nb_autotune (a
+ * nact_split; 0 <= ens_chunks <= 4.  An ensemble context takes equal small
+ * and large i-tiles and j splits and tiny_split 0.  The shapes hold until the next nb_autotune (a
  * context created with autotune = 1 retunes on every load).  Errors:
  * NB_EINVAL (shape or boundary out of range; nothing changes), NB_ECUDA. */
 nb_status nb_set_tuning(nb_ctx* ctx, const nb_tuning* tuning);

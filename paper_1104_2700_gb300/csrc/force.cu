@@ -140,7 +140,8 @@ int64_t force_counter_stride(int64_t n_act_max, int warps)
 
 int64_t force_counter_entries(int64_t n_act_max, int warps)
 {
-    return RLEVELS * force_counter_stride(n_act_max, warps);
+    // the reduction levels, then the chunk queue word
+    return RLEVELS * force_counter_stride(n_act_max, warps) + 1;
 }
 
 cudaError_t force_launch(const ForceArgs& a, cudaStream_t s)
@@ -190,6 +191,8 @@ cudaError_t force_launch(const ForceArgs& a, cudaStream_t s)
     f.n_act_host = a.n_act_host;
     f.idx_map = a.idx_map;
     f.guard_eta = static_cast<float>(HY_GUARD * a.eta);
+    f.dyn_chunks = ens ? (a.dyn_chunks < MAX_CHUNKS ? a.dyn_chunks : MAX_CHUNKS) : 0;
+    f.queue = a.counters + RLEVELS * a.counter_stride;
     if (f.jt_hi > 0 && (a.plan.grp_tile0 || f.jt_lo < 0 || f.jt_hi <= f.jt_lo ||
                         f.jt_hi > f.n_pad / TJ))
         return cudaErrorInvalidValue;

@@ -78,6 +78,10 @@ struct ForceParams {
     int32_t n_act_host;
     const int32_t* idx_map;
     float guard_eta;  // HYBRID: the guard's coefficient times eta
+    // Ensemble plans: stream-K chunks per warp, >= 2 handed out by a queue
+    // (see force_kernel); the queue word, zero between launches.
+    int32_t dyn_chunks;
+    uint32_t* queue;
 };
 
 // A double narrowed to FP32 with integer operations only: the top 23
@@ -1028,6 +1032,7 @@ constexpr int CTA_BATCH = 16;
 // fewest tiles a chunk is cut down to.
 constexpr int MAX_CHUNKS = 4;
 constexpr int64_t CHUNK_MIN_TILES = 32;
+constexpr int64_t DYN_MIN_TILES = 4;  // chunks handed out by the queue
 
 // One i-group of a launch: up to 32*IT consecutive active-list entries of
 // one system and the j tiles of that system, placed at flattened tile0.
@@ -1086,7 +1091,7 @@ struct UniformPlan {
         jstride = tile_stride(NT);
         e2 = make_eps2(f.eps2);
     }
-    __device__ int64_t find(int64_t t) const { return t / NT; }
+    __device__ int64_t find(int64_t t, int) const { return t / NT; }
     __device__ GroupInfo group(int64_t g) const
     {
         GroupInfo gi;
@@ -1102,9 +1107,11 @@ struct UniformPlan {
     }
 };
 
-// Independent systems (ensemble): group descriptors from plan_launch.  Its
-// groups are small and many, so one stream-K range per warp already mixes
-// them (no chunks).
+// Independent systems (ensemble): group descriptors from plan_launch.  The
+// cost of a tile varies several-fold between systems and groups (far tiles,
+// near tiles of compact systems, groups under the hybrid integration
+// guard), so a launch may cut the tiles into several chunks per warp and
+// hand them out from a queue (ForceParams::dyn_chunks).
 struct ClusterPlan {
     static constexpr bool CHUNKED = false;
     const ForceParams* f;
@@ -1116,14 +1123,23 @@ struct ClusterPlan {
         G = fp.plan_scalars[0];
         T = fp.plan_scalars[1];
     }
-    __device__ int64_t find(int64_t t) const
+    // The last group g with tile0[g] <= t, found by the whole warp (called
+    // converged): each round the lanes test 32 evenly spaced tile0 entries
+    // of [lo, hi), so a plan of G groups takes ceil(log32 G) rounds of one
+    // load each instead of log2 G dependent loads.  tile0[lo] <= t holds
+    // throughout (tile0[0] = 0), so lane 0's test always passes.
+    __device__ int64_t find(int64_t t, int lane) const
     {
-        int64_t lo = 0, hi = G;  // last g with tile0[g] <= t
-        while (hi - lo > 1) {
-            const int64_t mid = (lo + hi) >> 1;
-            if (f->grp_tile0[mid] <= t) lo = mid; else hi = mid;
+        int64_t lo = 0, hi = G;
+        for (;;) {
+            const int64_t step = hi - lo > 32 ? (hi - lo + 31) / 32 : 1;
+            const int64_t k = lo + lane * step;
+            const bool le = k < hi && f->grp_tile0[k] <= t;
+            const uint32_t m = __ballot_sync(0xffffffffu, le);
+            lo += static_cast<int64_t>(31 - __clz(m)) * step;
+            if (step == 1) return lo;
+            hi = lo + step < hi ? lo + step : hi;
         }
-        return lo;
     }
     __device__ GroupInfo group(int64_t g) const
     {
@@ -1343,10 +1359,33 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
     // KC stretches of the space, so that regions of dearer tiles (the near
     // tiles of the hybrid precision crowd where the particles do) are shared
     // by all warps.  Chunks keep at least CHUNK_MIN_TILES tiles.
-    int64_t KC = Plan::CHUNKED ? K::CHUNKS : 1;
-    while (KC > 1 && T < P * KC * CHUNK_MIN_TILES) --KC;
+    //
+    // Ensemble plans with dyn_chunks >= 2 cut the space into up to that many
+    // chunks per warp instead, of at least DYN_MIN_TILES tiles: warp w takes
+    // chunk w, then chunks P, P + 1, ... from a queue, in the order warps
+    // come free, so warps whose tiles were cheap take more of them.  Chunk
+    // bounds, and with them the split-group sums below, do not depend on
+    // which warp takes a chunk.  Every warp makes exactly one fetch that
+    // finds the queue empty, so the launch makes n_queued + P fetches, and
+    // the one that draws the last value puts the queue word back to zero.
+    const bool dyn = !Plan::CHUNKED && f.dyn_chunks > 1;
+    int64_t KC = Plan::CHUNKED ? K::CHUNKS : (dyn ? f.dyn_chunks : 1);
+    const int64_t min_tiles = dyn ? DYN_MIN_TILES : CHUNK_MIN_TILES;
+    while (KC > 1 && T < P * KC * min_tiles) --KC;
     const int64_t NCH = cta ? 1 : (P * KC < T ? P * KC : T);
-    if (!cta && w >= NCH) return;
+    if (!cta && !dyn && w >= NCH) return;
+    const int64_t n_queued = dyn && NCH > P ? NCH - P : 0;
+    auto next_chunk = [&](int64_t ch) -> int64_t {
+        if (cta) return ch + 1;
+        if (!dyn) return ch + P;
+        uint32_t v = 0;
+        if (lane == 0) {
+            v = atomicAdd(f.queue, 1u);
+            if (v == static_cast<uint32_t>(n_queued + P - 1)) atomicExch(f.queue, 0u);
+        }
+        v = __shfl_sync(0xffffffffu, v, 0);
+        return v < n_queued ? P + static_cast<int64_t>(v) : NCH;
+    };
 
     unsigned char* wsm = smem + (size_t)wib * WarpSmem<K>::BYTES;
     uint64_t* bars = reinterpret_cast<uint64_t*>(wsm);
@@ -1389,7 +1428,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
         loaded = true;
     };
 
-    for (int64_t ch = cta ? 0 : w; ch < NCH; ch += cta ? 1 : P) {
+    for (int64_t ch = cta ? 0 : (w < NCH ? w : next_chunk(w)); ch < NCH; ch = next_chunk(ch)) {
     int64_t t0, t1;
     if (!cta) {
         t0 = T * ch / NCH;
@@ -1413,7 +1452,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, K::MIN_CTAS)
     }
     // Compute cursor (g, gi) and load cursor (lg, lgi): both start at the
     // group of tile t0; the load cursor runs STAGES tiles ahead.
-    int64_t g = cta ? cg : plan.find(t0);
+    int64_t g = cta ? cg : plan.find(t0, lane);
     GroupInfo gi = plan.group(g);
     int64_t lg = g;
     GroupInfo lgi = gi;

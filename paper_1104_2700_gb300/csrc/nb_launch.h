@@ -176,6 +176,10 @@ struct ForceArgs {
     int32_t n_act_host = -1;
     // Optional: idx holds caller indices, idx_map[i] is the layout slot of i.
     const int32_t* idx_map = nullptr;
+    // Ensemble plans: up to this many stream-K chunks per warp (at most
+    // MAX_CHUNKS), the chunks after each warp's first taken from a queue in
+    // the order warps come free; 0 or 1: one chunk per warp.
+    int32_t dyn_chunks = 0;
 };
 
 cudaError_t force_setup(Prec p, int it, int split);  // one-time attribute setup

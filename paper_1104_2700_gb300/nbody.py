@@ -58,6 +58,7 @@ class NbTuning(ctypes.Structure):
         ("tiny_ctas_per_sm", c_int32),
         ("tiny_j_split", c_int32),
         ("tiny_us", c_double),
+        ("ens_chunks", c_int32),
     ]
 
 

@@ -39,7 +39,7 @@ def test_config_defaults(nbody_lib):
     assert cfg.wait_limit_cycles == 0
     assert ctypes.sizeof(nbody_lib.NbConfig) == 72
     assert cfg.j_split == 0
-    assert ctypes.sizeof(nbody_lib.NbTuning) == 72
+    assert ctypes.sizeof(nbody_lib.NbTuning) == 80
 
 
 @pytest.mark.parametrize("field,value", [("dt_max", 0.1), ("dt_max", -1.0),

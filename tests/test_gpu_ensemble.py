@@ -64,6 +64,42 @@ def test_ensemble_force_equals_each_system_alone(gpu, orc, prec, tol, split):
                 assert (np.abs(pot[sel] - p0) / np.abs(p0)).max() < tol
 
 
+@pytest.mark.parametrize("chunks", [1, 2, 4])
+@pytest.mark.parametrize("prec,tol", [("ds", 1e-9), ("hybrid", 1e-6)])
+def test_ensemble_queued_chunks(gpu, orc, prec, tol, chunks):
+    """Several stream-K chunks per warp, those past each warp's first handed
+    out by a queue in the order warps come free.  Groups of 4 (j split 8)
+    and one CTA per SM give ~23000 tiles for 608 warps, so with 4 chunks per
+    warp 1824 chunks go through the queue.  Every system's forces equal the
+    oracle's, in two launches in a row (a queue left non-zero by the first
+    would drop chunks from the second), and the second repeats the first
+    bit for bit where nothing else changed between them (DS)."""
+    sizes = [100, 333, 1000, 64, 2049, 1, 700]
+    off, m, r, v, eps = _systems(sizes, 500)
+    n = int(off[-1])
+    shape = dict(small_i_per_thread=1, small_j_split=8, small_ctas_per_sm=1,
+                 large_i_per_thread=1, large_j_split=8, large_ctas_per_sm=1,
+                 nact_split=1024, ens_chunks=chunks)
+    idx = np.arange(n, dtype=np.int32)
+    with gpu.Context(prec) as ctx:
+        ctx.set_ensemble(off, m, r, v, eps, 0.02)
+        ctx.set_tuning(**shape)
+        ctx.predict(0.0)
+        runs = [ctx.force(idx), ctx.force(idx)]
+    for q in range(len(sizes)):
+        lo, hi = off[q], off[q + 1]
+        if hi - lo == 1:
+            continue
+        a0, j0, p0 = orc.force(m[lo:hi], r[lo:hi], v[lo:hi], eps[q], nthreads=NTHREADS)
+        for acc, jerk, pot in runs:
+            assert _rel(acc[lo:hi], a0).max() < tol, q
+            assert _rel(jerk[lo:hi], j0).max() < tol, q
+            assert (np.abs(pot[lo:hi] - p0) / np.abs(p0)).max() < tol, q
+    if prec == "ds":
+        for x, y in zip(*runs):
+            assert np.array_equal(x, y)
+
+
 def test_ensemble_integration_matches_each_system_alone(gpu):
     sizes = [128, 300, 512, 77]
     off, m, r, v, eps = _systems(sizes, 400)
