@@ -107,6 +107,10 @@ def test_set_tuning_rejects_bad_shapes(gpu, plummer8k):
         with pytest.raises(gpu.NbError) as e:  # two i per thread take no j split
             ctx.set_tuning(**dict(_shapes(), small_i_per_thread=2))
         assert e.value.status == gpu.NB_EINVAL
+        for chunks in (-1, 5):  # stream-K chunks per warp: 0 (default) to 4
+            with pytest.raises(gpu.NbError) as e:
+                ctx.set_tuning(**dict(_shapes(), ens_chunks=chunks))
+            assert e.value.status == gpu.NB_EINVAL
         ctx.set_tuning(**_shapes(tiny_split=0, tiny_j_split=0))  # tiny unused: unchecked
         ctx.predict(0.0)
         ctx.force(np.arange(10, dtype=np.int32))  # the errors were not sticky
