@@ -857,7 +857,7 @@ nb_status nb_create(const nb_config* cfg, nb_ctx** out)
         c->var[v].split = split;
         c->var[v].grid = per_sm * c->num_sms;
     }
-    c->var[2] = c->var[0];  // no tiny variant until the autotuner sets one
+    c->var[2] = c->var[0];  // no tiny variant until nb_autotune or nb_set_tuning sets one
     if (nb::force_setup(Prec::FP64, 1, 1) != cudaSuccess) return bail(NB_ECUDA);
     const int per_sm64 = nb::force_ctas_per_sm(Prec::FP64, 1, 1);
     if (per_sm64 < 1) return bail(NB_ECUDA);
