@@ -166,29 +166,33 @@ typedef struct nb_tuning {
                            * default, 4 for the hybrid precisions, else 1) */
 } nb_tuning;
 
-/* Autotuner: time every candidate launch shape of the force kernel on the
- * loaded system (probe blocks of 32, 96, 256, 2048 and min(n, 65536)
- * particles spread evenly over the context's stored order, nb_spatial_order,
- * like the scattered members of a block step; for the hybrid precision with
- * the integration guard idle, as in a steady integration) and keep the
- * fastest for each bucket, with the bucket boundary nact_split at 1024
- * (probes up to 256 small) or 4096 (2048 small too), whichever gives the
- * least total.  A single system then may take a tiny shape (tiny_split 64:
- * probe 32; 160: probes 32 and 96), kept only when it beats the small shape
- * on those probes by more than 0.5 us.  Predicts all particles to the time
- * of particle 0 first, so call nb_predict again before nb_force.  *out (may
- * be NULL) receives the choice.  Blocks.  Errors: NB_ESTATE (nothing
- * loaded), NB_ECUDA. */
+/* Autotuner.  The paper compares blockings of its force loop (i by j
+ * particles per AVX register) by measurement and fixes the fastest (Sec.
+ * 3.3); this makes that comparison at run time, on the loaded workload.  It
+ * times every candidate launch shape of the force kernel on probe blocks of
+ * 32, 96, 256, 2048 and min(n, 65536) particles, spread evenly over the
+ * context's stored order (nb_spatial_order) like the scattered members of a
+ * block step (for the hybrid precision with the integration guard idle, as
+ * in a steady integration), and keeps the fastest for each bucket, with the
+ * bucket boundary nact_split at 1024 (probes up to 256 small) or 4096 (2048
+ * small too), whichever gives the least total.  A single system then may
+ * take a tiny shape (tiny_split 64: probe 32; 160: probes 32 and 96), kept
+ * only when it beats the small shape on those probes by more than 0.5 us.
+ * Predicts all particles to the time of particle 0 first, so call
+ * nb_predict again before nb_force.  *out (may be NULL) receives the choice.
+ * Blocks.  Errors: NB_ESTATE (nothing loaded), NB_ECUDA. */
 nb_status nb_autotune(nb_ctx* ctx, nb_tuning* out);
 
-/* Set the force launch shapes by hand, e.g. ones an earlier nb_autotune
- * returned for the same workload (its *_us fields are ignored).  Each shape
+/* Set the force launch shapes by hand (a fixed blocking, as Sec. 3.3
+ * fixes its own), e.g. ones an earlier nb_autotune returned for the same
+ * workload (its *_us fields are ignored).  Each shape
  * used (the tiny one only when tiny_split > 0) must name a built kernel
  * (i_per_thread 1 or 2, j_split 1, 2, 4 or 8; 2 i per thread only with j
  * split 1) and 1 to its occupancy of CTAs per SM; 0 <= tiny_split <
  * nact_split; 0 <= ens_chunks <= 4.  An ensemble context takes equal small
- * and large i-tiles and j splits and tiny_split 0.  The shapes hold until the next nb_autotune (a
- * context created with autotune = 1 retunes on every load).  Errors:
+ * and large i-tiles and j splits and tiny_split 0.  The shapes hold until
+ * the next nb_autotune (a context created with autotune = 1 retunes on
+ * every load).  Errors:
  * NB_EINVAL (shape or boundary out of range; nothing changes), NB_ECUDA. */
 nb_status nb_set_tuning(nb_ctx* ctx, const nb_tuning* tuning);
 
