@@ -142,11 +142,11 @@ void nb_config_init(nb_config* cfg);
  * i-tile and one j split for both shapes (its force plan is cut once per
  * block) and no tiny shape.  An ensemble's force launch cuts its (i-group,
  * j tile) pairs into ens_chunks chunks per warp: with 1 each warp takes one
- * contiguous range; with more (by default 4 for the hybrid precisions, whose
- * tiles differ several-fold in cost), each warp's first chunk is its own
- * and the rest go to warps in the order they come free.  The *_us fields give the force time the autotuner
- * measured for the chosen shapes on their probe blocks (tiny_us 0 without a
- * tiny shape). */
+ * contiguous range; with more (by default 4 for the hybrid precisions,
+ * whose tiles differ several-fold in cost), each warp's first chunk is its
+ * own and the rest go to warps in the order they come free.  The *_us
+ * fields give the force time the autotuner measured for the chosen shapes
+ * on their probe blocks (tiny_us 0 without a tiny shape). */
 typedef struct nb_tuning {
     int32_t small_i_per_thread;
     int32_t small_ctas_per_sm;
