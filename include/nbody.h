@@ -415,9 +415,9 @@ const char* nb_status_string(nb_status s);
  * kernel attributes).  Under the CUDA runtime's default lazy module
  * loading, that is also when the driver loads this part of the library onto
  * the device and so reserves the array's NB_STATIC_SCRATCH_BYTES: a caller
- * that later reserves all remaining GPU memory must make its first call
- * (a call with n_act = 0 is enough) before it does so, and before any stream capture.
- * Later calls allocate nothing.
+ * that later reserves all remaining GPU memory must make its first call (a
+ * call with n_act = 0 is enough) before it does so, and before any stream
+ * capture.  Later calls allocate nothing.
  *
  * Every call synchronises `stream` to read back the kernel's status word, so
  * the call cannot be made while `stream` is being captured into a graph.
